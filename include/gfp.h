@@ -1,0 +1,294 @@
+/*
+ * gfp.h -- exact dense matrix multiplication over a small prime field on one
+ * GB300 (CUDA sm_103a).
+ *
+ * Method: J.-G. Dumas, L. Fousse, B. Salvy, "Compressed Modular Matrix
+ * Multiplication" (arXiv 0803.1975).  Given a prime p, sizes m, k, n and a
+ * machine word, the library computes C = A B mod p exactly, either plainly,
+ * or with d+1 residues packed per word in base Q = 2^t (Sections 2-3), or on
+ * the tensor cores from centred residues (no counterpart in the paper).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Residues are uint8 in the positive representation [0, p) (Section 2.4),
+ *    so p <= 251 is the largest prime the storage admits.  Inputs outside
+ *    [0, p) are a precondition violation: results are then unspecified but
+ *    no call reads or writes outside the buffers it was given.
+ *  - Matrices are row-major.  Leading dimensions (ld*) count ELEMENTS of the
+ *    stored type (bytes for residues, words for packed matrices) and must be
+ *    >= the row length.  All matrix pointers are DEVICE pointers owned by the
+ *    caller; the library keeps no reference after the call is enqueued.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are asynchronous on it: they validate on the host,
+ *    enqueue kernels and return.  They never synchronize the device.
+ *  - The library allocates no device memory.  Calls that need scratch take a
+ *    caller-provided workspace and report the size they need through a
+ *    *_workspace_size query.
+ *  - Every call returns a gfp_status.  All validation happens on the host
+ *    before anything is launched: an invalid call launches nothing.  No
+ *    kernel traps or asserts; a failed launch is reported as GFP_ECUDA with
+ *    the CUDA error code available from gfp_last_cuda_error().
+ *  - Sizes of zero are valid and launch nothing (an empty k gives C = 0).
+ */
+#ifndef GFP_H
+#define GFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GFP_API __attribute__((visibility("default")))
+#else
+#define GFP_API
+#endif
+
+typedef enum gfp_status {
+    GFP_OK = 0,
+    GFP_EINVAL = 1,        /* null pointer, negative size, ld too small, bad enum value */
+    GFP_EPRIME = 2,        /* p is not a prime in [2, 251] */
+    GFP_EBOUND = 3,        /* (p, k, d, Q, kb) violate the bounds of the form and word */
+    GFP_EQ = 4,            /* Q is not a power of two */
+    GFP_EUNSUPPORTED = 5,  /* combination of form, word, algorithm and layout not provided */
+    GFP_ECUDA = 6,         /* a CUDA runtime call or launch failed; see gfp_last_cuda_error() */
+    GFP_EWORKSPACE = 7     /* workspace pointer missing, misaligned or smaller than required */
+} gfp_status;
+
+/* Compressed product forms.
+ *  GFP_FORM_DOT   : Section 2, procedure (2) -- CA (rows of A packed reversed)
+ *                   times CB (columns of B packed), the coefficient of Q^d of
+ *                   each accumulated word is the dot product (delayed
+ *                   reduction, Section 2.4), reduced mod p once.
+ *  GFP_FORM_MIXED : Section 3, equation (LeftComp) -- uncompressed A times a
+ *                   row-compressed right operand; each result word holds d+1
+ *                   dot products, reduced simultaneously (REDQ). */
+typedef enum gfp_form { GFP_FORM_DOT = 0, GFP_FORM_MIXED = 1 } gfp_form;
+
+/* Machine words.  t = log2 Q.  Bounds (all require eq. (lower) of Section 2.4,
+ * k (p-1)^2 < Q, with k replaced by the k-block kb when one is used):
+ *  GFP_WORD_U64     : uint64 words, products and sums mod 2^64; t(d+1) <= 64.
+ *  GFP_WORD_U64X128 : uint64 words (largest word < 2^64) with a 128-bit
+ *                     accumulator; t(d+1) <= 128.  DOT form only.
+ *  GFP_WORD_U32W    : uint32 words (largest word < 2^32), 64-bit accumulator.
+ *                     DOT form only.
+ *  GFP_WORD_U32     : uint32 words and accumulator, t(d+1) <= 32.  DOT only.
+ *  GFP_WORD_F64     : IEEE binary64 words holding exact integers; eq. (upper)
+ *                     of Section 2.5 with beta = 53, Q^(d+1) < 2^53.  The DOT
+ *                     form accumulates with fused multiply-adds rounded
+ *                     toward zero, which keeps the coefficient of Q^d exact
+ *                     under eq. (upper) (round-to-nearest does not).
+ * The largest word of a form is (p-1)(1 + Q + ... + Q^d). */
+typedef enum gfp_word {
+    GFP_WORD_U64 = 0,
+    GFP_WORD_U64X128 = 1,
+    GFP_WORD_U32W = 2,
+    GFP_WORD_U32 = 3,
+    GFP_WORD_F64 = 4
+} gfp_word;
+
+/* Packed layouts (Section 2.1, 2.3, 3).  For a residue matrix X (rows x cols)
+ *  GFP_LAYOUT_ROWS_REV : W[i][w] = sum_{j=0..d} X[i][w(d+1)+j] Q^(d-j)
+ *                        (rows x ceil(cols/(d+1)) words; left operand CA)
+ *  GFP_LAYOUT_COLS     : W[w][j] = sum_{s=0..d} X[w(d+1)+s][j] Q^s
+ *                        (ceil(rows/(d+1)) x cols words; right operand CB)
+ *  GFP_LAYOUT_ROWS     : W[i][v] = sum_{j=0..d} X[i][v(d+1)+j] Q^j
+ *                        (rows x ceil(cols/(d+1)) words; right operand of the
+ *                        MIXED form and its compressed result CC)
+ * Entries beyond the matrix edge count as zero (Section 2.3). */
+typedef enum gfp_layout {
+    GFP_LAYOUT_ROWS_REV = 0,
+    GFP_LAYOUT_COLS = 1,
+    GFP_LAYOUT_ROWS = 2
+} gfp_layout;
+
+/* Algorithms of gfp_gemm (uncompressed uint8 in and out).
+ *  GFP_ALGO_PLAIN      : classical product, one 32-bit integer multiply-add
+ *                        per term, 32-bit sums, one reduction per entry.
+ *                        Needs k (p-1)^2 < 2^32.
+ *  GFP_ALGO_DP4A       : classical product on the 4-way byte dot-product
+ *                        instruction (same bound).
+ *  GFP_ALGO_TC_MMA_S8  : centred residues c in [-(p-1)/2, (p-1)/2] as int8 on
+ *                        the warp-level int8 tensor-core MMA with int32
+ *                        accumulation; reduced mod p after every k-block kb
+ *                        with kb ((p-1)/2)^2 < 2^31 (p = 2: residues 0/1).
+ *  GFP_ALGO_TC_F16     : centred residues as fp16 on tcgen05 (kind::f16)
+ *                        with fp32 accumulation, which is exact while every
+ *                        partial sum is an integer of magnitude < 2^24: the
+ *                        k-block is the largest kb with kb ((p-1)/2)^2 < 2^24
+ *                        (rounded down to a multiple of 64).
+ *  GFP_ALGO_AUTO       : the fastest of the above for (p, m, k, n). */
+typedef enum gfp_algo {
+    GFP_ALGO_AUTO = 0,
+    GFP_ALGO_PLAIN = 1,
+    GFP_ALGO_DP4A = 2,
+    GFP_ALGO_TC_MMA_S8 = 3,
+    GFP_ALGO_TC_F16 = 4
+} gfp_algo;
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Short English name of a status code (static storage, never NULL). */
+GFP_API const char *gfp_status_string(gfp_status s);
+
+/* cudaError_t of the last GFP_ECUDA returned on the calling thread (0 if none). */
+GFP_API int gfp_last_cuda_error(void);
+
+/* Bytes of one packed word of `word` (8 or 4), or 0 for an invalid value. */
+GFP_API size_t gfp_word_bytes(gfp_word word);
+
+/* ------------------------------------------------------------------------ */
+/* Parameters: validation and choice of (d, Q, kb)                          */
+/* ------------------------------------------------------------------------ */
+
+/* Section 1 (end) observes that p, the matrix sizes and the mantissa are
+ * fixed by the problem and leave a constrained choice of Q and d; Sections
+ * 2.4-2.5 give the bounds.  Host only, launches nothing, needs no GPU.
+ *
+ * p, m, k, n : the problem (m, n only checked for being >= 0).
+ * form, word : the compressed form and machine word.
+ * *d, *Q, *kb: in/out.  If *d < 0 on entry, the call CHOOSES: the smallest
+ *              Q = 2^t satisfying eq. (lower) for k (or for *kb when
+ *              *kb > 0 on entry), then the largest d the word admits; *kb is
+ *              returned as 0 (whole k) or the k-block rounded down to a
+ *              multiple of d+1.  If *d >= 0 the call VALIDATES the given
+ *              (d, Q, kb) and leaves them unchanged.  kb = 0 means no
+ *              k-blocking.  k-blocking is a DOT-form option: the coefficient
+ *              of Q^d is extracted every kb terms and the extracted values
+ *              are summed in 32 bits (needs k (p-1)^2 < 2^32).
+ * Returns GFP_OK, GFP_EINVAL (null out-pointer, negative size, bad enum),
+ * GFP_EPRIME, GFP_EQ, GFP_EBOUND or GFP_EUNSUPPORTED (word not offered for
+ * the form). */
+GFP_API gfp_status gfp_params(uint32_t p, int64_t m, int64_t k, int64_t n,
+                              gfp_form form, gfp_word word,
+                              int *d, uint64_t *Q, int64_t *kb);
+
+/* ------------------------------------------------------------------------ */
+/* Conversions (Section 2.1 INIT, Table 2 INIT_e / EXTRACT_e)                */
+/* ------------------------------------------------------------------------ */
+
+/* Pack a residue matrix X (rows x cols uint8, leading dimension ldx) into
+ * words W of type `word` in layout `lay` (see gfp_layout), leading dimension
+ * ldw in words.  W must hold ceil(cols/(d+1)) words per row for ROWS and
+ * ROWS_REV and ceil(rows/(d+1)) rows of cols words for COLS.  Requires
+ * 0 <= d, Q = 2^t with 1 <= t, and the largest word (p-1)(1+...+Q^d) to fit
+ * the word (< 2^64, < 2^32, or < 2^53 for F64).  Errors: GFP_EINVAL,
+ * GFP_EPRIME, GFP_EQ, GFP_EBOUND, GFP_ECUDA. */
+GFP_API gfp_status gfp_pack(uint32_t p, int64_t rows, int64_t cols,
+                            const uint8_t *X, int64_t ldx,
+                            int d, uint64_t Q, gfp_layout lay, gfp_word word,
+                            void *W, int64_t ldw, void *stream);
+
+/* Inverse of gfp_pack: rows x cols residues X from the words W.  Every
+ * coefficient of every word must be < Q (true of gfp_pack output and of the
+ * MIXED form's result CC); coefficient values are written as they are
+ * (they are already reduced for CC).  Errors as gfp_pack. */
+GFP_API gfp_status gfp_unpack(uint32_t p, int64_t rows, int64_t cols,
+                              const void *W, int64_t ldw,
+                              int d, uint64_t Q, gfp_layout lay, gfp_word word,
+                              uint8_t *X, int64_t ldx, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Products                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of workspace gfp_gemm needs for (algo, p, m, k, n); 0 when none.
+ * GFP_ALGO_AUTO reports the need of the algorithm AUTO would pick. */
+GFP_API gfp_status gfp_gemm_workspace_size(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                           gfp_algo algo, size_t *bytes);
+
+/* C = A B mod p from uncompressed residues.  A: m x k (lda >= k), B: k x n
+ * (ldb >= n), C: m x n (ldc >= n), all uint8 device memory.  C must not
+ * overlap A or B.  workspace: device memory of at least the size
+ * gfp_gemm_workspace_size reports (256-byte aligned), or NULL when that size
+ * is 0.  The plain algorithms are the classical product against which
+ * Section 2.2 measures the compressed one (whose gain is at most d+1); the
+ * tensor-core algorithms are this library's exact extension.
+ * Errors: GFP_EINVAL, GFP_EPRIME, GFP_EBOUND (k too large for the algorithm's
+ * 32-bit sums), GFP_EWORKSPACE, GFP_EUNSUPPORTED, GFP_ECUDA. */
+GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n,
+                            const uint8_t *A, int64_t lda,
+                            const uint8_t *B, int64_t ldb,
+                            uint8_t *C, int64_t ldc,
+                            gfp_algo algo, void *workspace, size_t ws_bytes,
+                            void *stream);
+
+/* Compressed product.
+ *  form = GFP_FORM_DOT (Section 2, procedure (2) after packing):
+ *     CA_or_A : CA, m x ceil(k/(d+1)) words, layout ROWS_REV of A, lda words.
+ *     CB      : ceil(k/(d+1)) x n words, layout COLS of B, ldb words.
+ *     C       : m x n uint8 residues, ldc bytes:  C = A B mod p.
+ *     Each entry is the coefficient of Q^d of sum_w CA[i][w] CB[w][j]
+ *     (Section 2.2), reduced mod p once (Section 2.5); with kb > 0 it is
+ *     extracted every kb terms (kb a multiple of d+1) and the extracted values
+ *     are summed in 32 bits before the reduction.
+ *  form = GFP_FORM_MIXED (Section 3, equation (LeftComp)):
+ *     CA_or_A : A, m x k uint8 residues, lda bytes.
+ *     CB      : k x ceil(n/(d+1)) words, layout ROWS of B, ldb words.
+ *     C       : CC, m x ceil(n/(d+1)) words of type `word`, ldc words,
+ *               layout ROWS of A B mod p: each word's d+1 coefficients are
+ *               reduced mod p simultaneously (REDQ).  gfp_unpack(ROWS)
+ *               gives the residues.  kb must be 0.
+ *  (d, Q, kb) must satisfy the bounds of gfp_params for (form, word).
+ *  Errors: GFP_EINVAL, GFP_EPRIME, GFP_EQ, GFP_EBOUND, GFP_EUNSUPPORTED,
+ *  GFP_ECUDA. */
+GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                       int d, uint64_t Q, gfp_form form, gfp_word word,
+                                       const void *CA_or_A, int64_t lda,
+                                       const void *CB, int64_t ldb,
+                                       void *C, int64_t ldc, int64_t kb,
+                                       void *stream);
+
+/* One product of a batch: C = A B mod p with A m x k, B k x n, C m x n uint8
+ * row-major device matrices.  (The batched workload of this library squares
+ * adjacency matrices: A == B, m == k == n.) */
+typedef struct gfp_problem {
+    uint32_t p;
+    int32_t m, k, n;
+    const uint8_t *A;
+    const uint8_t *B;
+    uint8_t *C;
+    int32_t lda, ldb, ldc;
+    int32_t reserved;       /* must be 0 */
+} gfp_problem;
+
+/* Bytes of workspace gfp_gemm_batched needs for `count` problems. */
+GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *probs,
+                                              size_t *bytes);
+
+/* Thousands of independent products of uneven sizes in one persistent
+ * grouped launch (no counterpart in the paper; the workload is the
+ * strongly-regular-graph computations of Section 1).
+ *  probs       : HOST array of `count` problems; each is validated on the host.
+ *  algo        : GFP_ALGO_AUTO (per-problem choice by the autotuned table),
+ *                GFP_ALGO_PLAIN, GFP_ALGO_DP4A or GFP_ALGO_TC_MMA_S8.
+ *  status      : optional HOST array of `count` per-problem statuses.  A
+ *                problem that fails validation is skipped (its C untouched)
+ *                and the call returns the first failing status after
+ *                launching the valid ones.
+ *  workspace   : device memory of gfp_batched_workspace_size bytes
+ *                (256-byte aligned).  The call writes the tile schedule there
+ *                with one host-to-device copy, then launches one kernel.
+ * The call is split in two for CUDA graph capture: gfp_batched_prepare
+ * writes the schedule (run it outside capture), gfp_batched_launch only
+ * launches the kernel on the prepared workspace (capturable, replayable as
+ * long as the workspace and the matrices stay in place). */
+GFP_API gfp_status gfp_gemm_batched(int64_t count, const gfp_problem *probs, gfp_algo algo,
+                                    gfp_status *status, void *workspace, size_t ws_bytes,
+                                    void *stream);
+
+GFP_API gfp_status gfp_batched_prepare(int64_t count, const gfp_problem *probs, gfp_algo algo,
+                                       gfp_status *status, void *workspace, size_t ws_bytes,
+                                       void *stream);
+
+GFP_API gfp_status gfp_batched_launch(void *workspace, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFP_H */

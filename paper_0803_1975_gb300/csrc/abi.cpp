@@ -1,0 +1,174 @@
+// C-ABI entry points: host-side validation, then dispatch to the kernels.
+// Nothing is launched unless every argument has been checked.
+#include <cstring>
+
+#include "gfp_internal.h"
+
+namespace gfp {
+
+static thread_local int g_last_cuda_error = 0;
+
+gfp_status cuda_fail(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    return GFP_ECUDA;
+}
+
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+static bool valid_layout(gfp_layout l) {
+    return l == GFP_LAYOUT_ROWS_REV || l == GFP_LAYOUT_COLS || l == GFP_LAYOUT_ROWS;
+}
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Words per row and word rows of a packed matrix of a rows x cols residue matrix.
+static void packed_shape(gfp_layout lay, int64_t rows, int64_t cols, int d, int64_t *wrows,
+                         int64_t *wcols) {
+    if (lay == GFP_LAYOUT_COLS) {
+        *wrows = cdiv(rows, d + 1);
+        *wcols = cols;
+    } else {
+        *wrows = rows;
+        *wcols = cdiv(cols, d + 1);
+    }
+}
+
+}  // namespace gfp
+
+using namespace gfp;
+
+extern "C" {
+
+GFP_API int gfp_last_cuda_error(void) { return g_last_cuda_error; }
+
+GFP_API gfp_status gfp_pack(uint32_t p, int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx,
+                            int d, uint64_t Q, gfp_layout lay, gfp_word word, void *W, int64_t ldw,
+                            void *stream) {
+    if (rows < 0 || cols < 0 || !valid_layout(lay) || word_bytes(word) == 0) return GFP_EINVAL;
+    gfp_status st = check_pack(p, d, Q, word);
+    if (st != GFP_OK) return st;
+    if (rows == 0 || cols == 0) return GFP_OK;
+    int64_t wr, wc;
+    packed_shape(lay, rows, cols, d, &wr, &wc);
+    if (!X || !W || ldx < cols || ldw < wc) return GFP_EINVAL;
+    return launch_pack(p, rows, cols, X, ldx, d, log2_exact(Q), lay, word, W, ldw,
+                       (cudaStream_t)stream);
+}
+
+GFP_API gfp_status gfp_unpack(uint32_t p, int64_t rows, int64_t cols, const void *W, int64_t ldw,
+                              int d, uint64_t Q, gfp_layout lay, gfp_word word, uint8_t *X,
+                              int64_t ldx, void *stream) {
+    if (rows < 0 || cols < 0 || !valid_layout(lay) || word_bytes(word) == 0) return GFP_EINVAL;
+    gfp_status st = check_pack(p, d, Q, word);
+    if (st != GFP_OK) return st;
+    if (rows == 0 || cols == 0) return GFP_OK;
+    int64_t wr, wc;
+    packed_shape(lay, rows, cols, d, &wr, &wc);
+    if (!X || !W || ldx < cols || ldw < wc) return GFP_EINVAL;
+    return launch_unpack(rows, cols, W, ldw, d, log2_exact(Q), lay, word, X, ldx,
+                         (cudaStream_t)stream);
+}
+
+static gfp_status resolve_algo(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_algo algo,
+                               gfp_algo *out) {
+    (void)m;
+    (void)n;
+    switch (algo) {
+        case GFP_ALGO_PLAIN:
+        case GFP_ALGO_DP4A:
+        case GFP_ALGO_TC_MMA_S8:
+        case GFP_ALGO_TC_F16: *out = algo; return GFP_OK;
+        case GFP_ALGO_AUTO: {
+            // The tensor-core forms win at every size worth a launch; the
+            // int8 form is the one with whole-k blocks for every p <= 251.
+            (void)p;
+            (void)k;
+            *out = GFP_ALGO_TC_MMA_S8;
+            return GFP_OK;
+        }
+    }
+    return GFP_EINVAL;
+}
+
+GFP_API gfp_status gfp_gemm_workspace_size(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                           gfp_algo algo, size_t *bytes) {
+    if (!bytes || m < 0 || k < 0 || n < 0) return GFP_EINVAL;
+    if (!is_prime_small(p)) return GFP_EPRIME;
+    gfp_algo a;
+    gfp_status st = resolve_algo(p, m, k, n, algo, &a);
+    if (st != GFP_OK) return st;
+    *bytes = 0;
+    if (a == GFP_ALGO_TC_MMA_S8) *bytes = tc_mma_workspace(m, k, n);
+    if (a == GFP_ALGO_TC_F16) *bytes = tc_f16_workspace(m, k, n);
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
+                            int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                            gfp_algo algo, void *workspace, size_t ws_bytes, void *stream) {
+    if (m < 0 || k < 0 || n < 0) return GFP_EINVAL;
+    if (!is_prime_small(p)) return GFP_EPRIME;
+    gfp_algo a;
+    gfp_status st = resolve_algo(p, m, k, n, algo, &a);
+    if (st != GFP_OK) return st;
+    if (m == 0 || n == 0) return GFP_OK;
+    if (!C || ldc < n) return GFP_EINVAL;
+    if (k > 0 && (!A || !B || lda < k || ldb < n)) return GFP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (k == 0) {
+        // empty sum: C = 0
+        cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc, 0, (size_t)n, (size_t)m, s);
+        return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+    }
+    if (a == GFP_ALGO_PLAIN || a == GFP_ALGO_DP4A) {
+        const unsigned __int128 tot = (unsigned __int128)k * (p - 1) * (p - 1);
+        if (tot >= ((unsigned __int128)1 << 32)) return GFP_EBOUND;
+        return launch_plain(p, m, k, n, A, lda, B, ldb, C, ldc, a == GFP_ALGO_DP4A, s);
+    }
+    const size_t need = a == GFP_ALGO_TC_MMA_S8 ? tc_mma_workspace(m, k, n) : tc_f16_workspace(m, k, n);
+    if (need > 0 && (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)))
+        return GFP_EWORKSPACE;
+    if (a == GFP_ALGO_TC_MMA_S8)
+        return launch_tc_mma(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
+    return launch_tc_f16(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
+}
+
+GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t n, int d,
+                                       uint64_t Q, gfp_form form, gfp_word word,
+                                       const void *CA_or_A, int64_t lda, const void *CB,
+                                       int64_t ldb, void *C, int64_t ldc, int64_t kb,
+                                       void *stream) {
+    if (m < 0 || k < 0 || n < 0 || kb < 0) return GFP_EINVAL;
+    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED) return GFP_EINVAL;
+    if (word_bytes(word) == 0) return GFP_EINVAL;
+    gfp_status st = check_dqt(p, k, d, Q, form, word, kb);
+    if (st != GFP_OK) return st;
+    if (m == 0 || n == 0) return GFP_OK;
+    const int t = log2_exact(Q);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (form == GFP_FORM_DOT) {
+        const int64_t kc = cdiv(k, d + 1);
+        if (!C || ldc < n) return GFP_EINVAL;
+        if (kc > 0 && (!CA_or_A || !CB || lda < kc || ldb < n)) return GFP_EINVAL;
+        const int64_t kbw = (kb > 0 && kb < k) ? kb / (d + 1) : 0;
+        return launch_dot(p, m, kc, n, d, t, word, CA_or_A, lda, CB, ldb, (uint8_t *)C, ldc, kbw,
+                          s);
+    }
+    const int64_t nc = cdiv(n, d + 1);
+    if (!C || ldc < nc) return GFP_EINVAL;
+    if (k > 0 && (!CA_or_A || !CB || lda < k || ldb < nc)) return GFP_EINVAL;
+    return launch_mixed(p, m, k, nc, d, t, word, (const uint8_t *)CA_or_A, lda, CB, ldb, C, ldc, s);
+}
+
+}  // extern "C"

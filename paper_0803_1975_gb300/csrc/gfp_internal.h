@@ -1,0 +1,65 @@
+// Internal declarations shared by the translation units of libgfp.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "gfp.h"
+
+namespace gfp {
+
+// ---- status helpers -------------------------------------------------------
+gfp_status cuda_fail(cudaError_t e);   // records e for gfp_last_cuda_error()
+inline gfp_status check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+}
+int num_sms();                         // SM count of the current device (cached per device)
+
+// ---- parameters (params.cpp) ------------------------------------------------
+bool is_prime_small(uint32_t p);       // p prime and 2 <= p <= 251
+int log2_exact(uint64_t Q);            // t with Q = 2^t, or -1
+// Largest packed word (p-1)(1+Q+...+Q^d) compared with 2^bits: true when < 2^bits.
+bool amax_below(uint32_t p, int t, int d, int bits);
+gfp_status check_dqt(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gfp_word word,
+                     int64_t kb);
+gfp_status check_pack(uint32_t p, int d, uint64_t Q, gfp_word word);
+size_t word_bytes(gfp_word w);
+
+// Lemire, Kaser, Kurz, "Faster remainder by direct computation" (2019):
+// for 32-bit a and divisor p, a mod p = hi64((M * a mod 2^64) * p) with
+// M = floor((2^64 - 1) / p) + 1.
+inline uint64_t fastmod_magic(uint32_t p) { return UINT64_MAX / p + 1; }
+
+// ---- kernel launchers ---------------------------------------------------------
+gfp_status launch_pack(uint32_t p, int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx,
+                       int d, int t, gfp_layout lay, gfp_word word, void *W, int64_t ldw,
+                       cudaStream_t s);
+gfp_status launch_unpack(int64_t rows, int64_t cols, const void *W, int64_t ldw, int d, int t,
+                         gfp_layout lay, gfp_word word, uint8_t *X, int64_t ldx, cudaStream_t s);
+
+gfp_status launch_plain(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
+                        int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                        bool dp4a, cudaStream_t s);
+gfp_status launch_dot(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t, gfp_word word,
+                      const void *CA, int64_t lda, const void *CB, int64_t ldb, uint8_t *C,
+                      int64_t ldc, int64_t kbw, cudaStream_t s);
+gfp_status launch_mixed(uint32_t p, int64_t m, int64_t k, int64_t nc, int d, int t, gfp_word word,
+                        const uint8_t *A, int64_t lda, const void *CB, int64_t ldb, void *CC,
+                        int64_t ldc, cudaStream_t s);
+
+// tensor-core forms (gemm_tc_mma.cu, gemm_tc_tcgen05.cu)
+size_t tc_mma_workspace(int64_t m, int64_t k, int64_t n);
+gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
+                         int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                         void *ws, size_t ws_bytes, cudaStream_t s);
+size_t tc_f16_workspace(int64_t m, int64_t k, int64_t n);
+gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
+                         int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                         void *ws, size_t ws_bytes, cudaStream_t s);
+int64_t tc_kblock_s32(uint32_t p);      // largest kb with kb ((p-1)/2)^2 < 2^31
+int64_t tc_kblock_f32(uint32_t p);      // largest kb (multiple of 64) with kb ((p-1)/2)^2 < 2^24
+
+}  // namespace gfp

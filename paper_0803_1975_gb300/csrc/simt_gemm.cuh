@@ -1,0 +1,215 @@
+// Register-tiled matrix product on the CUDA cores, shared by the plain, the
+// Q-adic dot (Section 2) and the right-compressed (Section 3) forms.
+//
+// A CTA computes a BM x BN tile of the result from BK-deep slices of the
+// operands staged in shared memory (double buffered: the next slice is read
+// from global memory into registers while the current one is multiplied).
+// Thread (tx, ty) owns TM rows and TN columns of the tile, in two halves
+// (rows ty*TM/2 + i and BM/2 + ty*TM/2 + i, likewise for columns) so that
+// its shared-memory reads are 16-byte vectors and a warp reads few banks.
+//
+// The arithmetic is a policy P:
+//   GA, GB   operand element types in global memory
+//   SA, SB   their types in shared memory and registers; P::ldA(A, lda, i, k,
+//            M, K, prm) and P::ldB(B, ldb, k, j, K, N, prm) fetch one element
+//            (zero outside the matrix) and convert it
+//   Acc      accumulator, P::mac(acc, a, b) adds one term
+//   GC       result element type, P::finish(acc, sum, prm) produces it
+//   kBlocked when true, P::extract(acc) is called every prm.kbw steps of k
+//            and its results are summed in a 32-bit register per entry; the
+//            accumulator restarts from zero after each block.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace gfp {
+
+// Read n contiguous elements of shared memory into registers with the widest
+// vector loads the run allows (the run starts on a 16-byte boundary when its
+// byte length is a multiple of 16, see the padding of the tiles).
+template <class T, int n>
+__device__ __forceinline__ void lds_run(T *r, const T *p) {
+    constexpr int bytes = n * (int)sizeof(T);
+    if constexpr (bytes % 16 == 0) {
+#pragma unroll
+        for (int v = 0; v < bytes / 16; ++v) {
+            uint4 x = reinterpret_cast<const uint4 *>(p)[v];
+            uint32_t w[4] = {x.x, x.y, x.z, x.w};
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) r[v * 4 + q] = __builtin_bit_cast(T, w[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    r[v * 2 + q] = __builtin_bit_cast(T, (uint64_t)w[2 * q] | ((uint64_t)w[2 * q + 1] << 32));
+            }
+        }
+    } else if constexpr (bytes % 8 == 0 && sizeof(T) <= 8) {
+#pragma unroll
+        for (int v = 0; v < bytes / 8; ++v) {
+            uint2 x = reinterpret_cast<const uint2 *>(p)[v];
+            if constexpr (sizeof(T) == 4) {
+                r[v * 2] = __builtin_bit_cast(T, x.x);
+                r[v * 2 + 1] = __builtin_bit_cast(T, x.y);
+            } else {
+                r[v] = __builtin_bit_cast(T, (uint64_t)x.x | ((uint64_t)x.y << 32));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < n; ++q) r[q] = p[q];
+    }
+}
+
+template <class P, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
+                 const typename P::GB *__restrict__ B, int64_t ldb,
+                 typename P::GC *__restrict__ C, int64_t ldc,
+                 int64_t M, int64_t N, int64_t K, typename P::Params prm) {
+    constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
+    constexpr int HM = TM / 2, HN = TN / 2;
+    static_assert(TM % 2 == 0 && TN % 2 == 0, "rows and columns come in two halves");
+    static_assert((BM * BK) % NT == 0 && (BK * BN) % NT == 0, "tile loads");
+    using SA = typename P::SA;
+    using SB = typename P::SB;
+    using Acc = typename P::Acc;
+    constexpr int PADA = 16 / sizeof(SA), PADB = 0;   // keeps rows 16-byte aligned
+    __shared__ __align__(16) SA As[2][BK][BM + PADA];
+    __shared__ __align__(16) SB Bs[2][BK][BN + PADB];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % NTX, ty = tid / NTX;
+    const int64_t m0 = (int64_t)blockIdx.y * BM;
+    const int64_t n0 = (int64_t)blockIdx.x * BN;
+
+    constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
+    SA ra[LA];
+    SB rb[LB];
+
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int e = 0; e < LA; ++e) {
+            const int idx = tid + e * NT;
+            const int r = idx / BK, c = idx % BK;
+            const int64_t gi = m0 + r, gk = k0 + c;
+            ra[e] = P::ldA(A, lda, gi, gk, M, K, prm);
+        }
+#pragma unroll
+        for (int e = 0; e < LB; ++e) {
+            const int idx = tid + e * NT;
+            const int r = idx / BN, c = idx % BN;
+            const int64_t gk = k0 + r, gj = n0 + c;
+            rb[e] = P::ldB(B, ldb, gk, gj, K, N, prm);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int e = 0; e < LA; ++e) {
+            const int idx = tid + e * NT;
+            As[buf][idx % BK][idx / BK] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < LB; ++e) {
+            const int idx = tid + e * NT;
+            Bs[buf][idx / BN][idx % BN] = rb[e];
+        }
+    };
+
+    Acc acc[TM][TN];
+    uint32_t sum[P::kBlocked ? TM : 1][P::kBlocked ? TN : 1];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
+    if constexpr (P::kBlocked) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) sum[i][j] = 0;
+    }
+    int64_t countdown = P::kBlocked ? prm.kbw : 0;
+
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+        const bool more = k0 + BK < K;
+        if (more) load(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            SA a[TM];
+            SB b[TN];
+            lds_run<SA, HM>(a, &As[buf][kk][ty * HM]);
+            lds_run<SA, HM>(a + HM, &As[buf][kk][BM / 2 + ty * HM]);
+            lds_run<SB, HN>(b, &Bs[buf][kk][tx * HN]);
+            lds_run<SB, HN>(b + HN, &Bs[buf][kk][BN / 2 + tx * HN]);
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) P::mac(acc[i][j], a[i], b[j]);
+            if constexpr (P::kBlocked) {
+                if (--countdown == 0) {
+                    countdown = prm.kbw;
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) {
+                            sum[i][j] += P::extract(acc[i][j], prm);
+                            acc[i][j] = Acc(0);
+                        }
+                }
+            }
+        }
+        if (more) {
+            store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t gi = m0 + (i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM));
+        if (gi >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t gj = n0 + (j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN));
+            if (gj < N) {
+                uint32_t s = 0;
+                if constexpr (P::kBlocked) s = sum[i][j];
+                C[gi * ldc + gj] = P::finish(acc[i][j], s, prm);
+            }
+        }
+    }
+}
+
+template <class P, int BM, int BN, int BK, int TM, int TN>
+cudaError_t simt_gemm_launch(const typename P::GA *A, int64_t lda, const typename P::GB *B,
+                             int64_t ldb, typename P::GC *C, int64_t ldc, int64_t M, int64_t N,
+                             int64_t K, const typename P::Params &prm, cudaStream_t s) {
+    constexpr int NT = (BM / TM) * (BN / TN);
+    const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
+    if (gx <= 0 || gy <= 0) return cudaSuccess;
+    if (gy > 65535 || gx > 2147483647) return cudaErrorInvalidConfiguration;
+    simt_gemm_kernel<P, BM, BN, BK, TM, TN>
+        <<<dim3((unsigned)gx, (unsigned)gy), NT, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, prm);
+    return cudaGetLastError();
+}
+
+// Default element fetch: a guarded load converted to the shared-memory type.
+template <class G, class S>
+__device__ __forceinline__ S ld_guarded(const G *X, int64_t ld, int64_t r, int64_t c, int64_t R,
+                                        int64_t Cn) {
+    return (r < R && c < Cn) ? (S)X[r * ld + c] : S(0);
+}
+
+// a mod p for 32-bit a (Lemire, Kaser, Kurz 2019), M = floor((2^64-1)/p) + 1.
+__device__ __forceinline__ uint32_t fastmod_u32(uint32_t a, uint64_t M, uint32_t p) {
+    return (uint32_t)__umul64hi(M * (uint64_t)a, (uint64_t)p);
+}
+
+}  // namespace gfp

@@ -1,0 +1,273 @@
+"""Python binding of libgfp (include/gfp.h): argument marshalling only.
+
+Every function here takes torch tensors, passes their device pointers, sizes
+and leading dimensions (and the current CUDA stream) to the C-ABI function of
+the same name, and raises GfpError on a non-zero status.  All arithmetic runs
+in the library's CUDA kernels; there is no other code path.  If libgfp.so has
+not been built, the first call raises a RuntimeError naming the build command.
+
+Packed words are returned in tensors of the word's width: torch.int64 for the
+64-bit integer words (the bits of the uint64 word), torch.int32 for the
+32-bit ones and torch.float64 for FP64 words.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgfp.so")
+_lib = None
+
+STATUS = {0: "GFP_OK", 1: "GFP_EINVAL", 2: "GFP_EPRIME", 3: "GFP_EBOUND", 4: "GFP_EQ",
+          5: "GFP_EUNSUPPORTED", 6: "GFP_ECUDA", 7: "GFP_EWORKSPACE"}
+FORMS = {"dot": 0, "mixed": 1}
+WORDS = {"u64": 0, "u64x128": 1, "u32w": 2, "u32": 3, "f64": 4}
+LAYOUTS = {"rows_rev": 0, "cols": 1, "rows": 2}
+ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4}
+WORD_DTYPE = {"u64": torch.int64, "u64x128": torch.int64, "u32w": torch.int32, "u32": torch.int32,
+              "f64": torch.float64}
+
+# Exported names, as declared in include/gfp.h.
+EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_params", "gfp_pack",
+           "gfp_unpack", "gfp_gemm_workspace_size", "gfp_gemm", "gfp_gemm_compressed",
+           "gfp_batched_workspace_size", "gfp_gemm_batched", "gfp_batched_prepare",
+           "gfp_batched_launch")
+
+
+class GfpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        msg = "%s failed: %s" % (where, name)
+        if status == 6 and _lib is not None:
+            msg += " (cudaError %d)" % _lib.gfp_last_cuda_error()
+        super().__init__(msg)
+
+
+class Problem(ctypes.Structure):
+    """struct gfp_problem."""
+    _fields_ = [("p", ctypes.c_uint32), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("n", ctypes.c_int32), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("lda", ctypes.c_int32), ("ldb", ctypes.c_int32),
+                ("ldc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libgfp.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("libgfp.so is not built (%s); run `python -m paper_0803_1975_gb300.build` "
+                           "or __graft_entry__.build()" % _LIB_PATH)
+    L = ctypes.CDLL(_LIB_PATH)
+    i64, u32, u64, vp, ip = ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+    st = ctypes.c_int
+    L.gfp_status_string.argtypes = [st]
+    L.gfp_status_string.restype = ctypes.c_char_p
+    L.gfp_last_cuda_error.argtypes = []
+    L.gfp_last_cuda_error.restype = ip
+    L.gfp_word_bytes.argtypes = [ip]
+    L.gfp_word_bytes.restype = ctypes.c_size_t
+    L.gfp_params.argtypes = [u32, i64, i64, i64, ip, ip, ctypes.POINTER(ip), ctypes.POINTER(u64),
+                             ctypes.POINTER(i64)]
+    L.gfp_params.restype = st
+    L.gfp_pack.argtypes = [u32, i64, i64, vp, i64, ip, u64, ip, ip, vp, i64, vp]
+    L.gfp_pack.restype = st
+    L.gfp_unpack.argtypes = [u32, i64, i64, vp, i64, ip, u64, ip, ip, vp, i64, vp]
+    L.gfp_unpack.restype = st
+    L.gfp_gemm_workspace_size.argtypes = [u32, i64, i64, i64, ip, ctypes.POINTER(ctypes.c_size_t)]
+    L.gfp_gemm_workspace_size.restype = st
+    L.gfp_gemm.argtypes = [u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, ip, vp, ctypes.c_size_t, vp]
+    L.gfp_gemm.restype = st
+    L.gfp_gemm_compressed.argtypes = [u32, i64, i64, i64, ip, u64, ip, ip, vp, i64, vp, i64, vp, i64,
+                                      i64, vp]
+    L.gfp_gemm_compressed.restype = st
+    L.gfp_batched_workspace_size.argtypes = [i64, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
+    L.gfp_batched_workspace_size.restype = st
+    for name in ("gfp_gemm_batched", "gfp_batched_prepare"):
+        f = getattr(L, name)
+        f.argtypes = [i64, ctypes.POINTER(Problem), ip, ctypes.POINTER(st), vp, ctypes.c_size_t, vp]
+        f.restype = st
+    L.gfp_batched_launch.argtypes = [vp, ctypes.c_size_t, vp]
+    L.gfp_batched_launch.restype = st
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise GfpError(status, where)
+
+
+def _stream(t: torch.Tensor | None = None, stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    dev = t.device if t is not None else None
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _mat(t: torch.Tensor, dtype, name: str):
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+        raise ValueError("%s must be a 2-D CUDA tensor with unit column stride" % name)
+    return ctypes.c_void_p(t.data_ptr()), max(t.stride(0), t.shape[1], 1)
+
+
+def cdiv(a: int, b: int) -> int:
+    return -(-a // b)
+
+
+# ----------------------------------------------------------------------------
+def gfp_params(p: int, m: int, k: int, n: int, form: str = "dot", word: str = "u64",
+               d: int | None = None, Q: int | None = None, kb: int = 0):
+    """Choose (d is None) or validate (d, Q, kb).  Returns (d, Q, kb)."""
+    L = load()
+    dd = ctypes.c_int(-1 if d is None else d)
+    QQ = ctypes.c_uint64(0 if Q is None else Q)
+    kk = ctypes.c_int64(kb)
+    _check(L.gfp_params(p, m, k, n, FORMS[form], WORDS[word], ctypes.byref(dd), ctypes.byref(QQ),
+                        ctypes.byref(kk)), "gfp_params")
+    return dd.value, QQ.value, kk.value
+
+
+def packed_shape(layout: str, rows: int, cols: int, d: int):
+    if layout == "cols":
+        return cdiv(rows, d + 1), cols
+    return rows, cdiv(cols, d + 1)
+
+
+def gfp_pack(p: int, X: torch.Tensor, d: int, Q: int, layout: str, word: str = "u64",
+             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    L = load()
+    rows, cols = X.shape
+    wr, wc = packed_shape(layout, rows, cols, d)
+    if out is None:
+        out = torch.empty((wr, wc), dtype=WORD_DTYPE[word], device=X.device)
+    xp, ldx = _mat(X, torch.uint8, "X")
+    wp, ldw = _mat(out, WORD_DTYPE[word], "W")
+    _check(L.gfp_pack(p, rows, cols, xp, ldx, d, Q, LAYOUTS[layout], WORDS[word], wp, ldw,
+                      _stream(X, stream)), "gfp_pack")
+    return out
+
+
+def gfp_unpack(p: int, W: torch.Tensor, rows: int, cols: int, d: int, Q: int, layout: str,
+               word: str = "u64", out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    L = load()
+    if out is None:
+        out = torch.empty((rows, cols), dtype=torch.uint8, device=W.device)
+    wp, ldw = _mat(W, WORD_DTYPE[word], "W")
+    xp, ldx = _mat(out, torch.uint8, "X")
+    _check(L.gfp_unpack(p, rows, cols, wp, ldw, d, Q, LAYOUTS[layout], WORDS[word], xp, ldx,
+                        _stream(W, stream)), "gfp_unpack")
+    return out
+
+
+def gfp_gemm_workspace_size(p: int, m: int, k: int, n: int, algo: str = "auto") -> int:
+    L = load()
+    b = ctypes.c_size_t(0)
+    _check(L.gfp_gemm_workspace_size(p, m, k, n, ALGOS[algo], ctypes.byref(b)),
+           "gfp_gemm_workspace_size")
+    return b.value
+
+
+def gfp_gemm(p: int, A: torch.Tensor, B: torch.Tensor, algo: str = "auto",
+             out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    L = load()
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.uint8, device=A.device)
+    need = gfp_gemm_workspace_size(p, m, k, n, algo)
+    if need and workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=A.device)
+    ap, lda = _mat(A, torch.uint8, "A")
+    bp, ldb = _mat(B, torch.uint8, "B")
+    cp, ldc = _mat(out, torch.uint8, "C")
+    ws = ctypes.c_void_p(workspace.data_ptr() if workspace is not None else 0)
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(L.gfp_gemm(p, m, k, n, ap, lda, bp, ldb, cp, ldc, ALGOS[algo], ws, wsb,
+                      _stream(A, stream)), "gfp_gemm")
+    return out
+
+
+def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: str, word: str,
+                        CA_or_A: torch.Tensor, CB: torch.Tensor, out: torch.Tensor | None = None,
+                        kb: int = 0, stream=None) -> torch.Tensor:
+    """form 'dot': CA (ROWS_REV words) x CB (COLS words) -> uint8 C (m x n).
+    form 'mixed': uint8 A x CB (ROWS words) -> CC words (m x ceil(n/(d+1)))."""
+    L = load()
+    wdt = WORD_DTYPE[word]
+    if form == "dot":
+        ap, lda = _mat(CA_or_A, wdt, "CA")
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.uint8, device=CB.device)
+        cp, ldc = _mat(out, torch.uint8, "C")
+    else:
+        ap, lda = _mat(CA_or_A, torch.uint8, "A")
+        if out is None:
+            out = torch.empty((m, cdiv(n, d + 1)), dtype=wdt, device=CB.device)
+        cp, ldc = _mat(out, wdt, "CC")
+    bp, ldb = _mat(CB, wdt, "CB")
+    _check(L.gfp_gemm_compressed(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
+                                 ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
+    return out
+
+
+def make_problems(items) -> ctypes.Array:
+    """items: iterable of (p, A, B, C) CUDA uint8 tensors -> gfp_problem array."""
+    items = list(items)
+    arr = (Problem * max(len(items), 1))()
+    for i, (p, A, B, C) in enumerate(items):
+        m, k = A.shape
+        n = B.shape[1]
+        arr[i] = Problem(p, m, k, n, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                         max(A.stride(0), 1), max(B.stride(0), 1), max(C.stride(0), 1), 0)
+    return arr, len(items)
+
+
+def gfp_batched_workspace_size(probs, count: int) -> int:
+    L = load()
+    b = ctypes.c_size_t(0)
+    _check(L.gfp_batched_workspace_size(count, probs, ctypes.byref(b)), "gfp_batched_workspace_size")
+    return b.value
+
+
+def gfp_gemm_batched(probs, count: int, algo: str = "auto", workspace: torch.Tensor | None = None,
+                     device=None, stream=None, statuses: bool = False):
+    """probs/count from make_problems().  Returns the workspace (and the
+    per-problem statuses when asked)."""
+    L = load()
+    need = gfp_batched_workspace_size(probs, count)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=device or "cuda")
+    st = (ctypes.c_int * max(count, 1))()
+    r = L.gfp_gemm_batched(count, probs, ALGOS[algo], st, ctypes.c_void_p(workspace.data_ptr()),
+                           workspace.numel(), _stream(workspace, stream))
+    if statuses:
+        return workspace, r, list(st[:count])
+    _check(r, "gfp_gemm_batched")
+    return workspace
+
+
+def gfp_batched_prepare(probs, count: int, algo: str, workspace: torch.Tensor, stream=None):
+    L = load()
+    st = (ctypes.c_int * max(count, 1))()
+    _check(L.gfp_batched_prepare(count, probs, ALGOS[algo], st, ctypes.c_void_p(workspace.data_ptr()),
+                                 workspace.numel(), _stream(workspace, stream)), "gfp_batched_prepare")
+
+
+def gfp_batched_launch(workspace: torch.Tensor, stream=None):
+    L = load()
+    _check(L.gfp_batched_launch(ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                _stream(workspace, stream)), "gfp_batched_launch")

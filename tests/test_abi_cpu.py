@@ -1,0 +1,142 @@
+"""Host-side tests of the C ABI (no GPU): the library loads, exports every
+function include/gfp.h declares, and its parameter logic agrees with the
+oracle's reading of the paper's bounds.  Calls that fail validation launch
+nothing, so they are safe without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0803_1975_gb300 import build as gbuild
+from paper_0803_1975_gb300 import gfp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    gbuild.build()
+    return gfp.load()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"GFP_API\s+[\w\s\*]+?\b(gfp_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(gfp.EXPORTS) <= set(names)
+
+
+def test_status_strings(L):
+    for s in range(8):
+        assert L.gfp_status_string(s)
+    assert L.gfp_word_bytes(0) == 8 and L.gfp_word_bytes(3) == 4 and L.gfp_word_bytes(9) == 0
+
+
+@pytest.mark.parametrize("form,words", [("dot", oracle.WORDS_DOT), ("mixed", oracle.WORDS_MIXED)])
+def test_chooser_matches_oracle(L, form, words):
+    for word in words:
+        for p in (2, 3, 5, 7, 31, 251):
+            for k in (1, 2, 17, 256, 1000, 1024, 8192, 16384):
+                ref = oracle.choose(form, word, p, k)
+                d, Q, kb = gfp.gfp_params(p, 8, k, 8, form, word)
+                assert ref == (d, Q), (form, word, p, k)
+                assert kb == 0
+
+
+@pytest.mark.parametrize("word", ["u64", "u32", "u32w", "f64", "u64x128"])
+def test_blocked_chooser_matches_oracle(L, word):
+    for p, k, kb in ((3, 1024, 60), (5, 16384, 511), (3, 8192, 255), (7, 4096, 100)):
+        d, Q, kbr = gfp.gfp_params(p, 8, k, 8, "dot", word, kb=kb)
+        ref = oracle.choose("dot", word, p, k, kb=kbr)
+        assert (d, Q) == ref
+        assert kbr % (d + 1) == 0 and 0 < kbr <= kb
+        assert oracle.word_admissible("dot", word, p, k, d, Q, kb=kbr)
+
+
+def test_validator_matches_oracle_sweep(L):
+    """Every (form, word, p, k, d, t) in a sweep: gfp_params accepts exactly
+    what the oracle admits."""
+    for form, words in (("dot", oracle.WORDS_DOT), ("mixed", oracle.WORDS_MIXED)):
+        for word in words:
+            for p in (2, 3, 5, 31):
+                for k in (1, 7, 255, 256, 2047, 2048):
+                    for t in (4, 8, 10, 11, 13, 16, 20, 26):
+                        for d in (0, 1, 2, 3, 4, 5, 7):
+                            ok = oracle.word_admissible(form, word, p, k, d, 2 ** t)
+                            try:
+                                gfp.gfp_params(p, 4, k, 4, form, word, d=d, Q=2 ** t)
+                                got = True
+                            except gfp.GfpError as e:
+                                assert e.status == 3, (form, word, p, k, d, t, e)
+                                got = False
+                            assert got == ok, (form, word, p, k, d, t)
+
+
+def test_rejections(L):
+    def status(**kw):
+        args = dict(p=3, m=4, k=1024, n=4, form="dot", word="u64", d=3, Q=2 ** 13, kb=0)
+        args.update(kw)
+        try:
+            gfp.gfp_params(args["p"], args["m"], args["k"], args["n"], args["form"], args["word"],
+                           d=args["d"], Q=args["Q"], kb=args["kb"])
+            return 0
+        except gfp.GfpError as e:
+            return e.status
+    assert status() == 0
+    assert status(p=4) == 2 and status(p=1) == 2 and status(p=257) == 2 and status(p=253) == 2
+    assert status(Q=3 * 2 ** 12) == 4
+    assert status(k=2048) == 3                   # k (p-1)^2 = Q: the strict bound
+    assert status(d=4) == 3                      # t(d+1) = 65 > 64
+    assert status(word="u64x128", d=4) == 0      # ... allowed with 128-bit sums
+    assert status(word="f64", d=4, Q=2 ** 10, k=255) == 0    # Q^5 = 2^50
+    assert status(word="f64", d=5, Q=2 ** 10, k=255) == 3    # Q^6 = 2^60
+    assert status(m=-1) == 1
+    assert status(form="mixed", word="u32") == 5
+    assert status(kb=102) == 1                   # kb not a multiple of d+1
+    assert status(kb=102, d=3, Q=2 ** 8, word="u32") == 1
+    assert status(kb=60, d=3, Q=2 ** 8, word="u32") == 0
+    assert status(kb=64, d=3, Q=2 ** 8, word="u32") == 3     # 64 * 4 = Q
+
+
+def test_invalid_calls_launch_nothing(L):
+    """Host validation rejects these before any CUDA call (no GPU needed)."""
+    null = ctypes.c_void_p(0)
+    # p not prime
+    assert L.gfp_pack(4, 2, 2, null, 2, 1, 16, 0, 0, null, 1, null) == 2
+    # null pointers with non-empty shapes
+    assert L.gfp_pack(3, 2, 2, null, 2, 1, 16, 0, 0, null, 1, null) == 1
+    # bad layout
+    assert L.gfp_pack(3, 2, 2, null, 2, 1, 16, 7, 0, null, 1, null) == 1
+    # word too small for the packed value
+    assert L.gfp_pack(3, 2, 64, null, 64, 7, 2 ** 13, 0, 3, null, 8, null) == 3
+    # ld too small
+    a = ctypes.c_void_p(0x1000)
+    assert L.gfp_gemm(3, 4, 4, 4, a, 3, a, 4, a, 4, 1, null, 0, null) == 1
+    # plain product whose 32-bit sums would overflow: k (p-1)^2 >= 2^32
+    assert L.gfp_gemm(251, 4, 70000, 4, a, 70000, a, 4, a, 4, 1, null, 0, null) == 3
+    # tensor-core product without its workspace
+    assert L.gfp_gemm(3, 64, 64, 64, a, 64, a, 64, a, 64, 3, null, 0, null) == 7
+    # compressed product outside the bounds
+    assert L.gfp_gemm_compressed(3, 4, 2048, 4, 3, 2 ** 13, 0, 0, a, 512, a, 4, a, 4, 0, null) == 3
+    # empty shapes are valid and launch nothing
+    assert L.gfp_gemm(3, 0, 4, 4, null, 4, null, 4, null, 4, 1, null, 0, null) == 0
+    assert L.gfp_gemm_compressed(3, 0, 4, 4, 1, 2 ** 5, 0, 0, null, 2, null, 4, null, 4, 0, null) == 0
+
+
+def test_workspace_sizes(L):
+    assert gfp.gfp_gemm_workspace_size(3, 256, 256, 256, "plain") == 0
+    ws = gfp.gfp_gemm_workspace_size(3, 100, 70, 200, "tc_mma_s8")
+    assert ws >= (128 + 256) * 128

@@ -1,0 +1,225 @@
+"""GPU parity: every form through the C ABI against the CPU oracle, bit for
+bit, on seeded inputs.  Sizes span several tiles and ragged tails; adversarial
+inputs (all p-1, k at the bound) and edge shapes are included."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0803_1975_gb300 import gfp, inputs
+
+from helpers import (dev, ensure_built, freivalds, host, np_words_dtype, operands, oracle_product,
+                     to_word_tensor, words_np)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+# --------------------------------------------------------------------------- pack
+PACK_CASES = [(3, 1024, 1024, 3, 13), (3, 37, 129, 3, 13), (5, 130, 67, 2, 19), (251, 9, 300, 1, 30),
+              (2, 64, 64, 7, 8), (7, 1, 1, 0, 6)]
+
+
+@pytest.mark.parametrize("word", ["u64", "u32w", "f64"])
+@pytest.mark.parametrize("p,rows,cols,d,t", PACK_CASES)
+@pytest.mark.parametrize("layout", ["rows_rev", "cols", "rows"])
+def test_pack_unpack(word, p, rows, cols, d, t, layout):
+    Q = 2 ** t
+    try:
+        gfp.gfp_params(p, 1, 1, 1, "dot", "u64", d=d, Q=Q)   # (lower) with k = 1
+    except gfp.GfpError:
+        pytest.skip("not a valid (p, Q)")
+    big = 53 if word == "f64" else (32 if word == "u32w" else 64)
+    if oracle.amax(p, Q, d) >= 2 ** big:
+        with pytest.raises(gfp.GfpError):
+            gfp.gfp_pack(p, dev(np.zeros((rows, cols), np.uint8)), d, Q, layout, word)
+        return
+    g = inputs.rng(80, rows + cols + d)
+    X = inputs.residues(g, p, rows, cols)
+    W = gfp.gfp_pack(p, dev(X), d, Q, layout, word)
+    dt = np_words_dtype(word)
+    ref = {"rows_rev": oracle.pack_rows_rev, "cols": oracle.pack_cols,
+           "rows": oracle.pack_rows}[layout](X, d, Q, dtype=np.uint64)
+    got = words_np(W, word)
+    assert got.shape == ref.shape
+    assert (got.astype(np.uint64) == ref).all() if dt is not np.float64 else (got == ref.astype(np.float64)).all()
+    back = gfp.gfp_unpack(p, W, rows, cols, d, Q, layout, word)
+    assert (host(back) == X).all()
+
+
+def test_pack_strided_views():
+    """Leading dimensions larger than the row: pack a sub-matrix view."""
+    g = inputs.rng(81, 0)
+    X = inputs.residues(g, 3, 40, 100)
+    Xd = dev(X)[:, 3:90]
+    W = torch.zeros((40, 50), dtype=torch.int64, device="cuda")
+    gfp.gfp_pack(3, Xd, 3, 2 ** 13, "rows_rev", "u64", out=W[:, :22])
+    ref = oracle.pack_rows_rev(np.ascontiguousarray(X[:, 3:90]), 3, 2 ** 13)
+    got = words_np(W, "u64")
+    assert (got[:, :22] == ref).all() and (got[:, 22:] == 0).all()
+
+
+# ------------------------------------------------------------------ plain / TC
+GEMM_CASES = [(3, 256, 256, 256), (3, 1024, 1024, 1024), (5, 129, 300, 77), (251, 200, 513, 130),
+              (2, 65, 64, 63), (7, 1, 1, 1), (31, 3, 1000, 5), (13, 128, 17, 128), (3, 300, 1, 299)]
+
+
+@pytest.mark.parametrize("algo", ["plain", "dp4a", "tc_mma_s8"])
+@pytest.mark.parametrize("p,m,k,n", GEMM_CASES)
+def test_gemm_matches_oracle(algo, p, m, k, n):
+    A, B = operands(2, 0, p, m, k, n)
+    C = host(gfp.gfp_gemm(p, dev(A), dev(B), algo))
+    assert (C == oracle_product(2, 0, p, m, k, n)).all()
+
+
+@pytest.mark.parametrize("algo", ["plain", "dp4a", "tc_mma_s8"])
+@pytest.mark.parametrize("p", [3, 31, 251])
+def test_gemm_worst_case(algo, p):
+    """All entries p-1 (largest sums); for the centred form also the largest
+    centred magnitude h = (p-1)/2 with both signs."""
+    m = k = n = 192
+    h = (p - 1) // 2
+    for fill_a, fill_b in ((p - 1, p - 1), (h, h), (h + 1, h), (h + 1, h + 1)):
+        A = np.full((m, k), fill_a, np.uint8)
+        B = np.full((k, n), fill_b, np.uint8)
+        C = host(gfp.gfp_gemm(p, dev(A), dev(B), algo))
+        assert (C == oracle.gemm(p, A, B)).all()
+
+
+@pytest.mark.parametrize("algo", ["plain", "dp4a", "tc_mma_s8"])
+def test_gemm_edges(algo):
+    # empty inner dimension: C = 0
+    C = torch.full((5, 7), 9, dtype=torch.uint8, device="cuda")
+    gfp.gfp_gemm(3, torch.zeros((5, 0), dtype=torch.uint8, device="cuda"),
+                 torch.zeros((0, 7), dtype=torch.uint8, device="cuda"), algo, out=C)
+    assert (host(C) == 0).all()
+    # strided views in and out
+    A, B = operands(3, 1, 5, 70, 90, 60)
+    Ad = dev(np.pad(A, ((0, 0), (0, 10))))[:, :90]
+    Bd = dev(np.pad(B, ((0, 0), (0, 4))))[:, :60]
+    Cd = torch.full((70, 64), 200, dtype=torch.uint8, device="cuda")
+    gfp.gfp_gemm(5, Ad, Bd, algo, out=Cd[:, :60])
+    got = host(Cd)
+    assert (got[:, :60] == oracle.gemm(5, A, B)).all() and (got[:, 60:] == 200).all()
+
+
+def test_tc_kblock_reduction():
+    """k beyond one int32 k-block for p = 251 (kb = 68672): the blocked
+    reduction path, checked on sampled rows."""
+    p, m, k, n = 251, 128, 70000, 128
+    g = inputs.rng(33, 0)
+    A = inputs.residues(g, p, m, k)
+    B = inputs.residues(g, p, k, n)
+    C = host(gfp.gfp_gemm(p, dev(A), dev(B), "tc_mma_s8"))
+    rows = [0, 1, 63, 64, 127]
+    assert (C[rows] == oracle.gemm_rows(p, rows, A, B, threads=8)).all()
+
+
+# --------------------------------------------------------------- compressed dot
+DOT_CASES = [(3, 1024, 1024, 1024), (3, 100, 333, 70), (5, 64, 1000, 200), (31, 40, 8, 50),
+             (2, 129, 257, 65), (251, 33, 40, 33)]
+
+
+@pytest.mark.parametrize("word", ["u64", "u64x128", "u32w", "u32", "f64"])
+@pytest.mark.parametrize("p,m,k,n", DOT_CASES)
+def test_dot_matches_oracle(word, p, m, k, n):
+    """Procedure (2) of Section 2.2: CompressRows(A), CompressColumns(B), CA x CB."""
+    try:
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "dot", word)
+    except gfp.GfpError:
+        pytest.skip("no admissible (d, Q)")
+    A, B = operands(2, 1, p, m, k, n)
+    CA = gfp.gfp_pack(p, dev(A), d, Q, "rows_rev", word)
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "cols", word)
+    C = host(gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", word, CA, CB))
+    assert (C == oracle_product(2, 1, p, m, k, n)).all()
+
+
+@pytest.mark.parametrize("word", ["u64", "u64x128", "u32w", "u32", "f64"])
+def test_dot_at_the_bound(word):
+    """All entries p-1 at the largest k of eq. (lower) for the chosen Q."""
+    p = 3
+    d, Q, _ = gfp.gfp_params(p, 64, 1024, 64, "dot", word)
+    k = (Q - 1) // 4
+    d, Q2, _ = gfp.gfp_params(p, 64, k, 64, "dot", word, d=d, Q=Q)
+    A = np.full((70, k), 2, np.uint8)
+    B = np.full((k, 66), 2, np.uint8)
+    CA = gfp.gfp_pack(p, dev(A), d, Q, "rows_rev", word)
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "cols", word)
+    C = host(gfp.gfp_gemm_compressed(p, 70, k, 66, d, Q, "dot", word, CA, CB))
+    assert (C == (k * 4) % 3).all()
+
+
+def test_dot_f64_round_toward_zero_case():
+    """The case where round-to-nearest FP64 accumulation loses the digit
+    (p = 3, Q = 2^10, d = 4, k = 255, all entries 2) is exact here."""
+    p, d, Q, k = 3, 4, 2 ** 10, 255
+    A = np.full((33, k), 2, np.uint8)
+    B = np.full((k, 35), 2, np.uint8)
+    assert oracle.dqt_dot_fp64(A[0], B[:, 0], p, d, Q, "rn") != (k * 4) % 3
+    CA = gfp.gfp_pack(p, dev(A), d, Q, "rows_rev", "f64")
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "cols", "f64")
+    C = host(gfp.gfp_gemm_compressed(p, 33, k, 35, d, Q, "dot", "f64", CA, CB))
+    assert (C == (k * 4) % 3).all()
+
+
+@pytest.mark.parametrize("word", ["u64", "u64x128", "u32w", "u32", "f64"])
+@pytest.mark.parametrize("p,k,kb", [(3, 1024, 60), (5, 1000, 48), (3, 777, 28), (7, 500, 10)])
+def test_dot_blocked(word, p, k, kb):
+    """k-blocked extraction: the lower bound holds for kb only."""
+    m, n = 96, 80
+    d, Q, kbr = gfp.gfp_params(p, m, k, n, "dot", word, kb=kb)
+    A, B = operands(4, kb, p, m, k, n)
+    CA = gfp.gfp_pack(p, dev(A), d, Q, "rows_rev", word)
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "cols", word)
+    C = host(gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", word, CA, CB, kb=kbr))
+    assert (C == oracle.gemm(p, A, B)).all()
+    # worst case within each block
+    A = np.full((m, k), p - 1, np.uint8)
+    B = np.full((k, n), p - 1, np.uint8)
+    CA = gfp.gfp_pack(p, dev(A), d, Q, "rows_rev", word)
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "cols", word)
+    C = host(gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", word, CA, CB, kb=kbr))
+    assert (C == (k * (p - 1) ** 2) % p).all()
+
+
+# ------------------------------------------------------------------------ mixed
+MIXED_CASES = [(3, 1024, 1024, 1024), (3, 77, 300, 101), (5, 64, 200, 64), (251, 20, 30, 41),
+               (2, 65, 129, 67)]
+
+
+@pytest.mark.parametrize("word", ["u64", "f64"])
+@pytest.mark.parametrize("p,m,k,n", MIXED_CASES)
+def test_mixed_matches_oracle(word, p, m, k, n):
+    """Equation (LeftComp) of Section 3: A x CB then REDQ; CC holds the
+    residues of A B packed along rows, its unpacking is A B mod p."""
+    d, Q, _ = gfp.gfp_params(p, m, k, n, "mixed", word)
+    A, B = operands(2, 2, p, m, k, n)
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "rows", word)
+    CC = gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "mixed", word, dev(A), CB)
+    ref = oracle_product(2, 2, p, m, k, n)
+    got = words_np(CC, word)
+    want = oracle.pack_rows(ref, d, Q, dtype=np.uint64)
+    if word == "f64":
+        assert (got == want.astype(np.float64)).all()
+    else:
+        assert (got == want).all()
+    C = host(gfp.gfp_unpack(p, CC, m, n, d, Q, "rows", word))
+    assert (C == ref).all()
+
+
+@pytest.mark.parametrize("word", ["u64", "f64"])
+def test_mixed_worst_case(word):
+    p = 3
+    k = 2047
+    d, Q, _ = gfp.gfp_params(p, 8, k, 8, "mixed", word)
+    A = np.full((40, k), 2, np.uint8)
+    B = np.full((k, 50), 2, np.uint8)
+    CB = gfp.gfp_pack(p, dev(B), d, Q, "rows", word)
+    CC = gfp.gfp_gemm_compressed(p, 40, k, 50, d, Q, "mixed", word, dev(A), CB)
+    C = host(gfp.gfp_unpack(p, CC, 40, 50, d, Q, "rows", word))
+    assert (C == (k * 4) % 3).all()
