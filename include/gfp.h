@@ -117,8 +117,11 @@ typedef enum gfp_layout {
  *  GFP_ALGO_TC_F16     : centred residues as fp16 on tcgen05 (kind::f16)
  *                        with fp32 accumulation, which is exact while every
  *                        partial sum is an integer of magnitude < 2^24: the
- *                        k-block is the largest kb with kb ((p-1)/2)^2 < 2^24
- *                        (rounded down to a multiple of 64).
+ *                        k-block is the largest kb with kb ((p-1)/2)^2 + p
+ *                        < 2^24 (rounded down to a multiple of 64).  After the
+ *                        call's kernels complete, the first 4 bytes of its
+ *                        workspace hold the kernel's status: 0, or non-zero if
+ *                        a bounded internal wait gave up (C is then invalid).
  *  GFP_ALGO_AUTO       : the fastest of the above for (p, m, k, n). */
 typedef enum gfp_algo {
     GFP_ALGO_AUTO = 0,

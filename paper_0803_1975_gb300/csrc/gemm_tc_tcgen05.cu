@@ -1,21 +1,544 @@
-// Exact C = A B mod p on the tcgen05 tensor cores (kind::f16): placeholder
-// until the kernel lands; reports GFP_EUNSUPPORTED.
+// Exact C = A B mod p on the 5th-generation tensor cores (tcgen05.mma,
+// kind::f16, fp32 accumulation in tensor memory).  No counterpart in the
+// paper; it is the tensor-core analogue of its delayed reduction (Section 2.4):
+// many products are accumulated before a single reduction mod p.
+//
+// Exactness.  Residues are centred, c = r - p [r > (p-1)/2], |c| <= h =
+// (p-1)/2 (p = 2 keeps 0/1), and held in fp16, where every integer of
+// magnitude <= 2048 is exact.  Each product is an integer of magnitude <= h^2
+// and every partial sum of a k-block of kb terms is an integer of magnitude
+// <= kb h^2 < 2^24, so it is representable in fp32 and no rounding occurs in
+// any order of summation.  kb is the largest multiple of 64 with
+// kb h^2 + p < 2^24: the whole k for p <= 31 at k = 8192, 1024 for p = 251.
+// After each k-block the accumulator is reduced to [0, p) and added to a
+// running residue held in registers (4 residues per 32-bit register).
+//
+// Kernel.  Persistent, one CTA per SM, 192 threads:
+//   warp 0    : TMA producer (one thread) -- A tile 128 x 64 and B tile
+//               256 x 64 fp16 per stage, 128-byte swizzle, 4 stages;
+//   warp 1    : tensor memory allocator and MMA issuer (one thread) --
+//               4 x tcgen05.mma 128 x 256 x 16 per stage into one of two
+//               256-column fp32 accumulators;
+//   warps 2-5 : epilogue -- tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32 (w % 4) .. +31), reduction mod p, uint8 stores.
+// A unit of work is one k-block of one 128 x 256 output tile; units alternate
+// between the two accumulators so the epilogue of one overlaps the MMAs of
+// the next.  Every mbarrier wait is bounded (globaltimer): on expiry the
+// kernel records an error in the status word, stops issuing, waits (bounded)
+// for its own copies and MMAs in flight, frees tensor memory and returns.
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
 #include "gfp_internal.h"
 
 namespace gfp {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;             // BK fp16 = 128 bytes
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;         // 48 KB, multiple of 1024
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;                    // 2 x 256 fp32 columns
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;   // 4 s
+
+// status codes written to the status word
+constexpr int ST_TIMEOUT_PRODUCER = 1, ST_TIMEOUT_MMA = 2, ST_TIMEOUT_EPI = 3, ST_TIMEOUT_DRAIN = 4;
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase of `parity` completed; false on abort
+// (another role gave up) or on expiry (this role gives up and says so).
+__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag,
+                                       int *status, int code) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            const uint64_t now = globaltimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > WAIT_LIMIT_NS) {
+                *abort_flag = 1;
+                if (status) atomicCAS(status, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of tcgen05: K-major operand in the 128-byte
+// swizzled layout (8-row atoms of 1024 bytes): start address >> 4 in bits
+// 0-13, leading byte offset (unused for this layout, 16 B) in 16-29, stride
+// byte offset (1024 B between 8-row groups) >> 4 in 32-45, version 1 in 46,
+// swizzle mode 2 (128 B) in 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: fp32 accumulator (bits 4-5 = 1), fp16 A
+// and B (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t fastmod(uint32_t a, uint64_t M, uint32_t p) {
+    return (uint32_t)__umul64hi(M * (uint64_t)a, (uint64_t)p);
+}
+
+struct TcArgs {
+    uint8_t *C;
+    int64_t ldc, m, n;
+    int tiles_m, tiles_n;
+    int ktiles;        // k in BK slices
+    int kb_tiles;      // k-block in BK slices
+    int kblocks;       // ceil(ktiles / kb_tiles)
+    uint32_t p, off;   // off = p ceil(2^24 / p): makes |x| < 2^24 non-negative
+    uint64_t M;        // fastmod magic of p
+    int *status;
+};
+
+// Tile order: groups of 8 tile-rows walk the tile-columns together, so the
+// B tiles a group shares stay in L2.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
+    const int G = 8;
+    const int group = t / (G * tiles_n);
+    const int first_m = group * G;
+    const int gsize = min(G, tiles_m - first_m);
+    const int r = t % (G * tiles_n);
+    tm = first_m + r % gsize;
+    tn = r / gsize;
+}
+
+template <bool BLOCKED>
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              TcArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;     // 1024-aligned for the swizzle atoms
+    uint8_t *gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 5));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = g.tiles_m * g.tiles_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 4);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        const uint32_t slot = (uint32_t)__cvta_generic_to_shared(tmem_slot);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_parity[STAGES];
+            bool issued[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = false;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
+                for (int kt = 0; kt < g.ktiles; ++kt) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+                    mbar_expect_tx(full_bar(stage), STAGE_BYTES);
+                    tma_load_2d(sa, &tmA, kt * BK, tm * BM, full_bar(stage));
+                    tma_load_2d(sb, &tmB, kt * BK, tn * BN, full_bar(stage));
+                    issued[stage] = true;
+                    issued_parity[stage] = phase;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued[s]) {
+                        uint64_t t0 = globaltimer();
+                        while (!mbar_try(full_bar(s), issued_parity[s]) &&
+                               globaltimer() - t0 < WAIT_LIMIT_NS) {
+                        }
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t unit = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                for (int j = 0; j < g.kblocks && ok; ++j, ++unit) {
+                    const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
+                    if (!mbar_wait(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t d = tmem + buf * 256u;
+                    const int k0 = j * g.kb_tiles;
+                    const int k1 = min(g.ktiles, k0 + g.kb_tiles);
+                    for (int kt = k0; kt < k1; ++kt) {
+                        if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_f16(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
+                                    (kt > k0 || kk > 0) ? 1u : 0u);
+                        mma_commit(empty_bar(stage));
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                    if (ok) mma_commit(accf_bar(buf));
+                }
+            }
+            // all MMAs issued by this thread complete before tensor memory is freed
+            mma_commit(drain_bar);
+            uint64_t t0 = globaltimer();
+            while (!mbar_try(drain_bar, 0)) {
+                if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                    if (g.status) atomicCAS(g.status, 0, ST_TIMEOUT_DRAIN);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: 4 warps, TMEM lanes 32 (warp % 4) .. +31
+        const int q = warp & 3;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        uint32_t unit = 0;
+        bool ok = true;
+        uint32_t run[BLOCKED ? 64 : 1];
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            int tm, tn;
+            tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
+            const int64_t row = (int64_t)tm * BM + q * 32 + lane;
+            const int64_t col0 = (int64_t)tn * BN;
+            if constexpr (BLOCKED) {
+#pragma unroll
+                for (int i = 0; i < 64; ++i) run[i] = 0;
+            }
+            for (int j = 0; j < g.kblocks; ++j, ++unit) {
+                const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
+                // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
+                int got = 0;
+                if (lane == 0) got = mbar_wait(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const bool last = (j == g.kblocks - 1);
+#pragma unroll
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_addr + buf * 256u + c * 32, v);
+                    uint32_t w[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        uint32_t packed = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int x = __float2int_rn(__uint_as_float(v[e * 4 + b]));
+                            uint32_t r = fastmod((uint32_t)x + g.off, g.M, g.p);
+                            if constexpr (BLOCKED) {
+                                r += (run[c * 8 + e] >> (8 * b)) & 0xffu;
+                                r = r >= g.p ? r - g.p : r;
+                            }
+                            packed |= r << (8 * b);
+                        }
+                        w[e] = packed;
+                        if constexpr (BLOCKED) run[c * 8 + e] = packed;
+                    }
+                    if (last && row < g.m) {
+                        const int64_t col = col0 + c * 32;
+                        uint8_t *dst = g.C + row * g.ldc + col;
+                        if (col + 32 <= g.n && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+                            reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        } else {
+                            for (int e = 0; e < 32; ++e)
+                                if (col + e < g.n) dst[e] = (uint8_t)(w[e >> 2] >> (8 * (e & 3)));
+                        }
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(buf));
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- preprocess: centred fp16 operands, zero padded to the tile multiples
+__global__ void to_f16_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m, int64_t k,
+                                   __half *__restrict__ out, int64_t kp, int64_t mp, uint32_t p,
+                                   uint32_t h) {
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+    if (l >= kp) return;
+    for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
+        __align__(16) __half v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            int c = 0;
+            if (i < m && l + e < k) {
+                const uint32_t r = A[i * lda + l + e];
+                c = (int)r - (r > h ? (int)p : 0);
+            }
+            v[e] = __int2half_rn(c);
+        }
+        *reinterpret_cast<uint4 *>(out + i * kp + l) = *reinterpret_cast<uint4 *>(v);
+    }
+}
+
+__global__ void to_f16_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k,
+                                        int64_t n, __half *__restrict__ out, int64_t kp, int64_t np,
+                                        uint32_t p, uint32_t h) {
+    __shared__ int8_t tile[64][64 + 4];
+    const int64_t l0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
+    for (int r = ty; r < 64; r += 4) {
+        const int64_t l = l0 + r, j = j0 + tx;
+        int c = 0;
+        if (l < k && j < n) {
+            const uint32_t v = B[l * ldb + j];
+            c = (int)v - (v > h ? (int)p : 0);
+        }
+        tile[r][tx] = (int8_t)c;
+    }
+    __syncthreads();
+    for (int r = ty; r < 64; r += 4) {
+        const int64_t j = j0 + r, l = l0 + tx;
+        if (j < np && l < kp) out[j * kp + l] = __int2half_rn((int)tile[tx][r]);
+    }
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const __half *base, int64_t rows, int64_t kp, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
 
 int64_t tc_kblock_f32(uint32_t p) {
     const int64_t h = p == 2 ? 1 : (p - 1) / 2;
-    int64_t kb = ((int64_t(1) << 24) - 1 - p) / (h * h);
-    return kb / 64 * 64;
+    const int64_t kb = ((int64_t(1) << 24) - 1 - p) / (h * h);
+    return kb / BK * BK;
 }
 
-size_t tc_f16_workspace(int64_t, int64_t, int64_t) { return 0; }
+// workspace: [status word, 256 B][A16: mp x kp fp16][B16: np x kp fp16]
+size_t tc_f16_workspace(int64_t m, int64_t k, int64_t n) {
+    const int64_t kp = round_up(k > 0 ? k : 1, BK);
+    return 256 + (size_t)(round_up(m, BM) + round_up(n, BN)) * (size_t)kp * 2;
+}
 
-gfp_status launch_tc_f16(uint32_t, int64_t, int64_t, int64_t, const uint8_t *, int64_t,
-                         const uint8_t *, int64_t, uint8_t *, int64_t, void *, size_t,
-                         cudaStream_t) {
-    return GFP_EUNSUPPORTED;
+gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
+                         const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,
+                         size_t ws_bytes, cudaStream_t s) {
+    const int64_t kp = round_up(k, BK), mp = round_up(m, BM), np = round_up(n, BN);
+    if (tc_f16_workspace(m, k, n) > ws_bytes) return GFP_EWORKSPACE;
+    if (mp / BM > (int64_t)1 << 30 || np / BN > (int64_t)1 << 30 || kp / BK > (int64_t)1 << 30)
+        return GFP_EINVAL;
+    int *status = static_cast<int *>(ws);
+    __half *A16 = reinterpret_cast<__half *>(static_cast<uint8_t *>(ws) + 256);
+    __half *B16 = A16 + mp * kp;
+    const uint32_t h = p == 2 ? 1u : (p - 1) / 2;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    {
+        dim3 grid((unsigned)((kp / 8 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
+        to_f16_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, A16, kp, mp, p, h);
+        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64));
+        to_f16_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, B16, kp, np, p, h);
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A16, mp, kp, BM) || !make_map(&mb, B16, np, kp, BN)) return GFP_EUNSUPPORTED;
+    TcArgs g;
+    g.C = C;
+    g.ldc = ldc;
+    g.m = m;
+    g.n = n;
+    g.tiles_m = (int)(mp / BM);
+    g.tiles_n = (int)(np / BN);
+    g.ktiles = (int)(kp / BK);
+    g.kb_tiles = (int)(tc_kblock_f32(p) / BK);
+    g.kblocks = (g.ktiles + g.kb_tiles - 1) / g.kb_tiles;
+    g.p = p;
+    g.off = (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);
+    g.M = fastmod_magic(p);
+    g.status = status;
+    const int tiles = g.tiles_m * g.tiles_n;
+    const int grid = tiles < num_sms() ? tiles : num_sms();
+    if (g.kblocks > 1) {
+        static bool set = false;
+        if (!set) {
+            cudaFuncSetAttribute(tc_f16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+            set = true;
+        }
+        tc_f16_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, g);
+    } else {
+        static bool set = false;
+        if (!set) {
+            cudaFuncSetAttribute(tc_f16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+            set = true;
+        }
+        tc_f16_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, g);
+    }
+    return check_launch();
 }
 
 }  // namespace gfp

@@ -68,7 +68,10 @@ GEMM_CASES = [(3, 256, 256, 256), (3, 1024, 1024, 1024), (5, 129, 300, 77), (251
               (2, 65, 64, 63), (7, 1, 1, 1), (31, 3, 1000, 5), (13, 128, 17, 128), (3, 300, 1, 299)]
 
 
-@pytest.mark.parametrize("algo", ["plain", "dp4a", "tc_mma_s8"])
+ALGOS = ["plain", "dp4a", "tc_mma_s8", "tc_f16"]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("p,m,k,n", GEMM_CASES)
 def test_gemm_matches_oracle(algo, p, m, k, n):
     A, B = operands(2, 0, p, m, k, n)
@@ -76,7 +79,7 @@ def test_gemm_matches_oracle(algo, p, m, k, n):
     assert (C == oracle_product(2, 0, p, m, k, n)).all()
 
 
-@pytest.mark.parametrize("algo", ["plain", "dp4a", "tc_mma_s8"])
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("p", [3, 31, 251])
 def test_gemm_worst_case(algo, p):
     """All entries p-1 (largest sums); for the centred form also the largest
@@ -90,7 +93,7 @@ def test_gemm_worst_case(algo, p):
         assert (C == oracle.gemm(p, A, B)).all()
 
 
-@pytest.mark.parametrize("algo", ["plain", "dp4a", "tc_mma_s8"])
+@pytest.mark.parametrize("algo", ALGOS)
 def test_gemm_edges(algo):
     # empty inner dimension: C = 0
     C = torch.full((5, 7), 9, dtype=torch.uint8, device="cuda")
@@ -105,6 +108,54 @@ def test_gemm_edges(algo):
     gfp.gfp_gemm(5, Ad, Bd, algo, out=Cd[:, :60])
     got = host(Cd)
     assert (got[:, :60] == oracle.gemm(5, A, B)).all() and (got[:, 60:] == 200).all()
+
+
+def tc_f16_status(ws: torch.Tensor) -> int:
+    torch.cuda.synchronize()
+    return int(ws[:4].cpu().numpy().view(np.int32)[0])
+
+
+@pytest.mark.parametrize("p", [3, 31, 251])
+def test_tc_f16_exact_accumulation(p):
+    """fp32 accumulation in tensor memory is exact while partial sums are
+    integers below 2^24.  Patterns at the k-block bound kb: all products +h^2
+    (partial sums reach kb h^2), alternating signs, a large accumulator
+    followed by small addends, and one k-block past the bound (blocked path)."""
+    h = (p - 1) // 2
+    kb = ((1 << 24) - 1 - p) // (h * h) // 64 * 64
+    k = min(kb, 80000)                        # p = 31: 74560, p = 251: 1024
+    m, n = 128, 256
+    pos, neg = h, h + 1                       # residues whose centred values are +h, -h
+    pats = {
+        "all+": (np.full((m, k), pos, np.uint8), np.full((k, n), pos, np.uint8)),
+        "all-+": (np.full((m, k), neg, np.uint8), np.full((k, n), pos, np.uint8)),
+        "alt": (np.full((m, k), pos, np.uint8),
+                np.where((np.arange(k) % 2)[:, None] == 0, pos, neg).astype(np.uint8).repeat(n, 1)),
+    }
+    big_then_small = np.full((m, k), pos, np.uint8)
+    big_then_small[:, k // 2:] = 1
+    pats["big-then-small"] = (big_then_small, np.full((k, n), pos, np.uint8))
+    for name, (A, B) in pats.items():
+        ws = torch.empty(gfp.gfp_gemm_workspace_size(p, m, k, n, "tc_f16"), dtype=torch.uint8,
+                         device="cuda")
+        C = host(gfp.gfp_gemm(p, dev(A), dev(B), "tc_f16", workspace=ws))
+        assert tc_f16_status(ws) == 0
+        assert (C == oracle.gemm(p, A[:2], B)[0]).all(), name   # rows are identical
+
+
+def test_tc_f16_blocked_path():
+    """p = 251 beyond one fp32 k-block (kb = 1024): running residues across
+    k-blocks, random and worst-case inputs."""
+    p, m, k, n = 251, 200, 3 * 1024 + 64 + 17, 300
+    A, B = operands(5, 0, p, m, k, n)
+    ws = torch.empty(gfp.gfp_gemm_workspace_size(p, m, k, n, "tc_f16"), dtype=torch.uint8, device="cuda")
+    C = host(gfp.gfp_gemm(p, dev(A), dev(B), "tc_f16", workspace=ws))
+    assert tc_f16_status(ws) == 0
+    assert (C == oracle.gemm(p, A, B, threads=8)).all()
+    A = np.full((m, k), 126, np.uint8)        # centred -125
+    B = np.full((k, n), 125, np.uint8)        # centred +125
+    C = host(gfp.gfp_gemm(p, dev(A), dev(B), "tc_f16", workspace=ws))
+    assert (C == oracle.gemm(p, A[:1], B)[0]).all()
 
 
 def test_tc_kblock_reduction():
