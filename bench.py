@@ -1,0 +1,476 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact GF(p) product, one JSON line on stdout.
+
+Workload: p = 3, m = k = n = 1024, residues i.i.d. uniform in [0, p) (seeded,
+synthetic: the paper has no dataset).  One step runs every stage of the hot
+path once on that input:
+
+  parameters (host)            gfp_params for every form
+  Q-adic dot form, u64 words   gfp_pack(A, rows reversed), gfp_pack(B, columns),
+                               gfp_gemm_compressed(dot, u64)
+  Q-adic dot form, FP64 words  the same with binary64 words (round-toward-zero)
+  right-compressed form, u64   gfp_pack(B, rows), gfp_gemm_compressed(mixed)
+                               with REDQ, gfp_unpack(CC)
+  classical product            gfp_gemm(plain)
+  exact tensor-core forms      gfp_gemm(tc_f16), gfp_gemm(tc_mma_s8)
+
+value = (products per step x 2mnk) / step time (every product is the full
+C = A B mod p).  Each step is timed alone with CUDA events; a 256 MiB buffer
+is written between steps so that no step starts with its inputs in L2.
+`forms` gives each form (and each machine word) timed on its own, `batched`
+the grouped launch over 4096 adjacency squares, `roofline` the dominant
+kernel of the step against its pipe's peak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfp|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P, M, K, N = 3, 1024, 1024, 1024
+FLOP = 2.0 * M * N * K
+METRIC = "GF(p) GEMM effective 2mnk/s (bit-exact) per form vs plain GPU; % of roofline"
+UNIT = "T(2mnk)/s"
+WORKLOAD = "Q-adic compressed GEMM and all forms, p=3, m=k=n=1024, uniform residues"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "gfp_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU step
+# ---------------------------------------------------------------------------
+class Step:
+    """Every stage of the hot path on one (A, B); buffers allocated once."""
+
+    LAUNCHES = 16   # kernels of this library per step (counted below)
+
+    def __init__(self, gfp, torch, A, B):
+        self.gfp, self.torch = gfp, torch
+        self.A, self.B = A, B
+        dev = A.device
+        e = lambda *s, dt=torch.uint8: torch.empty(*s, dtype=dt, device=dev)
+        self.d64, self.Q64, _ = gfp.gfp_params(P, M, K, N, "dot", "u64")
+        self.df, self.Qf, _ = gfp.gfp_params(P, M, K, N, "dot", "f64")
+        self.dm, self.Qm, _ = gfp.gfp_params(P, M, K, N, "mixed", "u64")
+        kc64 = -(-K // (self.d64 + 1))
+        kcf = -(-K // (self.df + 1))
+        self.CA64 = e((M, kc64), dt=torch.int64)
+        self.CB64 = e((kc64, N), dt=torch.int64)
+        self.CAf = e((M, kcf), dt=torch.float64)
+        self.CBf = e((kcf, N), dt=torch.float64)
+        ncm = -(-N // (self.dm + 1))
+        self.CBr = e((K, ncm), dt=torch.int64)
+        self.CC = e((M, ncm), dt=torch.int64)
+        self.outs = {name: e((M, N)) for name in ("dot_u64", "dot_f64", "mixed_u64", "plain", "tc_f16",
+                                                  "tc_mma_s8")}
+        self.ws16 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_f16"))
+        self.ws8 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_mma_s8"))
+        self.dom = None   # (start, end) events around the dominant kernel
+
+    def run(self, dom_events=None):
+        g = self.gfp
+        # parameters (host)
+        d64, Q64, _ = g.gfp_params(P, M, K, N, "dot", "u64")
+        df, Qf, _ = g.gfp_params(P, M, K, N, "dot", "f64")
+        dm, Qm, _ = g.gfp_params(P, M, K, N, "mixed", "u64")
+        # dot form, u64 words: 3 launches
+        g.gfp_pack(P, self.A, d64, Q64, "rows_rev", "u64", out=self.CA64)
+        g.gfp_pack(P, self.B, d64, Q64, "cols", "u64", out=self.CB64)
+        g.gfp_gemm_compressed(P, M, K, N, d64, Q64, "dot", "u64", self.CA64, self.CB64, out=self.outs["dot_u64"])
+        # dot form, FP64 words: 3 launches (the product is the step's dominant kernel)
+        g.gfp_pack(P, self.A, df, Qf, "rows_rev", "f64", out=self.CAf)
+        g.gfp_pack(P, self.B, df, Qf, "cols", "f64", out=self.CBf)
+        if dom_events is not None:
+            dom_events[0].record()
+        g.gfp_gemm_compressed(P, M, K, N, df, Qf, "dot", "f64", self.CAf, self.CBf, out=self.outs["dot_f64"])
+        if dom_events is not None:
+            dom_events[1].record()
+        # right-compressed form with REDQ: 3 launches
+        g.gfp_pack(P, self.B, dm, Qm, "rows", "u64", out=self.CBr)
+        g.gfp_gemm_compressed(P, M, K, N, dm, Qm, "mixed", "u64", self.A, self.CBr, out=self.CC)
+        g.gfp_unpack(P, self.CC, M, N, dm, Qm, "rows", "u64", out=self.outs["mixed_u64"])
+        # classical product: 1 launch
+        g.gfp_gemm(P, self.A, self.B, "plain", out=self.outs["plain"])
+        # tensor-core forms: 3 + 3 launches (operand conversion, product)
+        g.gfp_gemm(P, self.A, self.B, "tc_f16", out=self.outs["tc_f16"], workspace=self.ws16)
+        g.gfp_gemm(P, self.A, self.B, "tc_mma_s8", out=self.outs["tc_mma_s8"], workspace=self.ws8)
+
+    @property
+    def products(self):
+        return len(self.outs)
+
+
+def event_time(torch, fn, reps, flush):
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def forms_breakdown(gfp, torch, A, B, flush, plain_ms):
+    """Each form and word timed on its own (median of 7, L2 flushed)."""
+    out = {}
+    dev = A.device
+
+    def rec(name, ms, **extra):
+        r = {"ms": round(ms, 5), "value": round(FLOP / ms / 1e9, 3), "speedup_vs_plain": round(plain_ms / ms, 3)}
+        r.update(extra)
+        out[name] = r
+
+    for algo in ("plain", "dp4a", "tc_mma_s8", "tc_f16"):
+        ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(P, M, K, N, algo)), dtype=torch.uint8, device=dev)
+        C = torch.empty((M, N), dtype=torch.uint8, device=dev)
+        rec(algo, event_time(torch, lambda: gfp.gfp_gemm(P, A, B, algo, out=C, workspace=ws), 7, flush))
+    for word, kb in (("u64", 0), ("u64x128", 0), ("u32w", 0), ("u32", 0), ("f64", 0), ("u32", 60),
+                     ("u32w", 140)):
+        d, Q, kbr = gfp.gfp_params(P, M, K, N, "dot", word, kb=kb)
+        CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", word)
+        CB = gfp.gfp_pack(P, B, d, Q, "cols", word)
+        C = torch.empty((M, N), dtype=torch.uint8, device=dev)
+        t_mm = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr), 7, flush)
+
+        def full():
+            gfp.gfp_pack(P, A, d, Q, "rows_rev", word, out=CA)
+            gfp.gfp_pack(P, B, d, Q, "cols", word, out=CB)
+            gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr)
+        t_full = event_time(torch, full, 7, flush)
+        name = "dot_%s" % word + ("_kb%d" % kbr if kbr else "")
+        rec(name, t_mm, d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr,
+            with_packing_ms=round(t_full, 5), with_packing_value=round(FLOP / t_full / 1e9, 3))
+    for word in ("u64", "f64"):
+        d, Q, _ = gfp.gfp_params(P, M, K, N, "mixed", word)
+        CB = gfp.gfp_pack(P, B, d, Q, "rows", word)
+        CC = torch.empty((M, -(-N // (d + 1))), dtype=gfp.WORD_DTYPE[word], device=dev)
+        rec("mixed_%s" % word, event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "mixed", word, A, CB, out=CC), 7, flush),
+            d_plus_1=d + 1, t=Q.bit_length() - 1)
+    # conversions: pack A reversed into u64 words, bytes moved per launch
+    d, Q, _ = gfp.gfp_params(P, M, K, N, "dot", "u64")
+    CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64")
+    t = event_time(torch, lambda: gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64", out=CA), 7, flush)
+    byts = M * K + CA.numel() * 8
+    out["pack_rows_rev_u64"] = {"ms": round(t, 5), "GB_per_s": round(byts / t / 1e6, 1), "bytes": byts}
+    return out
+
+
+def batched_measure(gfp, torch, flush):
+    """4096 squares of adjacency matrices in one grouped launch (CUDA graph)."""
+    from paper_0803_1975_gb300 import inputs
+    probs = inputs.batched_problems()
+    dev = torch.device("cuda")
+    items = []
+    flops = 0.0
+    for p, A in probs:
+        Ad = torch.from_numpy(A).to(dev)
+        n = A.shape[0]
+        items.append((p, Ad, Ad, torch.empty((n, n), dtype=torch.uint8, device=dev)))
+        flops += 2.0 * n ** 3
+    arr, cnt = gfp.make_problems(items)
+    need = gfp.gfp_batched_workspace_size(arr, cnt)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    gfp.gfp_batched_prepare(arr, cnt, "auto", ws)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        gfp.gfp_batched_launch(ws)      # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        gfp.gfp_batched_launch(ws)
+    ms = event_time(torch, graph.replay, 7, flush)
+    return {"problems": cnt, "sum_2n3": flops, "ms": round(ms, 4), "value": round(flops / ms / 1e9, 3),
+            "unit": UNIT, "launches_per_replay": 1}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(A, B, budget_s=10.0):
+    """The oracle (plain C triple loop over all host cores) on the same
+    product; repeated until about budget_s of CPU time."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    oracle.gemm(P, A, B, threads=cores)
+    one = time.time() - t0
+    reps = max(1, int(budget_s / max(one, 1e-3)) - 1)
+    reps = min(reps, 50)
+    t0 = time.time()
+    for _ in range(reps):
+        oracle.gemm(P, A, B, threads=cores)
+    per = (time.time() - t0) / reps
+    return FLOP / per / 1e12, cores, "%d full %dx%dx%d products (p=%d) after one untimed" % (reps, M, K, N, P), per
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle as it stands, timed on the host cores."""
+    if rank != 0:
+        return
+    from paper_0803_1975_gb300 import inputs
+    import oracle
+    oracle.build()
+    g = inputs.rng(2, 0)
+    A = inputs.residues(g, P, M, K)
+    B = inputs.residues(g, P, K, N)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.gemm(P, A, B, threads=cores)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        oracle.gemm(P, A, B, threads=cores)
+        ts.append(time.time() - t0)
+    per = float(np.sum(ts)) / args.steps
+    v = FLOP / per / 1e12
+    line = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "p": P, "m": M, "k": K, "n": N},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full %dx%dx%d product per step" % (M, K, N)},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfp", choices=["gfp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-form and batched breakdowns")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_0803_1975_gb300 import build as gbuild
+    from paper_0803_1975_gb300 import gfp, inputs
+
+    gbuild.build()
+    gfp.load()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # every rank runs its own replica of the workload (independent products)
+    g = inputs.rng(2, 0)
+    A_h = inputs.residues(g, P, M, K)
+    B_h = inputs.residues(g, P, K, N)
+    A = torch.from_numpy(A_h).cuda()
+    B = torch.from_numpy(B_h).cuda()
+    step = Step(gfp, torch, A, B)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        step.run()
+    torch.cuda.synchronize()
+
+    # correctness of the step's outputs (cheap check against one oracle product on rank 0)
+    import oracle
+    oracle.build()
+    ref = oracle.gemm(P, A_h, B_h, threads=os.cpu_count() or 1)
+    for name, C in step.outs.items():
+        if not (C.cpu().numpy() == ref).all():
+            raise SystemExit("bench: %s result differs from the oracle" % name)
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    step_ms, dom_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step.run(dom_events=(d0, d1))
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        dom_ms.append(d0.elapsed_time(d1))
+    barrier()
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * step.products * FLOP / ms_per_step / 1e9
+
+    # end to end: pinned host inputs -> device -> all forms -> results to pinned host memory
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    B_pin = torch.from_numpy(B_h).pin_memory()
+    outs_pin = {k: torch.empty((M, N), dtype=torch.uint8).pin_memory() for k in step.outs}
+    barrier()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        A.copy_(A_pin, non_blocking=True)
+        B.copy_(B_pin, non_blocking=True)
+        step.run()
+        for k_, C in step.outs.items():
+            outs_pin[k_].copy_(C, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_per = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_per], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_per = float(t.item())
+    for k_, C in outs_pin.items():
+        if not (C.numpy() == ref).all():
+            raise SystemExit("bench: end-to-end %s result differs from the oracle" % k_)
+
+    # roofline of the dominant kernel: the FP64 dot product (DFMA pipe)
+    kcf = -(-K // (step.df + 1))
+    dfma = M * N * kcf
+    dom_avg = float(np.mean(dom_ms))
+    achieved = 2.0 * dfma / dom_avg / 1e9            # TFLOP/s (FP64, 2 per fused multiply-add)
+    fp64_peak = 1.25                                   # nominal FP64 of GB300 (TFLOP/s)
+    roofline = {"kernel": "simt_gemm_kernel<DotF64> (dot form, FP64 words)", "bound": "alu",
+                "achieved": round(achieved, 4), "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": round(achieved / fp64_peak, 4), "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "traffic": None, "launch_ms": round(dom_avg, 5),
+                "algorithmic_flops_per_launch": 2 * dfma,
+                "share_of_step": round(dom_avg / (float(np.mean(step_ms))), 3)}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        plain_ms = event_time(torch, lambda: gfp.gfp_gemm(P, A, B, "plain", out=step.outs["plain"]), 7, flush)
+        extras["forms"] = forms_breakdown(gfp, torch, A, B, flush, plain_ms)
+        try:
+            extras["batched"] = batched_measure(gfp, torch, flush)
+        except gfp.GfpError as e:
+            extras["batched"] = {"unavailable": str(e)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _ = cpu_oracle_rate(A_h, B_h)
+        cpu = {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        peaks = measured_peaks()
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/u32/u64/f64/f16",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "p": P, "m": M, "k": K, "n": N,
+                           "products_per_step": step.products,
+                           "l2": "256 MiB buffer written between timed steps (flush)",
+                           "replicas": world},
+                "e2e": {"value": round(world * step.products * FLOP / e2e_per / 1e9, 3), "unit": UNIT,
+                        "ms_per_step": round(e2e_per, 5),
+                        "h2d_bytes_per_step": 2 * M * K, "d2h_bytes_per_step": step.products * M * N},
+                "gpu_launches": Step.LAUNCHES * args.steps,
+                "roofline": roofline,
+                "clocks": clk,
+                "cpu_baseline": cpu,
+                "measured_peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

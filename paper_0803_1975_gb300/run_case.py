@@ -1,0 +1,78 @@
+"""Run one form of C = A B mod p on seeded uniform residues and report its
+time (CUDA events, L2 flushed between repetitions) and effective 2mnk/s.
+
+    python -m paper_0803_1975_gb300.run_case --form tc_f16 --p 3 --size 8192 --reps 3
+    python -m paper_0803_1975_gb300.run_case --form dot --word u32 --kb 60 --size 1024
+
+Forms: plain, dp4a, tc_mma_s8, tc_f16 (gfp_gemm); dot, mixed
+(gfp_gemm_compressed, after packing).  Useful for profiling one kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import gfp, inputs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--form", default="tc_f16")
+    ap.add_argument("--word", default="u64")
+    ap.add_argument("--kb", type=int, default=0)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--m", type=int, default=0)
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=1)
+    a = ap.parse_args()
+    m = a.m or a.size
+    k = a.k or a.size
+    n = a.n or a.size
+    p = a.p
+    g = inputs.rng(3, p)
+    A = torch.from_numpy(inputs.residues(g, p, m, k)).cuda()
+    B = torch.from_numpy(inputs.residues(g, p, k, n)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if a.form in ("plain", "dp4a", "tc_mma_s8", "tc_f16"):
+        ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(p, m, k, n, a.form)), dtype=torch.uint8,
+                         device="cuda")
+        C = torch.empty((m, n), dtype=torch.uint8, device="cuda")
+        fn = lambda: gfp.gfp_gemm(p, A, B, a.form, out=C, workspace=ws)
+    elif a.form == "dot":
+        d, Q, kb = gfp.gfp_params(p, m, k, n, "dot", a.word, kb=a.kb)
+        CA = gfp.gfp_pack(p, A, d, Q, "rows_rev", a.word)
+        CB = gfp.gfp_pack(p, B, d, Q, "cols", a.word)
+        C = torch.empty((m, n), dtype=torch.uint8, device="cuda")
+        fn = lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", a.word, CA, CB, out=C, kb=kb)
+    elif a.form == "mixed":
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "mixed", a.word)
+        CB = gfp.gfp_pack(p, B, d, Q, "rows", a.word)
+        C = torch.empty((m, -(-n // (d + 1))), dtype=gfp.WORD_DTYPE[a.word], device="cuda")
+        fn = lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "mixed", a.word, A, CB, out=C)
+    else:
+        raise SystemExit("unknown form %s" % a.form)
+    for _ in range(a.warmup):
+        fn()
+    ts = []
+    for _ in range(a.reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    print(json.dumps({"form": a.form, "word": a.word, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
+                      "T_2mnk_per_s": round(2.0 * m * n * k / ms / 1e9, 3)}))
+
+
+if __name__ == "__main__":
+    main()
