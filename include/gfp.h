@@ -128,7 +128,8 @@ typedef enum gfp_algo {
     GFP_ALGO_PLAIN = 1,
     GFP_ALGO_DP4A = 2,
     GFP_ALGO_TC_MMA_S8 = 3,
-    GFP_ALGO_TC_F16 = 4
+    GFP_ALGO_TC_F16 = 4,
+    GFP_ALGO_DOT32 = 5      /* batched only: Q-adic dot form in 32-bit words */
 } gfp_algo;
 
 /* ------------------------------------------------------------------------ */
@@ -267,19 +268,31 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  * grouped launch (no counterpart in the paper; the workload is the
  * strongly-regular-graph computations of Section 1).
  *  probs       : HOST array of `count` problems; each is validated on the host.
- *  algo        : GFP_ALGO_AUTO (per-problem choice by the autotuned table),
- *                GFP_ALGO_PLAIN, GFP_ALGO_DP4A or GFP_ALGO_TC_MMA_S8.
+ *  algo        : GFP_ALGO_AUTO   -- per size bucket (the largest of m, k, n),
+ *                                   the tile kind gfp_batched_autotune chose;
+ *                                   untuned buckets use fp16 tensor-core tiles;
+ *                GFP_ALGO_TC_F16 -- warp-level fp16 tensor-core MMA tiles
+ *                                   (64 x 64, or 32 x 32 for m, n <= 48) on
+ *                                   centred residues, fp32 accumulation kept
+ *                                   exact by k-blocks (kb h^2 + p < 2^24);
+ *                GFP_ALGO_DOT32  -- the Q-adic dot form (Section 2) in 32-bit
+ *                                   words, residues packed while staged, with
+ *                                   (Q, d, k-block) chosen per problem.
  *  status      : optional HOST array of `count` per-problem statuses.  A
  *                problem that fails validation is skipped (its C untouched)
  *                and the call returns the first failing status after
  *                launching the valid ones.
- *  workspace   : device memory of gfp_batched_workspace_size bytes
- *                (256-byte aligned).  The call writes the tile schedule there
- *                with one host-to-device copy, then launches one kernel.
- * The call is split in two for CUDA graph capture: gfp_batched_prepare
- * writes the schedule (run it outside capture), gfp_batched_launch only
- * launches the kernel on the prepared workspace (capturable, replayable as
- * long as the workspace and the matrices stay in place). */
+ *  workspace   : device memory of gfp_batched_workspace_size bytes (256-byte
+ *                aligned).  It receives the schedule: problem table, tiles,
+ *                and each CTA's range of tiles, balanced on the host
+ *                (longest tile first onto the least loaded CTA).
+ * gfp_gemm_batched = gfp_batched_prepare + gfp_batched_launch.
+ * gfp_batched_prepare writes the schedule with one host-to-device copy and
+ * synchronizes `stream` (run it outside stream capture).  gfp_batched_launch
+ * launches the one grouped kernel that reads the prepared workspace; it
+ * allocates nothing and does not synchronize, so it can be captured in a CUDA
+ * graph and replayed while the workspace and matrices stay in place.  Both
+ * must run on the same device. */
 GFP_API gfp_status gfp_gemm_batched(int64_t count, const gfp_problem *probs, gfp_algo algo,
                                     gfp_status *status, void *workspace, size_t ws_bytes,
                                     void *stream);
@@ -289,6 +302,22 @@ GFP_API gfp_status gfp_batched_prepare(int64_t count, const gfp_problem *probs, 
                                        void *stream);
 
 GFP_API gfp_status gfp_batched_launch(void *workspace, size_t ws_bytes, void *stream);
+
+/* Autotuner of the batched launch: for each size bucket present in `probs`
+ * (largest of m, k, n in (0,32], (32,64], (64,128], (128,256], (256,512],
+ * (512,2048], above) it times one grouped launch of that bucket's problems
+ * with each tile kind (0 = fp16 MMA 64 x 64, 1 = fp16 MMA 32 x 32, 2 = Q-adic
+ * 32-bit words with per-problem Q and d) and keeps the fastest; the choice
+ * is stored in the library (used by GFP_ALGO_AUTO from then on, process
+ * wide) and, if `table` is not NULL, written to table[0 .. table_len) (-1 for
+ * buckets without problems).  It writes the problems' C matrices and uses
+ * `workspace` (gfp_batched_workspace_size bytes); it synchronizes `stream`. */
+GFP_API gfp_status gfp_batched_autotune(int64_t count, const gfp_problem *probs, void *workspace,
+                                        size_t ws_bytes, void *stream, int *table, int table_len);
+
+/* Install a tile-kind table (as written by gfp_batched_autotune, e.g. from a
+ * cache file); -1 entries fall back to the default.  Host only. */
+GFP_API gfp_status gfp_batched_set_table(const int *table, int table_len);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,8 @@ STATUS = {0: "GFP_OK", 1: "GFP_EINVAL", 2: "GFP_EPRIME", 3: "GFP_EBOUND", 4: "GF
 FORMS = {"dot": 0, "mixed": 1}
 WORDS = {"u64": 0, "u64x128": 1, "u32w": 2, "u32": 3, "f64": 4}
 LAYOUTS = {"rows_rev": 0, "cols": 1, "rows": 2}
-ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4}
+ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4, "dot32": 5}
+BATCHED_KINDS = {0: "hmma64", 1: "hmma32", 2: "dot32"}
 WORD_DTYPE = {"u64": torch.int64, "u64x128": torch.int64, "u32w": torch.int32, "u32": torch.int32,
               "f64": torch.float64}
 
@@ -33,7 +34,7 @@ WORD_DTYPE = {"u64": torch.int64, "u64x128": torch.int64, "u32w": torch.int32, "
 EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_params", "gfp_pack",
            "gfp_unpack", "gfp_gemm_workspace_size", "gfp_gemm", "gfp_gemm_compressed",
            "gfp_batched_workspace_size", "gfp_gemm_batched", "gfp_batched_prepare",
-           "gfp_batched_launch")
+           "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table")
 
 
 class GfpError(RuntimeError):
@@ -97,6 +98,11 @@ def load():
         f.restype = st
     L.gfp_batched_launch.argtypes = [vp, ctypes.c_size_t, vp]
     L.gfp_batched_launch.restype = st
+    L.gfp_batched_autotune.argtypes = [i64, ctypes.POINTER(Problem), vp, ctypes.c_size_t, vp,
+                                       ctypes.POINTER(ip), ip]
+    L.gfp_batched_autotune.restype = st
+    L.gfp_batched_set_table.argtypes = [ctypes.POINTER(ip), ip]
+    L.gfp_batched_set_table.restype = st
     _lib = L
     return L
 
@@ -271,3 +277,24 @@ def gfp_batched_launch(workspace: torch.Tensor, stream=None):
     L = load()
     _check(L.gfp_batched_launch(ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                 _stream(workspace, stream)), "gfp_batched_launch")
+
+
+def gfp_batched_autotune(probs, count: int, workspace: torch.Tensor | None = None, device=None,
+                         stream=None):
+    """Time each tile kind per size bucket on these problems; the library keeps
+    the fastest for GFP_ALGO_AUTO.  Returns the table (kind index or -1 per
+    bucket)."""
+    L = load()
+    if workspace is None:
+        workspace = torch.empty(max(gfp_batched_workspace_size(probs, count), 1), dtype=torch.uint8,
+                                device=device or "cuda")
+    table = (ctypes.c_int * 7)()
+    _check(L.gfp_batched_autotune(count, probs, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                  _stream(workspace, stream), table, 7), "gfp_batched_autotune")
+    return list(table)
+
+
+def gfp_batched_set_table(table):
+    L = load()
+    arr = (ctypes.c_int * len(table))(*table)
+    _check(L.gfp_batched_set_table(arr, len(table)), "gfp_batched_set_table")

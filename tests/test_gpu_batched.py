@@ -1,0 +1,139 @@
+"""GPU parity of the batched grouped launch: every tile kind, uneven and
+rectangular problems, invalid entries, CUDA-graph replay, the autotuner, and
+the 4096-problem adjacency workload (sampled problems against the oracle,
+Freivalds' check on every problem)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0803_1975_gb300 import gfp, inputs
+
+from helpers import dev, ensure_built, freivalds, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def random_batch(seed, count, primes=(2, 3, 5, 7, 31, 251), smax=300):
+    g = np.random.Generator(np.random.PCG64(seed))
+    items, host_ops = [], []
+    for _ in range(count):
+        p = int(g.choice(primes))
+        m, k, n = (int(x) for x in g.integers(1, smax, size=3))
+        A = inputs.residues(g, p, m, k)
+        B = inputs.residues(g, p, k, n)
+        items.append((p, dev(A), dev(B), torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A, B))
+    return items, host_ops
+
+
+@pytest.mark.parametrize("algo", ["tc_f16", "dot32", "auto"])
+def test_batched_rectangular_mixed_primes(algo):
+    items, host_ops = random_batch(11, 120)
+    arr, cnt = gfp.make_problems(items)
+    gfp.gfp_gemm_batched(arr, cnt, algo)
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all()
+
+
+def test_batched_worst_case_and_kblocks():
+    """All entries p-1, and k beyond one fp16 k-block for p = 251."""
+    items, refs = [], []
+    for p, m, k, n in ((251, 70, 2500, 90), (7, 64, 512, 64), (3, 33, 1000, 31), (251, 5, 1100, 7)):
+        A = np.full((m, k), p - 1, np.uint8)
+        B = np.full((k, n), p - 1, np.uint8)
+        items.append((p, dev(A), dev(B), torch.zeros((m, n), dtype=torch.uint8, device="cuda")))
+        refs.append(oracle.gemm(p, A[:1], B)[0])
+    for algo in ("tc_f16", "dot32"):
+        arr, cnt = gfp.make_problems(items)
+        gfp.gfp_gemm_batched(arr, cnt, algo)
+        for (p, A, B, C), ref in zip(items, refs):
+            assert (host(C) == ref).all(), (algo, p)
+
+
+def test_batched_invalid_entries_are_skipped():
+    items, host_ops = random_batch(12, 6)
+    arr, cnt = gfp.make_problems(items)
+    arr[2].p = 4                       # not prime
+    arr[4].lda = 0                     # ld too small
+    ws, r, st = gfp.gfp_gemm_batched(arr, cnt, "auto", statuses=True)
+    assert r == 2 and st[2] == 2 and st[4] == 1
+    for i, ((p, A, B), (_, _, _, C)) in enumerate(zip(host_ops, items)):
+        got = host(C)
+        if i in (2, 4):
+            assert (got == 255).all()
+        else:
+            assert (got == oracle.gemm(p, A, B)).all()
+
+
+def test_batched_empty_and_degenerate():
+    arr, cnt = gfp.make_problems([])
+    gfp.gfp_gemm_batched(arr, 0, "auto")
+    C = torch.full((3, 4), 9, dtype=torch.uint8, device="cuda")
+    Z = torch.zeros((3, 0), dtype=torch.uint8, device="cuda")
+    arr, cnt = gfp.make_problems([(5, Z, torch.zeros((0, 4), dtype=torch.uint8, device="cuda"), C)])
+    gfp.gfp_gemm_batched(arr, cnt, "tc_f16")
+    assert (host(C) == 0).all()
+
+
+def test_batched_graph_replay():
+    items, host_ops = random_batch(13, 40, smax=200)
+    arr, cnt = gfp.make_problems(items)
+    ws = torch.empty(gfp.gfp_batched_workspace_size(arr, cnt), dtype=torch.uint8, device="cuda")
+    gfp.gfp_batched_prepare(arr, cnt, "auto", ws)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        gfp.gfp_batched_launch(ws)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gfp.gfp_batched_launch(ws)
+    for rep in range(2):
+        for it in items:
+            it[3].fill_(255)
+        graph.replay()
+        torch.cuda.synchronize()
+        for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+            assert (host(C) == oracle.gemm(p, A, B)).all()
+
+
+def test_autotune_then_auto():
+    items, host_ops = random_batch(14, 60, primes=(3, 5, 7), smax=520)
+    arr, cnt = gfp.make_problems(items)
+    table = gfp.gfp_batched_autotune(arr, cnt)
+    assert len(table) == 7 and all(v in (-1, 0, 1, 2) for v in table) and any(v >= 0 for v in table)
+    for it in items:
+        it[3].fill_(255)
+    gfp.gfp_gemm_batched(arr, cnt, "auto")
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all()
+    gfp.gfp_batched_set_table([-1] * 7)
+
+
+def test_adjacency_workload_4096():
+    """The full batched workload: 4096 squares of symmetric 0/1 adjacency
+    matrices, n log-uniform in [16, 512], p in {3, 5, 7}.  Every product is
+    checked by Freivalds' test; 256 of them (and every one with n <= 40)
+    against the oracle entry by entry."""
+    probs = inputs.batched_problems()
+    items = []
+    for p, A in probs:
+        Ad = dev(A)
+        items.append((p, Ad, Ad, torch.empty(A.shape, dtype=torch.uint8, device="cuda")))
+    arr, cnt = gfp.make_problems(items)
+    gfp.gfp_gemm_batched(arr, cnt, "auto")
+    torch.cuda.synchronize()
+    g = np.random.Generator(np.random.PCG64(5))
+    sample = set(g.choice(len(probs), size=256, replace=False).tolist())
+    for i, ((p, A), it) in enumerate(zip(probs, items)):
+        C = it[3].cpu().numpy()
+        assert freivalds(p, A, A, C, rounds=4, seed=i)
+        if i in sample or A.shape[0] <= 40:
+            assert (C == oracle.gemm(p, A, A)).all(), i
