@@ -333,6 +333,7 @@ def main():
     import torch.distributed as dist
     from paper_0803_1975_gb300 import build as gbuild
     from paper_0803_1975_gb300 import gfp, inputs
+    from paper_0803_1975_gb300.dist import max_over_ranks
 
     gbuild.build()
     gfp.load()
@@ -384,11 +385,7 @@ def main():
         dom_ms.append(d0.elapsed_time(d1))
     barrier()
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), device="cuda")
     ms_per_step = total_ms / args.steps
     value = world * step.products * FLOP / ms_per_step / 1e9
 
@@ -412,11 +409,7 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     barrier()
-    e2e_per = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_per], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_per = float(t.item())
+    e2e_per = max_over_ranks(float(np.mean(e2e_ms)), device="cuda")
     for k_, C in outs_pin.items():
         if not (C.numpy() == ref).all():
             raise SystemExit("bench: end-to-end %s result differs from the oracle" % k_)

@@ -337,3 +337,20 @@ def test_blocked_reading():
 def test_compression_factor():
     for t in range(2, 54):
         assert oracle.compression_factor(2 ** t) == 53 // t
+
+
+def test_round53_against_binary64():
+    """The rounding emulation used by dqt_dot_fp64, against the host's own
+    binary64: float(int) rounds to nearest even; rounding toward zero gives a
+    representable value z <= x whose next representable value exceeds x."""
+    g = np.random.Generator(np.random.PCG64(3))
+    cases = [2 ** 53 + 1, 2 ** 53 + 3, 2 ** 60 + 2 ** 7, 2 ** 60 + 3 * 2 ** 6, 2 ** 106 - 1, 0, 1, 2 ** 53]
+    for _ in range(3000):
+        hi = int(g.integers(1, 2 ** 62))
+        cases.append((hi << int(g.integers(0, 60))) | int(g.integers(0, 2 ** 20)))
+    for x in cases:
+        assert oracle._round53(x, "rn") == int(float(x))
+        z = oracle._round53(x, "rz")
+        assert z <= x and int(float(z)) == z
+        nxt = z + 1 if z < 2 ** 53 else int(math.nextafter(float(z), math.inf))
+        assert nxt > x
