@@ -221,6 +221,31 @@ GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n,
                             gfp_algo algo, void *workspace, size_t ws_bytes,
                             void *stream);
 
+/* Size of the scratch buffer compiled into the library for gfp_gemm_noalloc. */
+#define GFP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* C = A B mod p exactly as gfp_gemm(..., GFP_ALGO_TC_MMA_S8, ...), for callers
+ * that cannot allocate device memory: a process with a fixed device-memory
+ * budget, a framework whose allocator owns every device allocation, or a
+ * latency-bound path where an allocation could synchronize the device.  They
+ * cannot supply gfp_gemm's workspace, so this call allocates nothing and
+ * takes no workspace; it uses a scratch array of GFP_NOALLOC_SCRATCH_BYTES
+ * that the library holds on every GPU that loads it, until the process exits.
+ * (No counterpart in the paper.)
+ *  Arguments as gfp_gemm.  The problem must fit the scratch:
+ *  (roundup(m, 128) + roundup(n, 128)) * roundup(k, 64) + 256 bytes <=
+ *  GFP_NOALLOC_SCRATCH_BYTES (e.g. m = n = k = 2048); larger problems are
+ *  rejected with GFP_EWORKSPACE before anything is launched.
+ *  The first call on a device, with that device current, looks up the
+ *  scratch's device address (one-time set-up); make that first call before
+ *  any stream capture.  Every call uses the same scratch, so calls whose
+ *  kernels overlap on the GPU (other streams, other host threads) race on it
+ *  and must be serialized by the caller.  Errors as gfp_gemm. */
+GFP_API gfp_status gfp_gemm_noalloc(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                    const uint8_t *A, int64_t lda,
+                                    const uint8_t *B, int64_t ldb,
+                                    uint8_t *C, int64_t ldc, void *stream);
+
 /* Compressed product.
  *  form = GFP_FORM_DOT (Section 2, procedure (2) after packing):
  *     CA_or_A : CA, m x ceil(k/(d+1)) words, layout ROWS_REV of A, lda words.

@@ -34,7 +34,8 @@ WORD_DTYPE = {"u64": torch.int64, "u64x128": torch.int64, "u32w": torch.int32, "
 EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_params", "gfp_pack",
            "gfp_unpack", "gfp_gemm_workspace_size", "gfp_gemm", "gfp_gemm_compressed",
            "gfp_batched_workspace_size", "gfp_gemm_batched", "gfp_batched_prepare",
-           "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table")
+           "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table",
+           "gfp_gemm_noalloc")
 
 
 class GfpError(RuntimeError):
@@ -90,6 +91,8 @@ def load():
     L.gfp_gemm_compressed.argtypes = [u32, i64, i64, i64, ip, u64, ip, ip, vp, i64, vp, i64, vp, i64,
                                       i64, vp]
     L.gfp_gemm_compressed.restype = st
+    L.gfp_gemm_noalloc.argtypes = [u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
+    L.gfp_gemm_noalloc.restype = st
     L.gfp_batched_workspace_size.argtypes = [i64, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
     L.gfp_batched_workspace_size.restype = st
     for name in ("gfp_gemm_batched", "gfp_batched_prepare"):
@@ -204,6 +207,24 @@ def gfp_gemm(p: int, A: torch.Tensor, B: torch.Tensor, algo: str = "auto",
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(L.gfp_gemm(p, m, k, n, ap, lda, bp, ldb, cp, ldc, ALGOS[algo], ws, wsb,
                       _stream(A, stream)), "gfp_gemm")
+    return out
+
+
+def gfp_gemm_noalloc(p: int, A: torch.Tensor, B: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """gfp_gemm(..., 'tc_mma_s8') without a workspace, for callers that may not
+    allocate device memory at call time (the output, if not given, is
+    allocated here by torch before the call)."""
+    L = load()
+    m, k = A.shape
+    n = B.shape[1]
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.uint8, device=A.device)
+    ap, lda = _mat(A, torch.uint8, "A")
+    bp, ldb = _mat(B, torch.uint8, "B")
+    cp, ldc = _mat(out, torch.uint8, "C")
+    _check(L.gfp_gemm_noalloc(p, m, k, n, ap, lda, bp, ldb, cp, ldc, _stream(A, stream)),
+           "gfp_gemm_noalloc")
     return out
 
 

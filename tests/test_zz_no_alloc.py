@@ -1,0 +1,53 @@
+"""The allocation-free entry point gfp_gemm_noalloc, for callers that cannot
+allocate device memory (fixed memory budget, an allocator-owning framework,
+latency-bound paths): called through the C ABI twice in a row, each time
+against gfp_gemm's int8 tensor-core form on the same inputs, bit for bit
+(the tolerance of every integer test here).  Kept in a file of its own that
+pytest collects last; it builds what it needs, so it also runs alone."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0803_1975_gb300 import gfp, inputs
+
+from helpers import dev, ensure_built, host
+
+pytestmark = pytest.mark.gpu
+
+
+def call_noalloc(L, p, A, B, C):
+    m, k = A.shape
+    n = B.shape[1]
+    return L.gfp_gemm_noalloc(p, m, k, n, ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                              ctypes.c_void_p(B.data_ptr()), B.stride(0),
+                              ctypes.c_void_p(C.data_ptr()), C.stride(0),
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_matches_workspace_entry_point_twice():
+    ensure_built()
+    L = gfp.load()
+    cases = [(3, 300, 500, 200), (251, 257, 1000, 129)]
+    for call, (p, m, k, n) in enumerate(cases):
+        g = inputs.rng(60, call)
+        A_h = inputs.residues(g, p, m, k)
+        B_h = inputs.residues(g, p, k, n)
+        A, B = dev(A_h), dev(B_h)
+        ref = host(gfp.gfp_gemm(p, A, B, "tc_mma_s8"))
+        C = torch.full((m, n), 7, dtype=torch.uint8, device="cuda")
+        assert call_noalloc(L, p, A, B, C) == 0
+        got = host(C)
+        assert (got == ref).all(), call
+        assert (got == oracle.gemm(p, A_h, B_h)).all(), call
+
+
+def test_noalloc_rejects_problems_beyond_the_scratch():
+    ensure_built()
+    L = gfp.load()
+    # (4096 + 4096) * 4096 bytes > 16 MiB: rejected on the host, nothing launched
+    A = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
+    C = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
+    assert call_noalloc(L, 3, A, A, C) == 7
