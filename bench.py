@@ -195,7 +195,7 @@ def forms_breakdown(gfp, torch, A, B, flush, plain_ms):
         r.update(extra)
         out[name] = r
 
-    for algo in ("plain", "dp4a", "tc_mma_s8", "tc_f16"):
+    for algo in ("plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8"):
         ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(P, M, K, N, algo)), dtype=torch.uint8, device=dev)
         C = torch.empty((M, N), dtype=torch.uint8, device=dev)
         rec(algo, event_time(torch, lambda: gfp.gfp_gemm(P, A, B, algo, out=C, workspace=ws), 7, flush))

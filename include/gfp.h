@@ -64,8 +64,13 @@ typedef enum gfp_status {
  *                   reduction, Section 2.4), reduced mod p once.
  *  GFP_FORM_MIXED : Section 3, equation (LeftComp) -- uncompressed A times a
  *                   row-compressed right operand; each result word holds d+1
- *                   dot products, reduced simultaneously (REDQ). */
-typedef enum gfp_form { GFP_FORM_DOT = 0, GFP_FORM_MIXED = 1 } gfp_form;
+ *                   dot products, reduced simultaneously (REDQ).
+ *  GFP_FORM_LEFT  : Table 2 "Left Comp." -- the same with the outer dimensions
+ *                   exchanged: A packed along m (layout COLS) times
+ *                   uncompressed B; each result word holds d+1 entries of a
+ *                   column of C, reduced by REDQ.
+ * Full compression (Section 4) has its own entry points (gfp_gemm_full). */
+typedef enum gfp_form { GFP_FORM_DOT = 0, GFP_FORM_MIXED = 1, GFP_FORM_LEFT = 2 } gfp_form;
 
 /* Machine words.  t = log2 Q.  Bounds (all require eq. (lower) of Section 2.4,
  * k (p-1)^2 < Q, with k replaced by the k-block kb when one is used):
@@ -118,18 +123,24 @@ typedef enum gfp_layout {
  *                        with fp32 accumulation, which is exact while every
  *                        partial sum is an integer of magnitude < 2^24: the
  *                        k-block is the largest kb with kb ((p-1)/2)^2 + p
- *                        < 2^24 (rounded down to a multiple of 64).  After the
+ *                        < 2^24 (rounded down to a multiple of 128).  After the
  *                        call's kernels complete, the first 4 bytes of its
  *                        workspace hold the kernel's status: 0, or non-zero if
  *                        a bounded internal wait gave up (C is then invalid).
- *  GFP_ALGO_AUTO       : the fastest of the above for (p, m, k, n). */
+ *  GFP_ALGO_TC_F8      : as GFP_ALGO_TC_F16 with fp8 e4m3 operands on tcgen05
+ *                        (kind::f8f6f4), which hold the centred residues of
+ *                        p <= 31 exactly (|c| <= 15); twice the fp16 rate.
+ *                        GFP_EUNSUPPORTED for p > 31.  Same status word.
+ *  GFP_ALGO_AUTO       : GFP_ALGO_TC_F8 for p <= 31, else GFP_ALGO_TC_F16 (the
+ *                        fastest exact forms measured on GB300). */
 typedef enum gfp_algo {
     GFP_ALGO_AUTO = 0,
     GFP_ALGO_PLAIN = 1,
     GFP_ALGO_DP4A = 2,
     GFP_ALGO_TC_MMA_S8 = 3,
     GFP_ALGO_TC_F16 = 4,
-    GFP_ALGO_DOT32 = 5      /* batched only: Q-adic dot form in 32-bit words */
+    GFP_ALGO_DOT32 = 5,     /* batched only: Q-adic dot form in 32-bit words */
+    GFP_ALGO_TC_F8 = 6
 } gfp_algo;
 
 /* ------------------------------------------------------------------------ */
@@ -262,6 +273,11 @@ GFP_API gfp_status gfp_gemm_noalloc(uint32_t p, int64_t m, int64_t k, int64_t n,
  *               layout ROWS of A B mod p: each word's d+1 coefficients are
  *               reduced mod p simultaneously (REDQ).  gfp_unpack(ROWS)
  *               gives the residues.  kb must be 0.
+ *  form = GFP_FORM_LEFT (Table 2, left compression):
+ *     CA_or_A : CA, ceil(m/(d+1)) x k words, layout COLS of A, lda words.
+ *     CB      : B, k x n uint8 residues, ldb bytes.
+ *     C       : CC, ceil(m/(d+1)) x n words, ldc words, layout COLS of
+ *               A B mod p (coefficients reduced by REDQ).  kb must be 0.
  *  (d, Q, kb) must satisfy the bounds of gfp_params for (form, word).
  *  Errors: GFP_EINVAL, GFP_EPRIME, GFP_EQ, GFP_EBOUND, GFP_EUNSUPPORTED,
  *  GFP_ECUDA. */
@@ -271,6 +287,41 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
                                        const void *CB, int64_t ldb,
                                        void *C, int64_t ldc, int64_t kb,
                                        void *stream);
+
+/* Full compression (Section 4): both outer dimensions packed.  With
+ * Theta = Q^(dq+1) (the smallest Theta of eq. (qtheta)):
+ *  CA : ceil(m/(dq+1)) x k words, layout COLS of A in base Q (degree dq),
+ *       lda words (gfp_pack(..., d = dq, Q, GFP_LAYOUT_COLS, ...));
+ *  CB : k x ceil(n/(dth+1)) words, layout ROWS of B in base Theta (degree
+ *       dth), ldb words (gfp_pack(..., d = dth, Theta, GFP_LAYOUT_ROWS, ...));
+ *  CC : ceil(m/(dq+1)) x ceil(n/(dth+1)) words, ldc words: word (u, v) holds
+ *       C[u(dq+1)+i][v(dth+1)+j] mod p as its coefficient of Q^i Theta^j
+ *       (gfp_unpack_block gives the residues).
+ * Word products keep every coefficient, so the whole sum must fit the word:
+ * eq. (lower) for Q and Q^((dq+1)(dth+1)) <= 2^64 (uint64, eq. (dq) with
+ * beta = 64) or < 2^53 (binary64).  Words: GFP_WORD_U64 and GFP_WORD_F64.
+ * Errors as gfp_gemm_compressed. */
+GFP_API gfp_status gfp_gemm_full(uint32_t p, int64_t m, int64_t k, int64_t n, int dq, int dth,
+                                 uint64_t Q, gfp_word word, const void *CA, int64_t lda,
+                                 const void *CB, int64_t ldb, void *CC, int64_t ldc, void *stream);
+
+/* Choose (*dq < 0 on entry) or validate (*dq >= 0) the parameters of
+ * gfp_gemm_full: the smallest Q of eq. (lower), then the split with the most
+ * coefficients per word, the most balanced one among equals.  Host only. */
+GFP_API gfp_status gfp_params_full(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_word word,
+                                   int *dq, int *dth, uint64_t *Q);
+
+/* The block layout of gfp_gemm_full's result for a residue matrix X (rows x
+ * cols): W[u][v] = sum_{i<=dq} sum_{j<=dth} X[u(dq+1)+i][v(dth+1)+j]
+ * Q^(i + j(dq+1)), entries past the edge zero; ceil(rows/(dq+1)) x
+ * ceil(cols/(dth+1)) words, ldw words.  Requires Q > p - 1 and the word
+ * bound of gfp_gemm_full.  Errors as gfp_pack. */
+GFP_API gfp_status gfp_pack_block(uint32_t p, int64_t rows, int64_t cols, const uint8_t *X,
+                                  int64_t ldx, int dq, int dth, uint64_t Q, gfp_word word, void *W,
+                                  int64_t ldw, void *stream);
+GFP_API gfp_status gfp_unpack_block(uint32_t p, int64_t rows, int64_t cols, const void *W,
+                                    int64_t ldw, int dq, int dth, uint64_t Q, gfp_word word,
+                                    uint8_t *X, int64_t ldx, void *stream);
 
 /* One product of a batch: C = A B mod p with A m x k, B k x n, C m x n uint8
  * row-major device matrices.  (The batched workload of this library squares

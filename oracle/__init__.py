@@ -152,7 +152,7 @@ def pack_rows_rev(X: np.ndarray, d: int, Q: int, dtype=np.uint64) -> np.ndarray:
 def pack_cols(X: np.ndarray, d: int, Q: int, dtype=np.uint64) -> np.ndarray:
     """Section 2.1: a column block [b_0 .. b_d] is stored forward, as
     bbar = sum_i b_i Q^i.  Missing entries of the last block are zero
-    (Section 2.3: 'on bbar this means just do nothing').
+    (Section 2.3: the forward word needs no adjustment for them).
     Result: (ceil(rows/(d+1)), cols) words."""
     _check_word_range(d, Q)
     rows, cols = X.shape
@@ -224,6 +224,35 @@ def unpack_rows(W: np.ndarray, cols: int, d: int, Q: int) -> np.ndarray:
     return X
 
 
+def pack_block(X: np.ndarray, dq: int, dth: int, Q: int, dtype=np.uint64) -> np.ndarray:
+    """Section 4 result layout: with Theta = Q^(dq+1), the word of block
+    (u, v) is sum_{i<=dq} sum_{j<=dth} X[u(dq+1)+i][v(dth+1)+j] Q^i Theta^j,
+    i.e. the coefficient of position i + j(dq+1) in base Q.  Entries past the
+    edge count as zero.  Result: (ceil(rows/(dq+1)), ceil(cols/(dth+1)))."""
+    rows, cols = X.shape
+    R = -(-rows // (dq + 1))
+    Cc = -(-cols // (dth + 1))
+    W = np.zeros((R, Cc), dtype=dtype)
+    for i in range(dq + 1):
+        for j in range(dth + 1):
+            sub = np.zeros((R, Cc), dtype=np.uint64)
+            part = X[i::dq + 1, j::dth + 1]
+            sub[:part.shape[0], :part.shape[1]] = part
+            W += (sub * np.uint64(Q ** (i + j * (dq + 1)))).astype(dtype)
+    return W
+
+
+def unpack_block(W: np.ndarray, rows: int, cols: int, dq: int, dth: int, Q: int) -> np.ndarray:
+    """Inverse of pack_block."""
+    X = np.zeros((rows, cols), dtype=np.uint8)
+    for r in range(rows):
+        u, i = divmod(r, dq + 1)
+        for c in range(cols):
+            v, j = divmod(c, dth + 1)
+            X[r, c] = (int(W[u, v]) // Q ** (i + j * (dq + 1))) % Q
+    return X
+
+
 # --------------------------------------------------------------------------
 # Bounds of the paper
 # --------------------------------------------------------------------------
@@ -276,6 +305,11 @@ def amax(p: int, Q: int, d: int) -> int:
 # For the right-compressed (mixed) product every coefficient of a result
 # word is a full dot product < Q, so the word value is < Q^(d+1):
 #   mixed u64 : t(d+1) <= 64;   mixed f64 : Q^(d+1) < 2^53.
+# Left compression (Table 2, "Left Comp.") is the right-compressed product
+# with the roles of the outer dimensions exchanged: the same readings apply.
+# Full compression (Section 4) keeps every coefficient of the word, so the
+# whole accumulated word must fit: t (dq+1)(dth+1) <= 64 for u64 (eq. dq with
+# beta = 64 and Theta = Q^(dq+1)), Q^((dq+1)(dth+1)) < 2^53 for f64.
 WORDS_DOT = ("u64", "u64x128", "u32w", "u32", "f64")
 WORDS_MIXED = ("u64", "f64")
 
@@ -308,12 +342,27 @@ def word_admissible(form: str, word: str, p: int, k: int, d: int, Q: int,
         if word == "f64":
             return upper_bound_holds(Q, d, 53)
         return False
-    if form == "mixed":
+    if form in ("mixed", "left"):
         if word == "u64":
             return t * (d + 1) <= 64
         if word == "f64":
             return upper_bound_holds(Q, d, 53)
         return False
+    return False
+
+
+def full_admissible(word: str, p: int, k: int, dq: int, dth: int, Q: int) -> bool:
+    """Section 4 with Theta = Q^(dq+1) (the smallest Theta of eq. qtheta):
+    eq. (lower) for Q and the whole word within the word size (eq. dq)."""
+    if p < 2 or dq < 0 or dth < 0 or Q < 2 or Q & (Q - 1):
+        return False
+    t = Q.bit_length() - 1
+    if not lower_bound_holds(p, k, Q):
+        return False
+    if word == "u64":
+        return t * (dq + 1) * (dth + 1) <= 64
+    if word == "f64":
+        return Q ** ((dq + 1) * (dth + 1)) < 2 ** 53
     return False
 
 

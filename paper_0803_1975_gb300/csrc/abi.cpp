@@ -89,12 +89,15 @@ static gfp_status resolve_algo(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_
         case GFP_ALGO_DP4A:
         case GFP_ALGO_TC_MMA_S8:
         case GFP_ALGO_TC_F16: *out = algo; return GFP_OK;
+        case GFP_ALGO_TC_F8:
+            if (p > 31) return GFP_EUNSUPPORTED;
+            *out = algo;
+            return GFP_OK;
         case GFP_ALGO_AUTO: {
-            // The tensor-core forms win at every size worth a launch; the
-            // int8 form is the one with whole-k blocks for every p <= 251.
-            (void)p;
+            // Measured on GB300: tcgen05 with fp8 operands (p <= 31) or fp16
+            // operands is the fastest exact form at every size worth a launch.
             (void)k;
-            *out = GFP_ALGO_TC_MMA_S8;
+            *out = p <= 31 ? GFP_ALGO_TC_F8 : GFP_ALGO_TC_F16;
             return GFP_OK;
         }
     }
@@ -111,6 +114,7 @@ GFP_API gfp_status gfp_gemm_workspace_size(uint32_t p, int64_t m, int64_t k, int
     *bytes = 0;
     if (a == GFP_ALGO_TC_MMA_S8) *bytes = tc_mma_workspace(m, k, n);
     if (a == GFP_ALGO_TC_F16) *bytes = tc_f16_workspace(m, k, n);
+    if (a == GFP_ALGO_TC_F8) *bytes = tc_f8_workspace(m, k, n);
     return GFP_OK;
 }
 
@@ -136,11 +140,15 @@ GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n, const u
         if (tot >= ((unsigned __int128)1 << 32)) return GFP_EBOUND;
         return launch_plain(p, m, k, n, A, lda, B, ldb, C, ldc, a == GFP_ALGO_DP4A, s);
     }
-    const size_t need = a == GFP_ALGO_TC_MMA_S8 ? tc_mma_workspace(m, k, n) : tc_f16_workspace(m, k, n);
+    const size_t need = a == GFP_ALGO_TC_MMA_S8 ? tc_mma_workspace(m, k, n)
+                        : a == GFP_ALGO_TC_F8   ? tc_f8_workspace(m, k, n)
+                                                : tc_f16_workspace(m, k, n);
     if (need > 0 && (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)))
         return GFP_EWORKSPACE;
     if (a == GFP_ALGO_TC_MMA_S8)
         return launch_tc_mma(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
+    if (a == GFP_ALGO_TC_F8)
+        return launch_tc_f8(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
     return launch_tc_f16(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
 }
 
@@ -150,7 +158,7 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
                                        int64_t ldb, void *C, int64_t ldc, int64_t kb,
                                        void *stream) {
     if (m < 0 || k < 0 || n < 0 || kb < 0) return GFP_EINVAL;
-    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED) return GFP_EINVAL;
+    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED && form != GFP_FORM_LEFT) return GFP_EINVAL;
     if (word_bytes(word) == 0) return GFP_EINVAL;
     gfp_status st = check_dqt(p, k, d, Q, form, word, kb);
     if (st != GFP_OK) return st;
@@ -165,10 +173,63 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
         return launch_dot(p, m, kc, n, d, t, word, CA_or_A, lda, CB, ldb, (uint8_t *)C, ldc, kbw,
                           s);
     }
+    if (form == GFP_FORM_LEFT) {
+        const int64_t mc = cdiv(m, d + 1);
+        if (!C || ldc < n) return GFP_EINVAL;
+        if (k > 0 && (!CA_or_A || !CB || lda < k || ldb < n)) return GFP_EINVAL;
+        return launch_left(p, mc, k, n, d, t, word, CA_or_A, lda, (const uint8_t *)CB, ldb, C, ldc, s);
+    }
     const int64_t nc = cdiv(n, d + 1);
     if (!C || ldc < nc) return GFP_EINVAL;
     if (k > 0 && (!CA_or_A || !CB || lda < k || ldb < nc)) return GFP_EINVAL;
     return launch_mixed(p, m, k, nc, d, t, word, (const uint8_t *)CA_or_A, lda, CB, ldb, C, ldc, s);
+}
+
+GFP_API gfp_status gfp_gemm_full(uint32_t p, int64_t m, int64_t k, int64_t n, int dq, int dth,
+                                 uint64_t Q, gfp_word word, const void *CA, int64_t lda,
+                                 const void *CB, int64_t ldb, void *CC, int64_t ldc, void *stream) {
+    if (m < 0 || k < 0 || n < 0) return GFP_EINVAL;
+    gfp_status st = check_full(p, k, dq, dth, Q, word);
+    if (st != GFP_OK) return st;
+    if (m == 0 || n == 0) return GFP_OK;
+    const int64_t mc = cdiv(m, dq + 1), nc = cdiv(n, dth + 1);
+    if (!CC || ldc < nc) return GFP_EINVAL;
+    if (k > 0 && (!CA || !CB || lda < k || ldb < nc)) return GFP_EINVAL;
+    return launch_full(p, mc, k, nc, dq, dth, log2_exact(Q), word, CA, lda, CB, ldb, CC, ldc,
+                       (cudaStream_t)stream);
+}
+
+static gfp_status block_args(uint32_t p, int64_t rows, int64_t cols, int dq, int dth, uint64_t Q,
+                             gfp_word word, int64_t ldx, int64_t ldw, bool have_x, bool have_w) {
+    if (rows < 0 || cols < 0 || dq < 0 || dth < 0 || dq > 63 || dth > 63) return GFP_EINVAL;
+    if (!is_prime_small(p)) return GFP_EPRIME;
+    const int t = log2_exact(Q);
+    if (t < 0) return GFP_EQ;
+    if (word != GFP_WORD_U64 && word != GFP_WORD_F64) return GFP_EUNSUPPORTED;
+    if ((uint64_t)(p - 1) >= Q) return GFP_EBOUND;
+    const int64_t bits = (int64_t)t * (dq + 1) * (dth + 1);
+    if (bits > (word == GFP_WORD_F64 ? 52 : 64)) return GFP_EBOUND;
+    if (rows == 0 || cols == 0) return GFP_OK;
+    if (!have_x || !have_w || ldx < cols || ldw < cdiv(cols, dth + 1)) return GFP_EINVAL;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_pack_block(uint32_t p, int64_t rows, int64_t cols, const uint8_t *X,
+                                  int64_t ldx, int dq, int dth, uint64_t Q, gfp_word word, void *W,
+                                  int64_t ldw, void *stream) {
+    gfp_status st = block_args(p, rows, cols, dq, dth, Q, word, ldx, ldw, X != nullptr, W != nullptr);
+    if (st != GFP_OK || rows == 0 || cols == 0) return st;
+    return launch_block(true, rows, cols, X, nullptr, ldx, dq, dth, log2_exact(Q), word, nullptr, W, ldw,
+                        (cudaStream_t)stream);
+}
+
+GFP_API gfp_status gfp_unpack_block(uint32_t p, int64_t rows, int64_t cols, const void *W,
+                                    int64_t ldw, int dq, int dth, uint64_t Q, gfp_word word,
+                                    uint8_t *X, int64_t ldx, void *stream) {
+    gfp_status st = block_args(p, rows, cols, dq, dth, Q, word, ldx, ldw, X != nullptr, W != nullptr);
+    if (st != GFP_OK || rows == 0 || cols == 0) return st;
+    return launch_block(false, rows, cols, nullptr, X, ldx, dq, dth, log2_exact(Q), word, W, nullptr, ldw,
+                        (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 // form of Section 2 in five machine words, and the right-compressed form of
 // Section 3 with the simultaneous reduction REDQ.
 #include <cstdint>
+#include <type_traits>
 
 #include "gfp_internal.h"
 #include "simt_gemm.cuh"
@@ -21,6 +22,8 @@ struct PlainP {
     using Acc = uint32_t;
     using GC = uint8_t;
     static constexpr bool kBlocked = false;
+    static constexpr bool kAtomic = false;
+    static constexpr bool kSlowPipe = false;
     struct Params {
         uint64_t M;
         uint32_t p;
@@ -104,6 +107,8 @@ struct DotBase {
     using GC = uint8_t;
     using Params = DotParams;
     static constexpr bool kBlocked = BLK;
+    static constexpr bool kAtomic = false;
+    static constexpr bool kSlowPipe = std::is_floating_point<W>::value;   // FP64 words: DFMA-bound
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                                     const Params &) {
         return ld_guarded<GA, SA>(A, lda, i, k, M, K);
@@ -233,15 +238,18 @@ __device__ __forceinline__ uint64_t redq(uint64_t r, const MixedParams &prm) {
     return out;
 }
 
-struct MixedU64 {
+template <bool PARTIAL>
+struct MixedU64T {
     using GA = uint8_t;
     using GB = uint64_t;
     using SA = uint32_t;
     using SB = uint64_t;
     using Acc = uint64_t;
-    using GC = uint64_t;
+    using GC = std::conditional_t<PARTIAL, unsigned long long, uint64_t>;
     using Params = MixedParams;
     static constexpr bool kBlocked = false;
+    static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kSlowPipe = std::is_floating_point<GB>::value;
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                                     const Params &) {
         return ld_guarded<GA, SA>(A, lda, i, k, M, K);
@@ -252,14 +260,17 @@ struct MixedU64 {
     }
     __device__ static void mac(uint64_t &acc, uint32_t a, uint64_t b) { acc += (uint64_t)a * b; }
     __device__ static uint32_t extract(uint64_t, const Params &) { return 0; }
-    __device__ static uint64_t finish(uint64_t acc, uint32_t, const Params &prm) {
-        return redq(acc, prm);
+    __device__ static GC finish(uint64_t acc, uint32_t, const Params &prm) {
+        if constexpr (PARTIAL) return (GC)acc;    // a slice's raw word sum
+        else return redq(acc, prm);
     }
 };
+using MixedU64 = MixedU64T<false>;
 
 // Binary64 words: every partial sum is an integer below Q^(d+1) < 2^53, so
 // the fused multiply-adds are exact in any rounding mode.
-struct MixedF64 {
+template <bool PARTIAL>
+struct MixedF64T {
     using GA = uint8_t;
     using GB = double;
     using SA = double;
@@ -268,6 +279,8 @@ struct MixedF64 {
     using GC = double;
     using Params = MixedParams;
     static constexpr bool kBlocked = false;
+    static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kSlowPipe = std::is_floating_point<GB>::value;
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                                     const Params &) {
         return (i < M && k < K) ? (double)A[i * lda + k] : 0.0;
@@ -279,20 +292,186 @@ struct MixedF64 {
     __device__ static void mac(double &acc, double a, double b) { acc = __fma_rn(a, b, acc); }
     __device__ static uint32_t extract(double, const Params &) { return 0; }
     __device__ static double finish(double acc, uint32_t, const Params &prm) {
-        return (double)redq(__double2ull_rz(acc), prm);
+        if constexpr (PARTIAL) return acc;        // a slice's raw word sum, exact
+        else return (double)redq(__double2ull_rz(acc), prm);
+    }
+};
+using MixedF64 = MixedF64T<false>;
+
+// In-place REDQ over a matrix of raw result words (after split-k slices were
+// summed into it).
+template <class W>
+__global__ void redq_inplace_kernel(W *__restrict__ CC, int64_t ldc, int64_t rows, int64_t cols,
+                                    MixedParams prm) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+        W *w = CC + i * ldc + j;
+        if constexpr (std::is_floating_point<W>::value) *w = (W)redq(__double2ull_rz(*w), prm);
+        else *w = (W)redq((uint64_t)*w, prm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Left compression (Table 2, "Left Comp."): A packed along m into column
+// words CA[u][l] = sum_i A[u(d+1)+i][l] Q^i, times uncompressed B; the result
+// word sum_l CA[u][l] B[l][j] holds the d+1 entries C[u(d+1)+i][j], reduced
+// by REDQ (the right-compressed product with the outer dimensions exchanged).
+//
+// Full compression (Section 4): A packed along m in base Q (degree dq), B
+// packed along n in base Theta = Q^(dq+1) (degree dth); the word product
+// sum_l CA[u][l] CB[l][v] holds all (dq+1)(dth+1) entries of a block of C as
+// base-Q coefficients, each below Q (eq. lower), so the whole word is exact
+// while it fits (eq. dq); REDQ reduces all of them at once.
+// ---------------------------------------------------------------------------
+template <class W, bool PARTIAL>
+struct LeftT {
+    static constexpr bool FP = std::is_floating_point<W>::value;
+    using GA = W;
+    using GB = uint8_t;
+    using SA = W;
+    using SB = std::conditional_t<FP, double, uint32_t>;
+    using Acc = W;
+    using GC = std::conditional_t<PARTIAL && !FP, unsigned long long, W>;
+    using Params = MixedParams;
+    static constexpr bool kBlocked = false;
+    static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kSlowPipe = FP;
+    __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
+                             const Params &) {
+        return ld_guarded<GA, SA>(A, lda, i, k, M, K);
+    }
+    __device__ static SB ldB(const GB *B, int64_t ldb, int64_t k, int64_t j, int64_t K, int64_t N,
+                             const Params &) {
+        return (k < K && j < N) ? (SB)B[k * ldb + j] : SB(0);
+    }
+    __device__ static void mac(Acc &acc, SA a, SB b) {
+        if constexpr (FP) acc = __fma_rn(a, b, acc);
+        else acc += a * (uint64_t)b;
+    }
+    __device__ static uint32_t extract(Acc, const Params &) { return 0; }
+    __device__ static GC finish(Acc acc, uint32_t, const Params &prm) {
+        if constexpr (PARTIAL) return (GC)acc;
+        else if constexpr (FP) return (GC)redq(__double2ull_rz(acc), prm);
+        else return (GC)redq(acc, prm);
     }
 };
 
-// Tile shapes: L = 128 x 128 (8 x 8 per thread) for grids that fill the GPU,
-// S = 64 x 64 (4 x 4 per thread) for smaller results.  256 threads either way.
+template <class W, bool PARTIAL>
+struct FullT {
+    static constexpr bool FP = std::is_floating_point<W>::value;
+    using GA = W;
+    using GB = W;
+    using SA = W;
+    using SB = W;
+    using Acc = W;
+    using GC = std::conditional_t<PARTIAL && !FP, unsigned long long, W>;
+    using Params = MixedParams;
+    static constexpr bool kBlocked = false;
+    static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kSlowPipe = FP;
+    __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
+                             const Params &) {
+        return ld_guarded<GA, SA>(A, lda, i, k, M, K);
+    }
+    __device__ static SB ldB(const GB *B, int64_t ldb, int64_t k, int64_t j, int64_t K, int64_t N,
+                             const Params &) {
+        return ld_guarded<GB, SB>(B, ldb, k, j, K, N);
+    }
+    __device__ static void mac(Acc &acc, SA a, SB b) {
+        if constexpr (FP) acc = __fma_rn(a, b, acc);   // exact: every partial sum < 2^53
+        else acc += a * b;                            // exact: the word stays < 2^64
+    }
+    __device__ static uint32_t extract(Acc, const Params &) { return 0; }
+    __device__ static GC finish(Acc acc, uint32_t, const Params &prm) {
+        if constexpr (PARTIAL) return (GC)acc;
+        else if constexpr (FP) return (GC)redq(__double2ull_rz(acc), prm);
+        else return (GC)redq(acc, prm);
+    }
+};
+
+// Tile shapes, 256 threads each: L = 128 x 128 (8 x 8 per thread), S = 64 x 64
+// (4 x 4), XS = 32 x 32 (2 x 2).  Larger register tiles issue fewer shared-
+// memory loads per multiply-add; smaller tiles balance better over the SMs.
+// The choice minimises (tiles on the busiest SM) x (tile area) / (issue
+// efficiency of the tile), with the efficiency taken as 1 for every shape when
+// the policy is bound by a slow pipe (kSlowPipe, e.g. FP64).
+enum class Tile { L, S, XS };
+
+template <class P>
+Tile choose_tile(int64_t M, int64_t N, bool allow_large) {
+    const int64_t sms = num_sms();
+    const double effL = 1.0, effS = P::kSlowPipe ? 1.0 : 0.7, effXS = P::kSlowPipe ? 1.0 : 0.4;
+    auto cost = [&](int bm, int bn, double eff) {
+        const int64_t t = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+        return (double)((t + sms - 1) / sms) * bm * bn / eff;
+    };
+    Tile best = Tile::S;
+    double c = cost(64, 64, effS);
+    if (allow_large && cost(128, 128, effL) < c) {
+        best = Tile::L;
+        c = cost(128, 128, effL);
+    }
+    if (cost(32, 32, effXS) < c) best = Tile::XS;
+    return best;
+}
+
 template <class P>
 cudaError_t run_simt(const typename P::GA *A, int64_t lda, const typename P::GB *B, int64_t ldb,
                      typename P::GC *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
-                     const typename P::Params &prm, cudaStream_t s, bool allow_large = true) {
-    const int64_t tiles_l = ((M + 127) / 128) * ((N + 127) / 128);
-    if (allow_large && tiles_l >= num_sms())
-        return simt_gemm_launch<P, 128, 128, 8, 8, 8>(A, lda, B, ldb, C, ldc, M, N, K, prm, s);
-    return simt_gemm_launch<P, 64, 64, 8, 4, 4>(A, lda, B, ldb, C, ldc, M, N, K, prm, s);
+                     const typename P::Params &prm, cudaStream_t s, bool allow_large = true,
+                     int splits = 1) {
+    switch (choose_tile<P>(M, N, allow_large)) {
+        case Tile::L:
+            return simt_gemm_launch<P, 128, 128, 8, 8, 8>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
+        case Tile::XS:
+            return simt_gemm_launch<P, 32, 32, 8, 2, 2>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
+        default:
+            return simt_gemm_launch<P, 64, 64, 8, 4, 4>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
+    }
+}
+
+MixedParams redq_params(uint32_t p, int t, int digits_minus_1) {
+    MixedParams prm;
+    prm.M = fastmod_magic(p);
+    prm.p = p;
+    prm.t = (uint32_t)t;
+    prm.d = digits_minus_1;
+    const uint32_t qmod = (uint32_t)((t >= 64 ? 0 : (1ull << t)) % p);
+    prm.qc = p - qmod;
+    prm.kbw = 0;
+    return prm;
+}
+
+// Products whose result words are reduced by REDQ: split k when the (narrow)
+// result cannot fill the GPU -- slices add exactly because every coefficient
+// of the full sum is below Q -- then REDQ in place.
+template <class PF, class PP, class W>
+gfp_status run_redq_form(const typename PF::GA *A, int64_t lda, const typename PF::GB *B, int64_t ldb,
+                         W *C, int64_t ldc, int64_t M, int64_t N, int64_t K, const MixedParams &prm,
+                         cudaStream_t s) {
+    const int64_t sms = num_sms();
+    const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    int splits = 1;
+    if (tiles < 2 * sms && K >= 512) {
+        splits = (int)((2 * sms + tiles - 1) / tiles);
+        const int maxs = (int)(K / 256);
+        if (splits > maxs) splits = maxs;
+        if (splits < 1) splits = 1;
+    }
+    cudaError_t e;
+    if (splits > 1) {
+        e = cudaMemset2DAsync(C, (size_t)ldc * sizeof(W), 0, (size_t)N * sizeof(W), (size_t)M, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = simt_gemm_launch<PP, 64, 64, 8, 4, 4>(A, lda, B, ldb, reinterpret_cast<typename PP::GC *>(C), ldc,
+                                                 M, N, K, prm, s, splits);
+        if (e != cudaSuccess) return cuda_fail(e);
+        dim3 grid((unsigned)((N + 255) / 256), (unsigned)(M < 65535 ? M : 65535));
+        redq_inplace_kernel<W><<<grid, 256, 0, s>>>(C, ldc, M, N, prm);
+        return check_launch();
+    }
+    e = run_simt<PF>(A, lda, B, ldb, reinterpret_cast<typename PF::GC *>(C), ldc, M, N, K, prm, s);
+    return e == cudaSuccess ? GFP_OK : cuda_fail(e);
 }
 
 DotParams dot_params(uint32_t p, int d, int t, int64_t kbw) {
@@ -368,7 +547,40 @@ gfp_status launch_mixed(uint32_t p, int64_t m, int64_t k, int64_t nc, int d, int
     const uint32_t qmod = (uint32_t)((t >= 64 ? 0 : (1ull << t)) % p);
     prm.qc = p - qmod;
     prm.kbw = 0;
+    // The result m x ceil(n/(d+1)) is narrow: when its tiles cannot fill the
+    // GPU, split k.  Each coefficient of a slice's word sum is below Q (eq.
+    // (lower) holds for the whole k), so the slices' words add without carries:
+    // zero CC, add the slices atomically, then REDQ in place.
+    const int64_t sms = num_sms();
+    const int64_t tiles = ((m + 63) / 64) * ((nc + 63) / 64);
+    int splits = 1;
+    if (tiles < 2 * sms && k >= 512) {
+        splits = (int)((2 * sms + tiles - 1) / tiles);
+        const int maxs = (int)(k / 256);
+        if (splits > maxs) splits = maxs;
+        if (splits < 1) splits = 1;
+    }
     cudaError_t e = cudaErrorInvalidValue;
+    const size_t wb = 8;
+    if (splits > 1) {
+        e = cudaMemset2DAsync(CC, (size_t)ldc * wb, 0, (size_t)nc * wb, (size_t)m, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (word == GFP_WORD_U64)
+            e = simt_gemm_launch<MixedU64T<true>, 64, 64, 8, 4, 4>(
+                A, lda, static_cast<const uint64_t *>(CB), ldb, static_cast<unsigned long long *>(CC),
+                ldc, m, nc, k, prm, s, splits);
+        else if (word == GFP_WORD_F64)
+            e = simt_gemm_launch<MixedF64T<true>, 64, 64, 8, 4, 4>(
+                A, lda, static_cast<const double *>(CB), ldb, static_cast<double *>(CC), ldc, m, nc, k,
+                prm, s, splits);
+        if (e != cudaSuccess) return cuda_fail(e);
+        dim3 grid((unsigned)((nc + 255) / 256), (unsigned)(m < 65535 ? m : 65535));
+        if (word == GFP_WORD_U64)
+            redq_inplace_kernel<uint64_t><<<grid, 256, 0, s>>>(static_cast<uint64_t *>(CC), ldc, m, nc, prm);
+        else
+            redq_inplace_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(CC), ldc, m, nc, prm);
+        return check_launch();
+    }
     if (word == GFP_WORD_U64)
         e = run_simt<MixedU64>(A, lda, static_cast<const uint64_t *>(CB), ldb,
                                static_cast<uint64_t *>(CC), ldc, m, nc, k, prm, s);
@@ -376,6 +588,38 @@ gfp_status launch_mixed(uint32_t p, int64_t m, int64_t k, int64_t nc, int d, int
         e = run_simt<MixedF64>(A, lda, static_cast<const double *>(CB), ldb,
                                static_cast<double *>(CC), ldc, m, nc, k, prm, s);
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+}
+
+}  // namespace gfp
+
+namespace gfp {
+
+gfp_status launch_left(uint32_t p, int64_t mc, int64_t k, int64_t n, int d, int t, gfp_word word,
+                       const void *CA, int64_t lda, const uint8_t *B, int64_t ldb, void *CC,
+                       int64_t ldc, cudaStream_t s) {
+    const MixedParams prm = redq_params(p, t, d);
+    if (word == GFP_WORD_U64)
+        return run_redq_form<LeftT<uint64_t, false>, LeftT<uint64_t, true>, uint64_t>(
+            static_cast<const uint64_t *>(CA), lda, B, ldb, static_cast<uint64_t *>(CC), ldc, mc, n, k, prm, s);
+    if (word == GFP_WORD_F64)
+        return run_redq_form<LeftT<double, false>, LeftT<double, true>, double>(
+            static_cast<const double *>(CA), lda, B, ldb, static_cast<double *>(CC), ldc, mc, n, k, prm, s);
+    return GFP_EUNSUPPORTED;
+}
+
+gfp_status launch_full(uint32_t p, int64_t mc, int64_t k, int64_t nc, int dq, int dth, int t,
+                       gfp_word word, const void *CA, int64_t lda, const void *CB, int64_t ldb,
+                       void *CC, int64_t ldc, cudaStream_t s) {
+    const MixedParams prm = redq_params(p, t, (dq + 1) * (dth + 1) - 1);
+    if (word == GFP_WORD_U64)
+        return run_redq_form<FullT<uint64_t, false>, FullT<uint64_t, true>, uint64_t>(
+            static_cast<const uint64_t *>(CA), lda, static_cast<const uint64_t *>(CB), ldb,
+            static_cast<uint64_t *>(CC), ldc, mc, nc, k, prm, s);
+    if (word == GFP_WORD_F64)
+        return run_redq_form<FullT<double, false>, FullT<double, true>, double>(
+            static_cast<const double *>(CA), lda, static_cast<const double *>(CB), ldb,
+            static_cast<double *>(CC), ldc, mc, nc, k, prm, s);
+    return GFP_EUNSUPPORTED;
 }
 
 }  // namespace gfp

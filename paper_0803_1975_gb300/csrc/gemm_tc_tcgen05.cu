@@ -1,11 +1,13 @@
 // Exact C = A B mod p on the 5th-generation tensor cores (tcgen05.mma,
-// kind::f16, fp32 accumulation in tensor memory).  No counterpart in the
-// paper; it is the tensor-core analogue of its delayed reduction (Section 2.4):
-// many products are accumulated before a single reduction mod p.
+// kind::f16 or kind::f8f6f4, fp32 accumulation in tensor memory).  No
+// counterpart in the paper; it is the tensor-core analogue of its delayed
+// reduction (Section 2.4): many products are accumulated before a single
+// reduction mod p.
 //
 // Exactness.  Residues are centred, c = r - p [r > (p-1)/2], |c| <= h =
-// (p-1)/2 (p = 2 keeps 0/1), and held in fp16, where every integer of
-// magnitude <= 2048 is exact.  Each product is an integer of magnitude <= h^2
+// (p-1)/2 (p = 2 keeps 0/1), and held in fp16 (every integer of magnitude
+// <= 2048 is exact) or, for p <= 31, in fp8 e4m3 (every integer of magnitude
+// <= 16 is exact).  Each product is an integer of magnitude <= h^2
 // and every partial sum of a k-block of kb terms is an integer of magnitude
 // <= kb h^2 < 2^24, so it is representable in fp32 and no rounding occurs in
 // any order of summation.  kb is the largest multiple of 64 with
@@ -14,14 +16,15 @@
 // running residue held in registers (4 residues per 32-bit register).
 //
 // Kernel.  Persistent, one CTA per SM, 192 threads:
-//   warp 0    : TMA producer (one thread) -- A tile 128 x 64 and B tile
-//               256 x 64 fp16 per stage, 128-byte swizzle, 4 stages;
+//   warp 0    : TMA producer (one thread) -- per stage an A tile of 128 rows
+//               and a B tile of BN (128 or 256) rows, 128 bytes of k each
+//               (64 fp16 or 128 fp8 values), 128-byte swizzle, 4 stages;
 //   warp 1    : tensor memory allocator and MMA issuer (one thread) --
-//               4 x tcgen05.mma 128 x 256 x 16 per stage into one of two
-//               256-column fp32 accumulators;
+//               4 x tcgen05.mma 128 x BN x (16 fp16 | 32 fp8) per stage into
+//               one of two BN-column fp32 accumulators;
 //   warps 2-5 : epilogue -- tcgen05.ld of the accumulator (warp w reads TMEM
 //               lanes 32 (w % 4) .. +31), reduction mod p, uint8 stores.
-// A unit of work is one k-block of one 128 x 256 output tile; units alternate
+// A unit of work is one k-block of one 128 x BN output tile; units alternate
 // between the two accumulators so the epilogue of one overlaps the MMAs of
 // the next.  Every mbarrier wait is bounded (globaltimer): on expiry the
 // kernel records an error in the status word, stops issuing, waits (bounded)
@@ -30,19 +33,33 @@
 
 #include <cuda.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "gfp_internal.h"
 
 namespace gfp {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;             // BK fp16 = 128 bytes
+constexpr int BM = 128;
+constexpr int ROWB = 128;                               // bytes of k per operand row per stage
 constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;         // 48 KB, multiple of 1024
 constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;                    // 2 x 256 fp32 columns
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+
+template <int BN_, bool FP8_>
+struct TcCfg {
+    static constexpr int BN = BN_;
+    static constexpr bool FP8 = FP8_;
+    static constexpr int BKE = FP8 ? 128 : 64;         // k elements per stage
+    static constexpr int A_BYTES = BM * ROWB, B_BYTES = BN * ROWB;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // multiple of 1024
+    static constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+    // Instruction descriptor (kind::f16 and kind::f8f6f4 share the layout):
+    // fp32 accumulator (bits 4-5 = 1), A and B types 0 (fp16, resp. e4m3) in
+    // bits 7-9 and 10-12, both K-major (bits 15, 16 = 0), N >> 3 in bits
+    // 17-22, M >> 4 in bits 24-28.
+    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;   // 4 s
 
 // status codes written to the status word
@@ -120,17 +137,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: fp32 accumulator (bits 4-5 = 1), fp16 A
-// and B (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 in
-// bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accum)
-        : "memory");
+template <bool FP8>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
+    if constexpr (FP8)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
@@ -165,8 +186,8 @@ struct TcArgs {
     uint8_t *C;
     int64_t ldc, m, n;
     int tiles_m, tiles_n;
-    int ktiles;        // k in BK slices
-    int kb_tiles;      // k-block in BK slices
+    int ktiles;        // k in stage slices (128 bytes of k)
+    int kb_tiles;      // k-block in stage slices
     int kblocks;       // ceil(ktiles / kb_tiles)
     uint32_t p, off;   // off = p ceil(2^24 / p): makes |x| < 2^24 non-negative
     uint64_t M;        // fastmod magic of p
@@ -185,10 +206,12 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     tn = r / gsize;
 }
 
-template <bool BLOCKED>
+template <class CFG, bool BLOCKED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs g) {
+    constexpr int BN = CFG::BN, STAGE_BYTES = CFG::STAGE_BYTES, A_BYTES = CFG::A_BYTES;
+    constexpr uint32_t TMEM_COLS = CFG::TMEM_COLS;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;     // 1024-aligned for the swizzle atoms
@@ -250,8 +273,8 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     }
                     const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
                     mbar_expect_tx(full_bar(stage), STAGE_BYTES);
-                    tma_load_2d(sa, &tmA, kt * BK, tm * BM, full_bar(stage));
-                    tma_load_2d(sb, &tmB, kt * BK, tn * BN, full_bar(stage));
+                    tma_load_2d(sa, &tmA, kt * CFG::BKE, tm * BM, full_bar(stage));
+                    tma_load_2d(sb, &tmB, kt * CFG::BKE, tn * BN, full_bar(stage));
                     issued[stage] = true;
                     issued_parity[stage] = phase;
                     if (++stage == STAGES) {
@@ -286,7 +309,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         break;
                     }
                     fence_after();
-                    const uint32_t d = tmem + buf * 256u;
+                    const uint32_t d = tmem + buf * (uint32_t)BN;
                     const int k0 = j * g.kb_tiles;
                     const int k1 = min(g.ktiles, k0 + g.kb_tiles);
                     for (int kt = k0; kt < k1; ++kt) {
@@ -297,9 +320,9 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         fence_after();
                         const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk)
-                            mma_f16(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
-                                    (kt > k0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < ROWB / 32; ++kk)   // 32 bytes of k per MMA
+                            mma_issue<CFG::FP8>(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
+                                                CFG::IDESC, (kt > k0 || kk > 0) ? 1u : 0u);
                         mma_commit(empty_bar(stage));
                         if (++stage == STAGES) {
                             stage = 0;
@@ -325,7 +348,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         uint32_t unit = 0;
         bool ok = true;
-        uint32_t run[BLOCKED ? 64 : 1];
+        uint32_t run[BLOCKED ? BN / 4 : 1];
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
             int tm, tn;
             tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
@@ -333,7 +356,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const int64_t col0 = (int64_t)tn * BN;
             if constexpr (BLOCKED) {
 #pragma unroll
-                for (int i = 0; i < 64; ++i) run[i] = 0;
+                for (int i = 0; i < BN / 4; ++i) run[i] = 0;
             }
             for (int j = 0; j < g.kblocks; ++j, ++unit) {
                 const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
@@ -350,7 +373,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t v[32];
-                    tmem_ld32(tmem + lane_addr + buf * 256u + c * 32, v);
+                    tmem_ld32(tmem + lane_addr + buf * (uint32_t)BN + c * 32, v);
                     uint32_t w[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
@@ -397,46 +420,78 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     }
 }
 
-// ---- preprocess: centred fp16 operands, zero padded to the tile multiples
-__global__ void to_f16_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m, int64_t k,
-                                   __half *__restrict__ out, int64_t kp, int64_t mp, uint32_t p,
-                                   uint32_t h) {
-    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
-    if (l >= kp) return;
-    for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
-        __align__(16) __half v[8];
+// ---- preprocess: centred fp16 / e4m3 operands, zero padded to tile multiples
+__device__ __forceinline__ int centre_i(uint32_t r, uint32_t p, uint32_t h) {
+    return (int)r - (r > h ? (int)p : 0);
+}
+
+// e4m3 code of an integer |c| <= 16 (exact): __nv_cvt_float_to_fp8 is exact
+// on representable values.
+template <bool FP8>
+__device__ __forceinline__ void put16(void *dst, const int (&c)[16]) {
+    if constexpr (FP8) {
+        uint32_t w[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            int c = 0;
-            if (i < m && l + e < k) {
-                const uint32_t r = A[i * lda + l + e];
-                c = (int)r - (r > h ? (int)p : 0);
-            }
-            v[e] = __int2half_rn(c);
+        for (int q = 0; q < 4; ++q) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                v |= (uint32_t)__nv_cvt_float_to_fp8((float)c[4 * q + b], __NV_SATFINITE, __NV_E4M3)
+                     << (8 * b);
+            w[q] = v;
         }
-        *reinterpret_cast<uint4 *>(out + i * kp + l) = *reinterpret_cast<uint4 *>(v);
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+        __align__(16) __half hv[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) hv[e] = __int2half_rn(c[e]);
+        reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(hv)[0];
+        reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(hv)[1];
     }
 }
 
-__global__ void to_f16_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k,
-                                        int64_t n, __half *__restrict__ out, int64_t kp, int64_t np,
-                                        uint32_t p, uint32_t h) {
+// out[i][l] = centre(A[i][l]) for i < m, l < k; zero elsewhere in mp x kp.
+// One thread per 16 consecutive values of a row.
+template <bool FP8>
+__global__ void to_op_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m, int64_t k,
+                                  uint8_t *__restrict__ out, int64_t kp, int64_t mp, uint32_t p,
+                                  uint32_t h) {
+    constexpr int ES = FP8 ? 1 : 2;
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    if (l >= kp) return;
+    for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
+        int c[16];
+        const uint8_t *a = A + i * lda + l;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) c[e] = (i < m && l + e < k) ? centre_i(a[e], p, h) : 0;
+        put16<FP8>(out + (i * kp + l) * ES, c);
+    }
+}
+
+// out[j][l] = centre(B[l][j]) for l < k, j < n; zero elsewhere in np x kp.
+// 64 x 64 tiles through shared memory; 256 threads, 16 values each way.
+template <bool FP8>
+__global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k,
+                                       int64_t n, uint8_t *__restrict__ out, int64_t kp, int64_t np,
+                                       uint32_t p, uint32_t h) {
+    constexpr int ES = FP8 ? 1 : 2;
     __shared__ int8_t tile[64][64 + 4];
     const int64_t l0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
-    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;
-    for (int r = ty; r < 64; r += 4) {
-        const int64_t l = l0 + r, j = j0 + tx;
-        int c = 0;
-        if (l < k && j < n) {
-            const uint32_t v = B[l * ldb + j];
-            c = (int)v - (v > h ? (int)p : 0);
-        }
-        tile[r][tx] = (int8_t)c;
+    const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
+    {
+        const int64_t l = l0 + r;
+        const uint8_t *b = B + l * ldb + j0 + q;
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            tile[r][q + e] = (int8_t)((l < k && j0 + q + e < n) ? centre_i(b[e], p, h) : 0);
     }
     __syncthreads();
-    for (int r = ty; r < 64; r += 4) {
-        const int64_t j = j0 + r, l = l0 + tx;
-        if (j < np && l < kp) out[j * kp + l] = __int2half_rn((int)tile[tx][r]);
+    const int64_t j = j0 + r;
+    if (j < np) {
+        int c[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) c[e] = tile[q + e][r];
+        put16<FP8>(out + (j * kp + l0 + q) * ES, c);
     }
 }
 
@@ -460,62 +515,76 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *map, const __half *base, int64_t rows, int64_t kp, int box_rows) {
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int box_rows, bool fp8) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
+    const int es = fp8 ? 1 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * es};
+    cuuint32_t box[2] = {(cuuint32_t)(ROWB / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+              const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-int64_t tc_kblock_f32(uint32_t p) {
-    const int64_t h = p == 2 ? 1 : (p - 1) / 2;
-    const int64_t kb = ((int64_t(1) << 24) - 1 - p) / (h * h);
-    return kb / BK * BK;
+template <class CFG, bool BLOCKED>
+void launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, int grid, cudaStream_t s) {
+    static bool set = false;   // per instantiation
+    if (!set) {
+        cudaFuncSetAttribute(tc_f16_kernel<CFG, BLOCKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             CFG::SMEM_BYTES);
+        set = true;
+    }
+    tc_f16_kernel<CFG, BLOCKED><<<grid, NTHREADS, CFG::SMEM_BYTES, s>>>(ma, mb, g);
 }
 
-// workspace: [status word, 256 B][A16: mp x kp fp16][B16: np x kp fp16]
-size_t tc_f16_workspace(int64_t m, int64_t k, int64_t n) {
-    const int64_t kp = round_up(k > 0 ? k : 1, BK);
-    return 256 + (size_t)(round_up(m, BM) + round_up(n, BN)) * (size_t)kp * 2;
+// Tile width: 256 columns when those tiles fill the GPU, else 128.
+int pick_bn(int64_t m, int64_t n) {
+    const int64_t t256 = ((m + BM - 1) / BM) * ((n + 255) / 256);
+    return t256 >= num_sms() ? 256 : 128;
 }
 
-gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
-                         const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,
-                         size_t ws_bytes, cudaStream_t s) {
-    const int64_t kp = round_up(k, BK), mp = round_up(m, BM), np = round_up(n, BN);
-    if (tc_f16_workspace(m, k, n) > ws_bytes) return GFP_EWORKSPACE;
-    if (mp / BM > (int64_t)1 << 30 || np / BN > (int64_t)1 << 30 || kp / BK > (int64_t)1 << 30)
+gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
+                     const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws, size_t ws_bytes,
+                     cudaStream_t s, bool fp8) {
+    const int es = fp8 ? 1 : 2;
+    const int bke = ROWB / es;
+    const int bn = pick_bn(m, n);
+    const int64_t kp = round_up(k, bke), mp = round_up(m, BM), np = round_up(n, 256);
+    if (256 + (size_t)(mp + np) * (size_t)kp * es > ws_bytes) return GFP_EWORKSPACE;
+    if (mp / BM > (int64_t)1 << 30 || np / bn > (int64_t)1 << 30 || kp / bke > (int64_t)1 << 30)
         return GFP_EINVAL;
     int *status = static_cast<int *>(ws);
-    __half *A16 = reinterpret_cast<__half *>(static_cast<uint8_t *>(ws) + 256);
-    __half *B16 = A16 + mp * kp;
+    uint8_t *Aop = static_cast<uint8_t *>(ws) + 256;
+    uint8_t *Bop = Aop + mp * kp * es;
     const uint32_t h = p == 2 ? 1u : (p - 1) / 2;
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e);
     {
-        dim3 grid((unsigned)((kp / 8 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
-        to_f16_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, A16, kp, mp, p, h);
+        dim3 grid((unsigned)((kp / 16 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
         dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64));
-        to_f16_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, B16, kp, np, p, h);
+        if (fp8) {
+            to_op_rows_kernel<true><<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, p, h);
+            to_op_transpose_kernel<true><<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
+        } else {
+            to_op_rows_kernel<false><<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, p, h);
+            to_op_transpose_kernel<false><<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
+        }
     }
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A16, mp, kp, BM) || !make_map(&mb, B16, np, kp, BN)) return GFP_EUNSUPPORTED;
+    if (!make_map(&ma, Aop, mp, kp, BM, fp8) || !make_map(&mb, Bop, np, kp, bn, fp8)) return GFP_EUNSUPPORTED;
     TcArgs g;
     g.C = C;
     g.ldc = ldc;
     g.m = m;
     g.n = n;
     g.tiles_m = (int)(mp / BM);
-    g.tiles_n = (int)(np / BN);
-    g.ktiles = (int)(kp / BK);
-    g.kb_tiles = (int)(tc_kblock_f32(p) / BK);
+    g.tiles_n = (int)((n + bn - 1) / bn);
+    g.ktiles = (int)(kp / bke);
+    g.kb_tiles = (int)(tc_kblock_f32(p) / bke);
+    if (g.kb_tiles < 1) g.kb_tiles = 1;
     g.kblocks = (g.ktiles + g.kb_tiles - 1) / g.kb_tiles;
     g.p = p;
     g.off = (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);
@@ -523,22 +592,49 @@ gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint
     g.status = status;
     const int tiles = g.tiles_m * g.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();
-    if (g.kblocks > 1) {
-        static bool set = false;
-        if (!set) {
-            cudaFuncSetAttribute(tc_f16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-            set = true;
-        }
-        tc_f16_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, g);
+    const bool blk = g.kblocks > 1;
+    if (fp8) {
+        if (bn == 256) blk ? launch_cfg<TcCfg<256, true>, true>(ma, mb, g, grid, s) : launch_cfg<TcCfg<256, true>, false>(ma, mb, g, grid, s);
+        else blk ? launch_cfg<TcCfg<128, true>, true>(ma, mb, g, grid, s) : launch_cfg<TcCfg<128, true>, false>(ma, mb, g, grid, s);
     } else {
-        static bool set = false;
-        if (!set) {
-            cudaFuncSetAttribute(tc_f16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-            set = true;
-        }
-        tc_f16_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, g);
+        if (bn == 256) blk ? launch_cfg<TcCfg<256, false>, true>(ma, mb, g, grid, s) : launch_cfg<TcCfg<256, false>, false>(ma, mb, g, grid, s);
+        else blk ? launch_cfg<TcCfg<128, false>, true>(ma, mb, g, grid, s) : launch_cfg<TcCfg<128, false>, false>(ma, mb, g, grid, s);
     }
     return check_launch();
+}
+
+}  // namespace
+
+// largest multiple of 128 with kb h^2 + p < 2^24 (one fp32-exact k-block)
+int64_t tc_kblock_f32(uint32_t p) {
+    const int64_t h = p == 2 ? 1 : (p - 1) / 2;
+    const int64_t kb = ((int64_t(1) << 24) - 1 - p) / (h * h);
+    return kb / 128 * 128;
+}
+
+// workspace: [status word, 256 B][A operand: mp x kp][B^T operand: np x kp],
+// fp16 (2 bytes) or e4m3 (1 byte) values, mp, np, kp rounded to the tiles
+size_t tc_f16_workspace(int64_t m, int64_t k, int64_t n) {
+    const int64_t kp = round_up(k > 0 ? k : 1, 64);
+    return 256 + (size_t)(round_up(m, BM) + round_up(n, 256)) * (size_t)kp * 2;
+}
+
+size_t tc_f8_workspace(int64_t m, int64_t k, int64_t n) {
+    const int64_t kp = round_up(k > 0 ? k : 1, 128);
+    return 256 + (size_t)(round_up(m, BM) + round_up(n, 256)) * (size_t)kp;
+}
+
+gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
+                         const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,
+                         size_t ws_bytes, cudaStream_t s) {
+    return launch_tc(p, m, k, n, A, lda, B, ldb, C, ldc, ws, ws_bytes, s, false);
+}
+
+gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
+                        const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,
+                        size_t ws_bytes, cudaStream_t s) {
+    if (p > 31) return GFP_EUNSUPPORTED;   // |c| <= 15 is what e4m3 holds exactly
+    return launch_tc(p, m, k, n, A, lda, B, ldb, C, ldc, ws, ws_bytes, s, true);
 }
 
 }  // namespace gfp

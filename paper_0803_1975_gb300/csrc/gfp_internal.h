@@ -50,6 +50,17 @@ gfp_status launch_mixed(uint32_t p, int64_t m, int64_t k, int64_t nc, int d, int
                         const uint8_t *A, int64_t lda, const void *CB, int64_t ldb, void *CC,
                         int64_t ldc, cudaStream_t s);
 
+gfp_status launch_left(uint32_t p, int64_t mc, int64_t k, int64_t n, int d, int t, gfp_word word,
+                       const void *CA, int64_t lda, const uint8_t *B, int64_t ldb, void *CC,
+                       int64_t ldc, cudaStream_t s);
+gfp_status launch_full(uint32_t p, int64_t mc, int64_t k, int64_t nc, int dq, int dth, int t,
+                       gfp_word word, const void *CA, int64_t lda, const void *CB, int64_t ldb,
+                       void *CC, int64_t ldc, cudaStream_t s);
+gfp_status launch_block(bool pack, int64_t rows, int64_t cols, const uint8_t *X, uint8_t *Xout,
+                        int64_t ldx, int dq, int dth, int t, gfp_word word, const void *Win, void *Wout,
+                        int64_t ldw, cudaStream_t s);
+gfp_status check_full(uint32_t p, int64_t k, int dq, int dth, uint64_t Q, gfp_word word);
+
 // tensor-core forms (gemm_tc_mma.cu, gemm_tc_tcgen05.cu)
 size_t tc_mma_workspace(int64_t m, int64_t k, int64_t n);
 gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
@@ -59,7 +70,11 @@ size_t tc_f16_workspace(int64_t m, int64_t k, int64_t n);
 gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
                          int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
                          void *ws, size_t ws_bytes, cudaStream_t s);
-int64_t tc_kblock_s32(uint32_t p);      // largest kb with kb ((p-1)/2)^2 < 2^31
-int64_t tc_kblock_f32(uint32_t p);      // largest kb (multiple of 64) with kb ((p-1)/2)^2 < 2^24
+size_t tc_f8_workspace(int64_t m, int64_t k, int64_t n);
+gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
+                        int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                        void *ws, size_t ws_bytes, cudaStream_t s);
+int64_t tc_kblock_s32(uint32_t p);      // largest kb with kb ((p-1)/2)^2 + p < 2^30
+int64_t tc_kblock_f32(uint32_t p);      // largest kb (multiple of 128) with kb ((p-1)/2)^2 + p < 2^24
 
 }  // namespace gfp

@@ -104,6 +104,48 @@ __global__ void unpack_cols_kernel(const W *__restrict__ Win, int64_t ldw, int64
     }
 }
 
+// Section 4 result layout: W[u][v] = sum_i sum_j X[u(dq+1)+i][v(dth+1)+j]
+// Q^(i + j(dq+1)); thread per word (u, v).
+template <class W>
+__global__ void pack_block_kernel(const uint8_t *__restrict__ X, int64_t ldx, int64_t rows,
+                                  int64_t cols, int dq1, int dth1, int t, W *__restrict__ out,
+                                  int64_t ldw, int64_t wcols, int64_t wrows) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= wcols) return;
+    for (int64_t u = blockIdx.y; u < wrows; u += gridDim.y) {
+        uint64_t acc = 0;
+        for (int i = 0; i < dq1; ++i) {
+            const int64_t r = u * dq1 + i;
+            if (r >= rows) break;
+            for (int j = 0; j < dth1; ++j) {
+                const int64_t c = v * dth1 + j;
+                if (c < cols) acc += (uint64_t)X[r * ldx + c] << (t * (i + j * dq1));
+            }
+        }
+        out[u * ldw + v] = to_word<W>(acc);
+    }
+}
+
+template <class W>
+__global__ void unpack_block_kernel(const W *__restrict__ Win, int64_t ldw, int64_t rows,
+                                    int64_t cols, int dq1, int dth1, int t, uint8_t *__restrict__ X,
+                                    int64_t ldx, int64_t wcols, int64_t wrows) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= wcols) return;
+    const uint64_t mask = (1ull << t) - 1;
+    for (int64_t u = blockIdx.y; u < wrows; u += gridDim.y) {
+        const uint64_t w = from_word<W>(Win[u * ldw + v]);
+        for (int i = 0; i < dq1; ++i) {
+            const int64_t r = u * dq1 + i;
+            if (r >= rows) break;
+            for (int j = 0; j < dth1; ++j) {
+                const int64_t c = v * dth1 + j;
+                if (c < cols) X[r * ldx + c] = (uint8_t)((w >> (t * (i + j * dq1))) & mask);
+            }
+        }
+    }
+}
+
 constexpr int kThreads = 256;
 
 dim3 grid_for(int64_t inner, int64_t outer) {
@@ -177,6 +219,35 @@ gfp_status launch_unpack(int64_t rows, int64_t cols, const void *W, int64_t ldw,
     else
         e = unpack_t<uint32_t>(rows, cols, W, ldw, d + 1, t, lay, X, ldx, s);
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+}
+
+}  // namespace gfp
+
+namespace gfp {
+
+gfp_status launch_block(bool pack, int64_t rows, int64_t cols, const uint8_t *X, uint8_t *Xout,
+                        int64_t ldx, int dq, int dth, int t, gfp_word word, const void *Win, void *Wout,
+                        int64_t ldw, cudaStream_t s) {
+    const int64_t wr = (rows + dq) / (dq + 1), wc = (cols + dth) / (dth + 1);
+    const dim3 grid = grid_for(wc, wr);
+    if (word == GFP_WORD_F64) {
+        if (pack)
+            pack_block_kernel<double><<<grid, kThreads, 0, s>>>(X, ldx, rows, cols, dq + 1, dth + 1, t,
+                                                                static_cast<double *>(Wout), ldw, wc, wr);
+        else
+            unpack_block_kernel<double><<<grid, kThreads, 0, s>>>(static_cast<const double *>(Win), ldw,
+                                                                  rows, cols, dq + 1, dth + 1, t, Xout,
+                                                                  ldx, wc, wr);
+    } else {
+        if (pack)
+            pack_block_kernel<uint64_t><<<grid, kThreads, 0, s>>>(X, ldx, rows, cols, dq + 1, dth + 1, t,
+                                                                  static_cast<uint64_t *>(Wout), ldw, wc, wr);
+        else
+            unpack_block_kernel<uint64_t><<<grid, kThreads, 0, s>>>(static_cast<const uint64_t *>(Win),
+                                                                    ldw, rows, cols, dq + 1, dth + 1, t,
+                                                                    Xout, ldx, wc, wr);
+    }
+    return check_launch();
 }
 
 }  // namespace gfp

@@ -10,6 +10,7 @@
 //    64-bit accumulator, <= 32 for a 32-bit one, <= 128 for 128 bits) and
 //    the packed words fit their storage.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "gfp_internal.h"
@@ -86,9 +87,9 @@ gfp_status check_dqt(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gf
     int t = log2_exact(Q);
     if (t < 0) return GFP_EQ;
     if (k < 0 || d < 0 || d > 255 || kb < 0) return GFP_EINVAL;
-    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED) return GFP_EINVAL;
+    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED && form != GFP_FORM_LEFT) return GFP_EINVAL;
     if (word_bytes(word) == 0) return GFP_EINVAL;
-    if (form == GFP_FORM_MIXED && word != GFP_WORD_U64 && word != GFP_WORD_F64)
+    if (form != GFP_FORM_DOT && word != GFP_WORD_U64 && word != GFP_WORD_F64)
         return GFP_EUNSUPPORTED;
     const bool blocked = kb > 0 && kb < k;
     if (kb > 0) {
@@ -121,9 +122,27 @@ gfp_status check_dqt(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gf
                 break;
         }
     } else {
+        // right (MIXED) and left compression: every coefficient of a result
+        // word is a full dot product < Q, so the word is below Q^(d+1)
         if (word == GFP_WORD_U64 && td1 > 64) return GFP_EBOUND;
         if (word == GFP_WORD_F64 && td1 > 52) return GFP_EBOUND;
     }
+    return GFP_OK;
+}
+
+// Section 4 with Theta = Q^(dq+1): eq. (lower) for Q, and the whole word, with
+// (dq+1)(dth+1) coefficients below Q, inside the word (eq. dq with beta = 64
+// for uint64 words, 53 for binary64).
+gfp_status check_full(uint32_t p, int64_t k, int dq, int dth, uint64_t Q, gfp_word word) {
+    if (!is_prime_small(p)) return GFP_EPRIME;
+    const int t = log2_exact(Q);
+    if (t < 0) return GFP_EQ;
+    if (k < 0 || dq < 0 || dth < 0 || dq > 63 || dth > 63) return GFP_EINVAL;
+    if (word != GFP_WORD_U64 && word != GFP_WORD_F64) return GFP_EUNSUPPORTED;
+    if (!lower_ok(p, k, t)) return GFP_EBOUND;
+    const int64_t bits = (int64_t)t * (dq + 1) * (dth + 1);
+    if (word == GFP_WORD_U64 && bits > 64) return GFP_EBOUND;
+    if (word == GFP_WORD_F64 && bits > 52) return GFP_EBOUND;
     return GFP_OK;
 }
 
@@ -153,10 +172,11 @@ GFP_API gfp_status gfp_params(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_f
                               gfp_word word, int *d, uint64_t *Q, int64_t *kb) {
     if (!d || !Q || !kb) return GFP_EINVAL;
     if (m < 0 || k < 0 || n < 0) return GFP_EINVAL;
-    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED) return GFP_EINVAL;
+    if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED && form != GFP_FORM_LEFT) return GFP_EINVAL;
     if (word_bytes(word) == 0) return GFP_EINVAL;
     if (!is_prime_small(p)) return GFP_EPRIME;
     if (*d >= 0) return check_dqt(p, k, *d, *Q, form, word, *kb);
+    if (form != GFP_FORM_DOT && *kb > 0) return GFP_EUNSUPPORTED;
     // choose
     const int64_t kreq = (*kb > 0 && *kb < k) ? *kb : k;
     int t = 1;
@@ -173,12 +193,41 @@ GFP_API gfp_status gfp_params(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_f
         }
         if (check_dqt(p, k, dd, QQ, form, word, kbb) == GFP_OK) best = dd;
     }
-    if (best < 0) return form == GFP_FORM_MIXED && word != GFP_WORD_U64 && word != GFP_WORD_F64
+    if (best < 0) return form != GFP_FORM_DOT && word != GFP_WORD_U64 && word != GFP_WORD_F64
                              ? GFP_EUNSUPPORTED
                              : GFP_EBOUND;
     *d = best;
     *Q = QQ;
     *kb = (*kb > 0 && *kb < k) ? (*kb / (best + 1)) * (best + 1) : 0;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_params_full(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_word word,
+                                   int *dq, int *dth, uint64_t *Q) {
+    if (!dq || !dth || !Q || m < 0 || k < 0 || n < 0) return GFP_EINVAL;
+    if (!is_prime_small(p)) return GFP_EPRIME;
+    if (word != GFP_WORD_U64 && word != GFP_WORD_F64) return GFP_EUNSUPPORTED;
+    if (*dq >= 0) return check_full(p, k, *dq, *dth, *Q, word);
+    int t = 1;
+    while (!lower_ok(p, k > 0 ? k : 1, t) || (uint64_t)(p - 1) >= (1ull << t)) {
+        if (++t > 62) return GFP_EBOUND;
+    }
+    // the most coefficients per word, then the most balanced split (Section 5
+    // compares full compression at equal degrees in both variables)
+    int bq = -1, bt = -1;
+    for (int a = 0; a < 64; ++a)
+        for (int b = 0; b < 64; ++b) {
+            if (check_full(p, k, a, b, 1ull << t, word) != GFP_OK) continue;
+            const int cur = (a + 1) * (b + 1), best = (bq + 1) * (bt + 1);
+            if (bq < 0 || cur > best || (cur == best && std::abs(a - b) < std::abs(bq - bt))) {
+                bq = a;
+                bt = b;
+            }
+        }
+    if (bq < 0) return GFP_EBOUND;
+    *dq = bq;
+    *dth = bt;
+    *Q = 1ull << t;
     return GFP_OK;
 }
 

@@ -18,6 +18,8 @@
 //   kBlocked when true, P::extract(acc) is called every prm.kbw steps of k
 //            and its results are summed in a 32-bit register per entry; the
 //            accumulator restarts from zero after each block.
+//   kAtomic  when true the result is added atomically to C (split-k slices
+//            of a linear accumulator; the caller zeroes C and finishes it).
 #pragma once
 
 #include <cstdint>
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
                  const typename P::GB *__restrict__ B, int64_t ldb,
                  typename P::GC *__restrict__ C, int64_t ldc,
-                 int64_t M, int64_t N, int64_t K, typename P::Params prm) {
+                 int64_t M, int64_t N, int64_t K, typename P::Params prm, int64_t kchunk) {
     constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
     constexpr int HM = TM / 2, HN = TN / 2;
     static_assert(TM % 2 == 0 && TN % 2 == 0, "rows and columns come in two halves");
@@ -84,6 +86,10 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
     const int tx = tid % NTX, ty = tid / NTX;
     const int64_t m0 = (int64_t)blockIdx.y * BM;
     const int64_t n0 = (int64_t)blockIdx.x * BN;
+    // split k: slice z of the grid covers [kz0, kz1); the slices' raw sums
+    // are added atomically (policies with kAtomic only)
+    const int64_t kz0 = kchunk > 0 ? (int64_t)blockIdx.z * kchunk : 0;
+    const int64_t kz1 = kchunk > 0 ? (kz0 + kchunk < K ? kz0 + kchunk : K) : K;
 
     constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
     SA ra[LA];
@@ -95,14 +101,14 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
             const int idx = tid + e * NT;
             const int r = idx / BK, c = idx % BK;
             const int64_t gi = m0 + r, gk = k0 + c;
-            ra[e] = P::ldA(A, lda, gi, gk, M, K, prm);
+            ra[e] = P::ldA(A, lda, gi, gk, M, kz1, prm);
         }
 #pragma unroll
         for (int e = 0; e < LB; ++e) {
             const int idx = tid + e * NT;
             const int r = idx / BN, c = idx % BN;
             const int64_t gk = k0 + r, gj = n0 + c;
-            rb[e] = P::ldB(B, ldb, gk, gj, K, N, prm);
+            rb[e] = P::ldB(B, ldb, gk, gj, kz1, N, prm);
         }
     };
     auto store = [&](int buf) {
@@ -132,12 +138,12 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
     }
     int64_t countdown = P::kBlocked ? prm.kbw : 0;
 
-    load(0);
+    load(kz0);
     store(0);
     __syncthreads();
     int buf = 0;
-    for (int64_t k0 = 0; k0 < K; k0 += BK) {
-        const bool more = k0 + BK < K;
+    for (int64_t k0 = kz0; k0 < kz1; k0 += BK) {
+        const bool more = k0 + BK < kz1;
         if (more) load(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
@@ -181,7 +187,8 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
             if (gj < N) {
                 uint32_t s = 0;
                 if constexpr (P::kBlocked) s = sum[i][j];
-                C[gi * ldc + gj] = P::finish(acc[i][j], s, prm);
+                if constexpr (P::kAtomic) atomicAdd(&C[gi * ldc + gj], P::finish(acc[i][j], s, prm));
+                else C[gi * ldc + gj] = P::finish(acc[i][j], s, prm);
             }
         }
     }
@@ -190,13 +197,17 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
 template <class P, int BM, int BN, int BK, int TM, int TN>
 cudaError_t simt_gemm_launch(const typename P::GA *A, int64_t lda, const typename P::GB *B,
                              int64_t ldb, typename P::GC *C, int64_t ldc, int64_t M, int64_t N,
-                             int64_t K, const typename P::Params &prm, cudaStream_t s) {
+                             int64_t K, const typename P::Params &prm, cudaStream_t s,
+                             int splits = 1) {
     constexpr int NT = (BM / TM) * (BN / TN);
     const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
     if (gx <= 0 || gy <= 0) return cudaSuccess;
-    if (gy > 65535 || gx > 2147483647) return cudaErrorInvalidConfiguration;
+    if (gy > 65535 || gx > 2147483647 || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
+    int64_t kchunk = 0;
+    if (splits > 1) kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    const unsigned gz = kchunk > 0 ? (unsigned)((K + kchunk - 1) / kchunk) : 1u;
     simt_gemm_kernel<P, BM, BN, BK, TM, TN>
-        <<<dim3((unsigned)gx, (unsigned)gy), NT, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, prm);
+        <<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, prm, kchunk);
     return cudaGetLastError();
 }
 

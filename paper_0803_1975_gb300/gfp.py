@@ -22,10 +22,10 @@ _lib = None
 
 STATUS = {0: "GFP_OK", 1: "GFP_EINVAL", 2: "GFP_EPRIME", 3: "GFP_EBOUND", 4: "GFP_EQ",
           5: "GFP_EUNSUPPORTED", 6: "GFP_ECUDA", 7: "GFP_EWORKSPACE"}
-FORMS = {"dot": 0, "mixed": 1}
+FORMS = {"dot": 0, "mixed": 1, "left": 2}
 WORDS = {"u64": 0, "u64x128": 1, "u32w": 2, "u32": 3, "f64": 4}
 LAYOUTS = {"rows_rev": 0, "cols": 1, "rows": 2}
-ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4, "dot32": 5}
+ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4, "dot32": 5, "tc_f8": 6}
 BATCHED_KINDS = {0: "hmma64", 1: "hmma32", 2: "dot32"}
 WORD_DTYPE = {"u64": torch.int64, "u64x128": torch.int64, "u32w": torch.int32, "u32": torch.int32,
               "f64": torch.float64}
@@ -35,7 +35,8 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_unpack", "gfp_gemm_workspace_size", "gfp_gemm", "gfp_gemm_compressed",
            "gfp_batched_workspace_size", "gfp_gemm_batched", "gfp_batched_prepare",
            "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table",
-           "gfp_gemm_noalloc")
+           "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
+           "gfp_unpack_block")
 
 
 class GfpError(RuntimeError):
@@ -91,6 +92,15 @@ def load():
     L.gfp_gemm_compressed.argtypes = [u32, i64, i64, i64, ip, u64, ip, ip, vp, i64, vp, i64, vp, i64,
                                       i64, vp]
     L.gfp_gemm_compressed.restype = st
+    L.gfp_gemm_full.argtypes = [u32, i64, i64, i64, ip, ip, u64, ip, vp, i64, vp, i64, vp, i64, vp]
+    L.gfp_gemm_full.restype = st
+    L.gfp_params_full.argtypes = [u32, i64, i64, i64, ip, ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                  ctypes.POINTER(u64)]
+    L.gfp_params_full.restype = st
+    for name in ("gfp_pack_block", "gfp_unpack_block"):
+        f = getattr(L, name)
+        f.argtypes = [u32, i64, i64, vp, i64, ip, ip, u64, ip, vp, i64, vp]
+        f.restype = st
     L.gfp_gemm_noalloc.argtypes = [u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp]
     L.gfp_gemm_noalloc.restype = st
     L.gfp_batched_workspace_size.argtypes = [i64, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
@@ -210,6 +220,60 @@ def gfp_gemm(p: int, A: torch.Tensor, B: torch.Tensor, algo: str = "auto",
     return out
 
 
+def gfp_params_full(p: int, m: int, k: int, n: int, word: str = "u64", dq: int | None = None,
+                    dth: int = 0, Q: int = 0):
+    """Choose (dq is None) or validate the (dq, dth, Q) of full compression."""
+    L = load()
+    a = ctypes.c_int(-1 if dq is None else dq)
+    b = ctypes.c_int(dth)
+    q = ctypes.c_uint64(Q)
+    _check(L.gfp_params_full(p, m, k, n, WORDS[word], ctypes.byref(a), ctypes.byref(b), ctypes.byref(q)),
+           "gfp_params_full")
+    return a.value, b.value, q.value
+
+
+def gfp_pack_block(p: int, X: torch.Tensor, dq: int, dth: int, Q: int, word: str = "u64",
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    L = load()
+    rows, cols = X.shape
+    if out is None:
+        out = torch.empty((cdiv(rows, dq + 1), cdiv(cols, dth + 1)), dtype=WORD_DTYPE[word], device=X.device)
+    xp, ldx = _mat(X, torch.uint8, "X")
+    wp, ldw = _mat(out, WORD_DTYPE[word], "W")
+    _check(L.gfp_pack_block(p, rows, cols, xp, ldx, dq, dth, Q, WORDS[word], wp, ldw, _stream(X, stream)),
+           "gfp_pack_block")
+    return out
+
+
+def gfp_unpack_block(p: int, W: torch.Tensor, rows: int, cols: int, dq: int, dth: int, Q: int,
+                     word: str = "u64", out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    L = load()
+    if out is None:
+        out = torch.empty((rows, cols), dtype=torch.uint8, device=W.device)
+    wp, ldw = _mat(W, WORD_DTYPE[word], "W")
+    xp, ldx = _mat(out, torch.uint8, "X")
+    _check(L.gfp_unpack_block(p, rows, cols, wp, ldw, dq, dth, Q, WORDS[word], xp, ldx, _stream(W, stream)),
+           "gfp_unpack_block")
+    return out
+
+
+def gfp_gemm_full(p: int, m: int, k: int, n: int, dq: int, dth: int, Q: int, word: str,
+                  CA: torch.Tensor, CB: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Section 4: CA (COLS of A, base Q) x CB (ROWS of B, base Q^(dq+1)) -> CC
+    words in the block layout."""
+    L = load()
+    wdt = WORD_DTYPE[word]
+    if out is None:
+        out = torch.empty((cdiv(m, dq + 1), cdiv(n, dth + 1)), dtype=wdt, device=CB.device)
+    ap, lda = _mat(CA, wdt, "CA")
+    bp, ldb = _mat(CB, wdt, "CB")
+    cp, ldc = _mat(out, wdt, "CC")
+    _check(L.gfp_gemm_full(p, m, k, n, dq, dth, Q, WORDS[word], ap, lda, bp, ldb, cp, ldc,
+                           _stream(CB, stream)), "gfp_gemm_full")
+    return out
+
+
 def gfp_gemm_noalloc(p: int, A: torch.Tensor, B: torch.Tensor, out: torch.Tensor | None = None,
                      stream=None) -> torch.Tensor:
     """gfp_gemm(..., 'tc_mma_s8') without a workspace, for callers that may not
@@ -224,7 +288,8 @@ def gfp_gemm_noalloc(p: int, A: torch.Tensor, B: torch.Tensor, out: torch.Tensor
     bp, ldb = _mat(B, torch.uint8, "B")
     cp, ldc = _mat(out, torch.uint8, "C")
     _check(L.gfp_gemm_noalloc(p, m, k, n, ap, lda, bp, ldb, cp, ldc, _stream(A, stream)),
-           "gfp_gemm_noalloc")
+           "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
+           "gfp_unpack_block")
     return out
 
 
@@ -240,6 +305,15 @@ def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: st
         if out is None:
             out = torch.empty((m, n), dtype=torch.uint8, device=CB.device)
         cp, ldc = _mat(out, torch.uint8, "C")
+    elif form == "left":
+        ap, lda = _mat(CA_or_A, wdt, "CA")
+        if out is None:
+            out = torch.empty((cdiv(m, d + 1), n), dtype=wdt, device=CB.device)
+        cp, ldc = _mat(out, wdt, "CC")
+        bp, ldb = _mat(CB, torch.uint8, "B")
+        _check(L.gfp_gemm_compressed(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
+                                     ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
+        return out
     else:
         ap, lda = _mat(CA_or_A, torch.uint8, "A")
         if out is None:

@@ -140,3 +140,34 @@ def test_workspace_sizes(L):
     assert gfp.gfp_gemm_workspace_size(3, 256, 256, 256, "plain") == 0
     ws = gfp.gfp_gemm_workspace_size(3, 100, 70, 200, "tc_mma_s8")
     assert ws >= (128 + 256) * 128
+
+
+def test_left_chooser_matches_oracle(L):
+    for word in oracle.WORDS_MIXED:
+        for p in (2, 3, 5, 31, 251):
+            for k in (1, 100, 1024, 16384):
+                assert gfp.gfp_params(p, 8, k, 8, "left", word)[:2] == oracle.choose("left", word, p, k)
+
+
+def test_full_params_match_oracle(L):
+    """gfp_params_full picks an admissible (dq, dth, Q) of Section 4 with the
+    most coefficients per word; validation agrees with the oracle's reading."""
+    for word in ("u64", "f64"):
+        for p in (2, 3, 5, 7, 31):
+            for k in (1, 64, 1024, 8192):
+                dq, dth, Q = gfp.gfp_params_full(p, 8, k, 8, word)
+                assert oracle.full_admissible(word, p, k, dq, dth, Q)
+                assert not oracle.lower_bound_holds(p, k, Q // 2) or Q == 2
+                best = max((a + 1) * (b + 1) for a in range(64) for b in range(64)
+                           if oracle.full_admissible(word, p, k, a, b, Q))
+                assert (dq + 1) * (dth + 1) == best
+                for a in range(5):
+                    for b in range(5):
+                        ok = oracle.full_admissible(word, p, k, a, b, Q)
+                        try:
+                            gfp.gfp_params_full(p, 8, k, 8, word, dq=a, dth=b, Q=Q)
+                            got = True
+                        except gfp.GfpError as e:
+                            assert e.status == 3
+                            got = False
+                        assert got == ok, (word, p, k, a, b)

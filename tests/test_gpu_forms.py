@@ -68,12 +68,21 @@ GEMM_CASES = [(3, 256, 256, 256), (3, 1024, 1024, 1024), (5, 129, 300, 77), (251
               (2, 65, 64, 63), (7, 1, 1, 1), (31, 3, 1000, 5), (13, 128, 17, 128), (3, 300, 1, 299)]
 
 
-ALGOS = ["plain", "dp4a", "tc_mma_s8", "tc_f16"]
+ALGOS = ["plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8"]
+
+
+def skip_unsupported(algo, p):
+    if algo == "tc_f8" and p > 31:
+        with pytest.raises(gfp.GfpError) as e:
+            gfp.gfp_gemm_workspace_size(p, 8, 8, 8, algo)
+        assert e.value.status == 5
+        pytest.skip("fp8 operands hold the centred residues of p <= 31 only")
 
 
 @pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("p,m,k,n", GEMM_CASES)
 def test_gemm_matches_oracle(algo, p, m, k, n):
+    skip_unsupported(algo, p)
     A, B = operands(2, 0, p, m, k, n)
     C = host(gfp.gfp_gemm(p, dev(A), dev(B), algo))
     assert (C == oracle_product(2, 0, p, m, k, n)).all()
@@ -84,6 +93,7 @@ def test_gemm_matches_oracle(algo, p, m, k, n):
 def test_gemm_worst_case(algo, p):
     """All entries p-1 (largest sums); for the centred form also the largest
     centred magnitude h = (p-1)/2 with both signs."""
+    skip_unsupported(algo, p)
     m = k = n = 192
     h = (p - 1) // 2
     for fill_a, fill_b in ((p - 1, p - 1), (h, h), (h + 1, h), (h + 1, h + 1)):
@@ -115,14 +125,15 @@ def tc_f16_status(ws: torch.Tensor) -> int:
     return int(ws[:4].cpu().numpy().view(np.int32)[0])
 
 
-@pytest.mark.parametrize("p", [3, 31, 251])
-def test_tc_f16_exact_accumulation(p):
+@pytest.mark.parametrize("algo,p", [("tc_f16", 3), ("tc_f16", 31), ("tc_f16", 251), ("tc_f8", 3),
+                                    ("tc_f8", 31)])
+def test_tc_exact_accumulation(algo, p):
     """fp32 accumulation in tensor memory is exact while partial sums are
     integers below 2^24.  Patterns at the k-block bound kb: all products +h^2
     (partial sums reach kb h^2), alternating signs, a large accumulator
     followed by small addends, and one k-block past the bound (blocked path)."""
     h = (p - 1) // 2
-    kb = ((1 << 24) - 1 - p) // (h * h) // 64 * 64
+    kb = ((1 << 24) - 1 - p) // (h * h) // 128 * 128
     k = min(kb, 80000)                        # p = 31: 74560, p = 251: 1024
     m, n = 128, 256
     pos, neg = h, h + 1                       # residues whose centred values are +h, -h
@@ -136,9 +147,9 @@ def test_tc_f16_exact_accumulation(p):
     big_then_small[:, k // 2:] = 1
     pats["big-then-small"] = (big_then_small, np.full((k, n), pos, np.uint8))
     for name, (A, B) in pats.items():
-        ws = torch.empty(gfp.gfp_gemm_workspace_size(p, m, k, n, "tc_f16"), dtype=torch.uint8,
+        ws = torch.empty(gfp.gfp_gemm_workspace_size(p, m, k, n, algo), dtype=torch.uint8,
                          device="cuda")
-        C = host(gfp.gfp_gemm(p, dev(A), dev(B), "tc_f16", workspace=ws))
+        C = host(gfp.gfp_gemm(p, dev(A), dev(B), algo, workspace=ws))
         assert tc_f16_status(ws) == 0
         assert (C == oracle.gemm(p, A[:2], B)[0]).all(), name   # rows are identical
 
@@ -274,3 +285,60 @@ def test_mixed_worst_case(word):
     CC = gfp.gfp_gemm_compressed(p, 40, k, 50, d, Q, "mixed", word, dev(A), CB)
     C = host(gfp.gfp_unpack(p, CC, 40, 50, d, Q, "rows", word))
     assert (C == (k * 4) % 3).all()
+
+
+# ------------------------------------------------------ left / full compression
+LEFT_CASES = [(3, 1024, 1024, 1024), (3, 77, 300, 101), (5, 64, 200, 64), (251, 41, 30, 20),
+              (2, 67, 129, 65)]
+
+
+@pytest.mark.parametrize("word", ["u64", "f64"])
+@pytest.mark.parametrize("p,m,k,n", LEFT_CASES)
+def test_left_matches_oracle(word, p, m, k, n):
+    """Table 2 left compression: A packed along m (COLS) times uncompressed B;
+    the result words are the COLS packing of A B mod p."""
+    d, Q, _ = gfp.gfp_params(p, m, k, n, "left", word)
+    A, B = operands(2, 3, p, m, k, n)
+    CA = gfp.gfp_pack(p, dev(A), d, Q, "cols", word)
+    CC = gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "left", word, CA, dev(B))
+    ref = oracle_product(2, 3, p, m, k, n)
+    want = oracle.pack_cols(ref, d, Q, dtype=np.uint64)
+    got = words_np(CC, word)
+    assert (got == (want.astype(np.float64) if word == "f64" else want)).all()
+    assert (host(gfp.gfp_unpack(p, CC, m, n, d, Q, "cols", word)) == ref).all()
+
+
+FULL_CASES = [(3, 1024, 1024, 1024), (3, 77, 300, 101), (5, 64, 200, 64), (7, 33, 40, 17),
+              (2, 65, 129, 67)]
+
+
+@pytest.mark.parametrize("word", ["u64", "f64"])
+@pytest.mark.parametrize("p,m,k,n", FULL_CASES)
+def test_full_matches_oracle(word, p, m, k, n):
+    """Section 4: A packed along m in base Q, B along n in base Theta =
+    Q^(dq+1); every result word is the block packing of A B mod p."""
+    dq, dth, Q = gfp.gfp_params_full(p, m, k, n, word)
+    Theta = Q ** (dq + 1)
+    A, B = operands(2, 4, p, m, k, n)
+    CA = gfp.gfp_pack(p, dev(A), dq, Q, "cols", word)
+    CB = gfp.gfp_pack(p, dev(B), dth, Theta, "rows", word)
+    CC = gfp.gfp_gemm_full(p, m, k, n, dq, dth, Q, word, CA, CB)
+    ref = oracle_product(2, 4, p, m, k, n)
+    want = oracle.pack_block(ref, dq, dth, Q)
+    got = words_np(CC, word)
+    assert (got == (want.astype(np.float64) if word == "f64" else want)).all()
+    assert (host(gfp.gfp_unpack_block(p, CC, m, n, dq, dth, Q, word)) == ref).all()
+    # the block layout written directly from the residues agrees
+    assert (words_np(gfp.gfp_pack_block(p, dev(ref), dq, dth, Q, word), word) == got).all()
+
+
+@pytest.mark.parametrize("word", ["u64", "f64"])
+def test_full_worst_case(word):
+    p, k = 3, 2047
+    dq, dth, Q = gfp.gfp_params_full(p, 8, k, 8, word)
+    A = np.full((30, k), 2, np.uint8)
+    B = np.full((k, 40), 2, np.uint8)
+    CA = gfp.gfp_pack(p, dev(A), dq, Q, "cols", word)
+    CB = gfp.gfp_pack(p, dev(B), dth, Q ** (dq + 1), "rows", word)
+    CC = gfp.gfp_gemm_full(p, 30, k, 40, dq, dth, Q, word, CA, CB)
+    assert (host(gfp.gfp_unpack_block(p, CC, 30, 40, dq, dth, Q, word)) == (k * 4) % 3).all()

@@ -354,3 +354,53 @@ def test_round53_against_binary64():
         assert z <= x and int(float(z)) == z
         nxt = z + 1 if z < 2 ** 53 else int(math.nextafter(float(z), math.inf))
         assert nxt > x
+
+
+def test_full_block_layout_worked_example():
+    """Section 4: the 2x2 product packs into one word whose coefficients of
+    1, Q, Theta, Q Theta are the four entries of C; pack_block of C gives it."""
+    Q = 16
+    for env in _instances(3):
+        env.update(Q=Q, Theta=Q ** 2)
+        C = np.asarray(eval(EX["C"], {}, env), dtype=np.uint8)
+        FULL = eval(EX["FULL"], {}, env)
+        W = oracle.pack_block(C, 1, 1, Q)
+        assert W.shape == (1, 1) and int(W[0, 0]) == FULL
+        assert (oracle.unpack_block(W, 2, 2, 1, 1, Q) == C).all()
+
+
+@pytest.mark.parametrize("rows,cols,dq,dth,t", [(5, 7, 1, 2, 8), (4, 4, 0, 3, 10), (9, 3, 2, 0, 7),
+                                               (1, 1, 1, 1, 12)])
+def test_block_round_trip_and_special_cases(rows, cols, dq, dth, t):
+    """Round trip; dth = 0 is the COLS layout, dq = 0 the ROWS layout."""
+    Q = 2 ** t
+    g = inputs.rng(99, rows * cols)
+    X = inputs.residues(g, 5, rows, cols)
+    W = oracle.pack_block(X, dq, dth, Q)
+    assert (oracle.unpack_block(W, rows, cols, dq, dth, Q) == X).all()
+    if dth == 0:
+        assert (W == oracle.pack_cols(X, dq, Q)).all()
+    if dq == 0:
+        assert (W == oracle.pack_rows(X, dth, Q)).all()
+
+
+def test_full_word_product_equals_block_of_C():
+    """Section 4 on random data: sum_l (sum_i a_il Q^i)(sum_j b_lj Theta^j)
+    equals pack_block(A B) when every coefficient stays below Q."""
+    p, dq, dth, t = 3, 1, 2, 10
+    Q = 2 ** t
+    Theta = Q ** (dq + 1)
+    g = inputs.rng(98, 7)
+    A = inputs.residues(g, p, 4, 200)
+    B = inputs.residues(g, p, 200, 6)
+    assert oracle.full_admissible("u64", p, 200, dq, dth, Q)
+    Aw = oracle.pack_cols(A, dq, Q)          # words along m
+    Bw = oracle.pack_rows(B, dth, Theta)     # words along n, base Theta
+    exact = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.uint64)
+    want = oracle.pack_block(exact.astype(np.uint8) if exact.max() < 256 else exact, dq, dth, Q)
+    for u in range(Aw.shape[0]):
+        for v in range(Bw.shape[1]):
+            w = oracle.full_word(Aw[u], Bw[:, v], Q, Theta)
+            assert w == int(want[u, v])
+            assert w < 2 ** 64
+    assert not oracle.full_admissible("u64", p, 200, dq, dth + 1, Q)     # 10 * 2 * 4 = 80 bits
