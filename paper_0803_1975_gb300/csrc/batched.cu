@@ -6,15 +6,19 @@
 // kind, cut it into output tiles, and balance the tiles over a fixed grid of
 // CTAs by longest-processing-time-first (tiles sorted by cost, each to the
 // least loaded CTA).  The schedule -- problem table, tile list, per-CTA tile
-// ranges -- is copied into the caller's workspace with one host-to-device
-// copy.  gfp_batched_launch then launches one kernel that only reads the
-// workspace, so it can be captured in a CUDA graph and replayed.
+// ranges, operand-conversion jobs -- is copied into the caller's workspace
+// with one host-to-device copy.  gfp_batched_launch then runs, on the
+// prepared workspace only (so it can be captured in a CUDA graph):
+//   1. the operand conversion: every distinct (matrix, p) operand of a
+//      tensor-core tile becomes centred fp16, row-major, zero padded to
+//      multiples of 64 in both dimensions (A^2 problems convert A once);
+//   2. the one persistent grouped kernel over all tiles.
 //
 // Tile kinds (all 128 threads):
 //   HMMA64 / HMMA32 : 64 x 64 / 32 x 32 output tiles on the warp-level fp16
-//       tensor-core MMA (m16n8k16, fp32 accumulation).  Operands are centred
-//       residues converted to fp16 while staged in shared memory; every
-//       partial sum is an integer below 2^24 within a k-block kb with
+//       tensor-core MMA (m16n8k16, fp32 accumulation), operands streamed from
+//       the converted copies with 16-byte cp.async through a 3-stage ring.
+//       Every partial sum is an integer below 2^24 within a k-block kb with
 //       kb h^2 + p < 2^24 (h = (p-1)/2), after which the accumulators are
 //       reduced mod p.
 //   DOT32 : 64 x 64 tiles of the Q-adic dot form (Section 2) in 32-bit words:
@@ -28,7 +32,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -40,38 +46,56 @@ namespace {
 
 enum Kind : int32_t { KIND_HMMA64 = 0, KIND_HMMA32 = 1, KIND_DOT32 = 2, KIND_COUNT = 3 };
 
-struct DevProblem {          // 80 bytes
+struct DevProblem {          // 96 bytes
     const uint8_t *A;
     const uint8_t *B;
     uint8_t *C;
+    const __half *A16;       // converted operands of the tensor-core kinds
+    const __half *B16;
     int32_t m, k, n, lda, ldb, ldc;
+    int32_t ld16a, ld16b;    // leading dimensions of A16, B16 (fp16 elements)
     uint32_t p;
     int32_t kind;
     uint64_t M;              // fastmod magic
     int32_t kb_steps;        // HMMA: k-block in 32-wide k steps; DOT32: words per block
     uint16_t t, d;           // DOT32: Q = 2^t, d
-    int32_t pad[2];
 };
-static_assert(sizeof(DevProblem) == 80, "layout");
+static_assert(sizeof(DevProblem) == 96, "layout");
 
 struct Item {                // 8 bytes: problem index, tile row, tile column
     int32_t prob;
     uint16_t tm, tn;
 };
 
-struct Header {              // 64 bytes at the start of the workspace
+struct ConvJob {             // 48 bytes: one operand to convert
+    const uint8_t *src;
+    __half *dst;
+    int32_t rows, cols, ld, dld, drows;
+    uint32_t p;
+    int32_t pad[2];
+};
+static_assert(sizeof(ConvJob) == 48, "layout");
+
+struct ConvItem {            // 16 padded rows of one job
+    int32_t job, row0;
+};
+
+struct Header {              // 128 bytes at the start of the workspace
     uint32_t magic;
     int32_t count;
     int32_t items;
     int32_t grid;
-    int64_t off_probs, off_items, off_ranges;
+    int64_t off_probs, off_items, off_ranges, off_jobs, off_citems, off_ops;
     int64_t bytes;
-    int32_t pad[4];
+    int32_t njobs, ncitems;
+    int32_t pad[12];
 };
-static_assert(sizeof(Header) == 64, "layout");
+static_assert(sizeof(Header) == 128, "layout");
 constexpr uint32_t kMagic = 0x47465042u;   // "GFPB"
 constexpr int NT = 128;
 constexpr int CTAS_PER_SM = 4;
+constexpr int PADQ = 64;                   // padding quantum of converted operands
+constexpr int HSTAGES = 3;
 
 __device__ __forceinline__ uint32_t fmod32(uint32_t a, uint64_t M, uint32_t p) {
     return (uint32_t)__umul64hi(M * (uint64_t)a, (uint64_t)p);
@@ -81,25 +105,60 @@ __device__ __forceinline__ uint32_t s2u(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// ------------------------------------------------------- operand conversion
+// c = r - p [r > h] as fp16, zero outside the matrix, 8 values per thread-step.
+__global__ void __launch_bounds__(256) convert_kernel(const uint8_t *__restrict__ ws) {
+    const Header *H = reinterpret_cast<const Header *>(ws);
+    const ConvJob *jobs = reinterpret_cast<const ConvJob *>(ws + H->off_jobs);
+    const ConvItem *items = reinterpret_cast<const ConvItem *>(ws + H->off_citems);
+    for (int it = blockIdx.x; it < H->ncitems; it += gridDim.x) {
+        const ConvItem ci = items[it];
+        const ConvJob J = jobs[ci.job];
+        const uint32_t h = J.p == 2 ? 1u : (J.p - 1) / 2;
+        const int per_row = J.dld / 8;
+        for (int idx = threadIdx.x; idx < 16 * per_row; idx += blockDim.x) {
+            const int r = ci.row0 + idx / per_row, c = (idx % per_row) * 8;
+            if (r >= J.drows) break;
+            __align__(16) __half v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                int x = 0;
+                if (r < J.rows && c + e < J.cols) {
+                    const uint32_t q = J.src[(int64_t)r * J.ld + c + e];
+                    x = (int)q - (q > h ? (int)J.p : 0);
+                }
+                v[e] = __int2half_rn(x);
+            }
+            *reinterpret_cast<uint4 *>(J.dst + (int64_t)r * J.dld + c) = *reinterpret_cast<const uint4 *>(v);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- HMMA tiles
 template <int BT>
 struct HmmaSmem {
-    __half As[BT][32 + 8];   // [m][k], rows of 80 bytes (16-byte aligned, conflict-free ldmatrix)
-    __half Bs[32][BT + 8];   // [k][n]
+    __half As[HSTAGES][BT][32 + 8];   // [stage][m][k], 80-byte rows: 16-byte aligned, conflict-free ldmatrix
+    __half Bs[HSTAGES][32][BT + 8];   // [stage][k][n]
 };
 
-__device__ __forceinline__ __half centre_h(uint32_t r, uint32_t p, uint32_t h) {
-    return __int2half_rn((int)r - (r > h ? (int)p : 0));
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
 template <int BT>
 __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) {
     constexpr int MT = BT / 32, NTL = BT / 16;      // per-warp m16 and n8 tiles
+    constexpr int ACH = BT * 4, BCH = 32 * (BT / 8);  // 16-byte chunks per stage
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1;
     const int64_t m0 = (int64_t)tm * BT, n0 = (int64_t)tn * BT;
-    const uint32_t p = P.p, h = p == 2 ? 1u : (p - 1) / 2;
-    const int64_t K = P.k;
+    const uint32_t p = P.p;
+    const int nk = (P.k + 31) / 32;
     float acc[MT][NTL][4];
 #pragma unroll
     for (int a = 0; a < MT; ++a)
@@ -109,36 +168,29 @@ __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) 
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
     const uint32_t off = (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);
     int kb_left = P.kb_steps;
-    constexpr int AE = BT * 32 / NT;                 // A elements per thread (16 or 8)
-    for (int64_t k0 = 0; k0 < K; k0 += 32) {
-        // stage A (BT x 32) and B (32 x BT) as centred fp16
-        {
-            const int r = (tid * AE) / 32, c = (tid * AE) % 32;
-            const int64_t gi = m0 + r;
-            __align__(16) __half v[AE];
-#pragma unroll
-            for (int e = 0; e < AE; ++e) {
-                const int64_t gk = k0 + c + e;
-                v[e] = (gi < P.m && gk < K) ? centre_h(P.A[gi * P.lda + gk], p, h) : __int2half_rn(0);
-            }
-#pragma unroll
-            for (int e = 0; e < AE; e += 8)
-                *reinterpret_cast<uint4 *>(&S.As[r][c + e]) = *reinterpret_cast<uint4 *>(&v[e]);
+    // padded operands: no edge tests
+    auto load_stage = [&](int s, int kt) {
+        const int64_t k0 = (int64_t)kt * 32;
+        for (int c = tid; c < ACH; c += NT) {
+            const int row = c >> 2, ch = c & 3;
+            cp_async16(s2u(&S.As[s][row][ch * 8]), P.A16 + (m0 + row) * P.ld16a + k0 + ch * 8);
         }
-        {
-            const int r = (tid * AE) / BT, c = (tid * AE) % BT;
-            const int64_t gk = k0 + r;
-            __align__(16) __half v[AE];
-#pragma unroll
-            for (int e = 0; e < AE; ++e) {
-                const int64_t gj = n0 + c + e;
-                v[e] = (gk < K && gj < P.n) ? centre_h(P.B[gk * P.ldb + gj], p, h) : __int2half_rn(0);
-            }
-#pragma unroll
-            for (int e = 0; e < AE; e += 8)
-                *reinterpret_cast<uint4 *>(&S.Bs[r][c + e]) = *reinterpret_cast<uint4 *>(&v[e]);
+        for (int c = tid; c < BCH; c += NT) {
+            const int row = c / (BT / 8), ch = c % (BT / 8);
+            cp_async16(s2u(&S.Bs[s][row][ch * 8]), P.B16 + (k0 + row) * P.ld16b + n0 + ch * 8);
         }
+    };
+#pragma unroll
+    for (int s = 0; s < HSTAGES - 1; ++s) {
+        if (s < nk) load_stage(s, s);
+        cp_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_wait<HSTAGES - 2>();
         __syncthreads();
+        if (kt + HSTAGES - 1 < nk) load_stage((kt + HSTAGES - 1) % HSTAGES, kt + HSTAGES - 1);
+        cp_commit();
+        const int s = kt % HSTAGES;
 #pragma unroll
         for (int ks = 0; ks < 32; ks += 16) {
             uint32_t af[MT][4], bf[NTL][2];
@@ -148,7 +200,7 @@ __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) 
                 const int col = ks + (lane >> 4) * 8;
                 asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                              : "=r"(af[mt][0]), "=r"(af[mt][1]), "=r"(af[mt][2]), "=r"(af[mt][3])
-                             : "r"(s2u(&S.As[row][col])));
+                             : "r"(s2u(&S.As[s][row][col])));
             }
 #pragma unroll
             for (int np = 0; np < NTL; np += 2) {
@@ -158,7 +210,7 @@ __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) 
                 uint32_t r0, r1, r2, r3;
                 asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
                              : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                             : "r"(s2u(&S.Bs[krow][ncol])));
+                             : "r"(s2u(&S.Bs[s][krow][ncol])));
                 bf[np][0] = r0;
                 bf[np][1] = r1;
                 bf[np + 1][0] = r2;
@@ -176,7 +228,6 @@ __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) 
                         : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]),
                           "r"(bf[nt][0]), "r"(bf[nt][1]));
         }
-        __syncthreads();
         if (--kb_left == 0) {
             kb_left = P.kb_steps;
 #pragma unroll
@@ -188,6 +239,8 @@ __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) 
                         acc[a][b][c] = (float)fmod32((uint32_t)__float2int_rn(acc[a][b][c]) + off, P.M, p);
         }
     }
+    cp_wait<0>();
+    __syncthreads();   // the next tile of this CTA reuses the ring
     // c0, c1 at (row g, cols 2t, 2t+1); c2, c3 at row g + 8
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
@@ -301,7 +354,7 @@ union BatchedSmem {
 };
 
 __global__ void __launch_bounds__(NT, CTAS_PER_SM) batched_kernel(const uint8_t *__restrict__ ws) {
-    __shared__ __align__(16) BatchedSmem S;
+    __shared__ __align__(128) BatchedSmem S;
     const Header *H = reinterpret_cast<const Header *>(ws);
     const DevProblem *probs = reinterpret_cast<const DevProblem *>(ws + H->off_probs);
     const Item *items = reinterpret_cast<const Item *>(ws + H->off_items);
@@ -387,8 +440,14 @@ struct Plan {
     std::vector<DevProblem> probs;
     std::vector<Item> items;
     std::vector<int32_t> ranges;
+    std::vector<ConvJob> jobs;               // dst holds the offset in the operand area
+    std::vector<ConvItem> citems;
+    std::vector<std::pair<int64_t, int64_t>> op_off;   // per problem: (A16, B16) offsets or -1
+    int64_t ops_bytes = 0;
     int grid = 0;
 };
+
+int64_t roundq(int64_t x) { return (x + PADQ - 1) / PADQ * PADQ; }
 
 gfp_status validate_problem(const gfp_problem &q) {
     if (!is_prime_small(q.p)) return GFP_EPRIME;
@@ -403,8 +462,8 @@ gfp_status validate_problem(const gfp_problem &q) {
 gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp_status *status,
                      const int *forced_kind, Plan &plan) {
     gfp_status first_bad = GFP_OK;
-    plan.probs.clear();
-    plan.items.clear();
+    plan = Plan();
+    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, uint32_t>, int64_t> seen;
     std::vector<double> cost;
     for (int64_t i = 0; i < count; ++i) {
         const gfp_problem &q = probs[i];
@@ -451,6 +510,36 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             P.kb_steps = (int32_t)std::max<int64_t>(1, std::min<int64_t>(kb / 32, 1 << 30));
         }
         const int pi = (int)plan.probs.size();
+        int64_t offA = -1, offB = -1;
+        if (kind != KIND_DOT32 && q.k > 0) {
+            // one converted copy per distinct (matrix, ld, shape, p); A^2 shares it
+            auto job_for = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld) -> int64_t {
+                const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, q.p);
+                auto it = seen.find(key);
+                if (it != seen.end()) return it->second;
+                ConvJob J{};
+                J.src = src;
+                J.rows = rows;
+                J.cols = cols;
+                J.ld = ld;
+                J.dld = (int32_t)roundq(cols);
+                J.drows = (int32_t)roundq(rows);
+                J.p = q.p;
+                const int64_t off = plan.ops_bytes;
+                J.dst = reinterpret_cast<__half *>((uintptr_t)off);
+                plan.ops_bytes += (int64_t)J.drows * J.dld * 2;
+                const int jid = (int)plan.jobs.size();
+                plan.jobs.push_back(J);
+                for (int32_t r = 0; r < J.drows; r += 16) plan.citems.push_back(ConvItem{jid, r});
+                seen[key] = off;
+                return off;
+            };
+            offA = job_for(q.A, q.m, q.k, q.lda);
+            offB = job_for(q.B, q.k, q.n, q.ldb);
+            P.ld16a = (int32_t)roundq(q.k);
+            P.ld16b = (int32_t)roundq(q.n);
+        }
+        plan.op_off.push_back({offA, offB});
         plan.probs.push_back(P);
         const int T = tile_of(kind);
         const int tmn = (int)((q.m + T - 1) / T), tnn = (int)((q.n + T - 1) / T);
@@ -495,25 +584,32 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t plan_bytes(int64_t nprobs, int64_t nitems, int grid) {
+size_t plan_bytes(int64_t nprobs, int64_t nitems, int grid, int64_t njobs, int64_t ncitems,
+                  int64_t ops_bytes) {
     return align256(sizeof(Header)) + align256(nprobs * sizeof(DevProblem)) +
-           align256(nitems * sizeof(Item)) + align256((grid + 1) * sizeof(int32_t));
+           align256(nitems * sizeof(Item)) + align256((grid + 1) * sizeof(int32_t)) +
+           align256(njobs * sizeof(ConvJob)) + align256(ncitems * sizeof(ConvItem)) +
+           align256((size_t)ops_bytes);
 }
 
-// upper bound of the schedule size: every problem cut into 32 x 32 tiles
+// Upper bound of the workspace: every problem cut into 32 x 32 tiles and both
+// operands converted separately.
 size_t bound_bytes(int64_t count, const gfp_problem *probs) {
-    int64_t items = 0;
+    int64_t items = 0, ops = 0, citems = 0;
     for (int64_t i = 0; i < count; ++i) {
         const int64_t m = std::max<int64_t>(probs[i].m, 0), n = std::max<int64_t>(probs[i].n, 0);
+        const int64_t k = std::max<int64_t>(probs[i].k, 0);
         items += ((m + 31) / 32) * ((n + 31) / 32);
+        ops += (roundq(m) * roundq(k) + roundq(k) * roundq(n)) * 2;
+        citems += (roundq(m) + roundq(k)) / 16;
     }
-    return plan_bytes(count, items, std::max(1, num_sms() * CTAS_PER_SM));
+    return plan_bytes(count, items, std::max(1, num_sms() * CTAS_PER_SM), 2 * count, citems, ops);
 }
 
-gfp_status upload(const Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
-    const size_t need = plan_bytes((int64_t)plan.probs.size(), (int64_t)plan.items.size(), plan.grid);
+gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
+    const size_t need = plan_bytes((int64_t)plan.probs.size(), (int64_t)plan.items.size(), plan.grid,
+                                   (int64_t)plan.jobs.size(), (int64_t)plan.citems.size(), plan.ops_bytes);
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return GFP_EWORKSPACE;
-    std::vector<uint8_t> host(need, 0);
     Header H{};
     H.magic = kMagic;
     H.count = (int32_t)plan.probs.size();
@@ -522,21 +618,44 @@ gfp_status upload(const Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
     H.off_probs = (int64_t)align256(sizeof(Header));
     H.off_items = H.off_probs + (int64_t)align256(plan.probs.size() * sizeof(DevProblem));
     H.off_ranges = H.off_items + (int64_t)align256(plan.items.size() * sizeof(Item));
+    H.off_jobs = H.off_ranges + (int64_t)align256(plan.ranges.size() * sizeof(int32_t));
+    H.off_citems = H.off_jobs + (int64_t)align256(plan.jobs.size() * sizeof(ConvJob));
+    H.off_ops = H.off_citems + (int64_t)align256(plan.citems.size() * sizeof(ConvItem));
     H.bytes = (int64_t)need;
+    H.njobs = (int32_t)plan.jobs.size();
+    H.ncitems = (int32_t)plan.citems.size();
+    // operand offsets -> device addresses
+    uint8_t *ops = static_cast<uint8_t *>(ws) + H.off_ops;
+    for (size_t i = 0; i < plan.probs.size(); ++i) {
+        if (plan.op_off[i].first >= 0) {
+            plan.probs[i].A16 = reinterpret_cast<const __half *>(ops + plan.op_off[i].first);
+            plan.probs[i].B16 = reinterpret_cast<const __half *>(ops + plan.op_off[i].second);
+        }
+    }
+    for (auto &J : plan.jobs) J.dst = reinterpret_cast<__half *>(ops + (uintptr_t)J.dst);
+    const size_t meta = (size_t)H.off_ops;   // the operand area itself is written by the launch
+    std::vector<uint8_t> host(meta, 0);
     std::memcpy(host.data(), &H, sizeof(H));
     if (!plan.probs.empty())
         std::memcpy(host.data() + H.off_probs, plan.probs.data(), plan.probs.size() * sizeof(DevProblem));
     if (!plan.items.empty())
         std::memcpy(host.data() + H.off_items, plan.items.data(), plan.items.size() * sizeof(Item));
     std::memcpy(host.data() + H.off_ranges, plan.ranges.data(), plan.ranges.size() * sizeof(int32_t));
+    if (!plan.jobs.empty())
+        std::memcpy(host.data() + H.off_jobs, plan.jobs.data(), plan.jobs.size() * sizeof(ConvJob));
+    if (!plan.citems.empty())
+        std::memcpy(host.data() + H.off_citems, plan.citems.data(), plan.citems.size() * sizeof(ConvItem));
     // pageable source: the copy is staged before the call returns
-    cudaError_t e = cudaMemcpyAsync(ws, host.data(), need, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(ws, host.data(), meta, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
 }
 
 gfp_status launch_plan(void *ws, cudaStream_t s) {
+    // operand conversion (a grid-stride loop over the jobs' 16-row items; it
+    // reads their count from the workspace), then the grouped product
+    convert_kernel<<<std::max(1, num_sms() * 4), 256, 0, s>>>(static_cast<const uint8_t *>(ws));
     batched_kernel<<<std::max(1, num_sms() * CTAS_PER_SM), NT, 0, s>>>(static_cast<const uint8_t *>(ws));
     return check_launch();
 }

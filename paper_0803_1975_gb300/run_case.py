@@ -5,7 +5,8 @@ time (CUDA events, L2 flushed between repetitions) and effective 2mnk/s.
     python -m paper_0803_1975_gb300.run_case --form dot --word u32 --kb 60 --size 1024
 
 Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8 (gfp_gemm); dot, mixed
-(gfp_gemm_compressed, after packing).  Useful for profiling one kernel.
+(gfp_gemm_compressed, after packing); batched (the 4096-problem adjacency
+workload, one prepared launch).  Useful for profiling one kernel.
 """
 from __future__ import annotations
 
@@ -50,6 +51,18 @@ def main():
         CB = gfp.gfp_pack(p, B, d, Q, "cols", a.word)
         C = torch.empty((m, n), dtype=torch.uint8, device="cuda")
         fn = lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", a.word, CA, CB, out=C, kb=kb)
+    elif a.form == "batched":
+        # the 4096-problem adjacency workload, one prepared schedule replayed
+        items = []
+        for pp, Ah in inputs.batched_problems():
+            Ad = torch.from_numpy(Ah).cuda()
+            items.append((pp, Ad, Ad, torch.empty(Ah.shape, dtype=torch.uint8, device="cuda")))
+        arr, cnt = gfp.make_problems(items)
+        ws = torch.empty(gfp.gfp_batched_workspace_size(arr, cnt), dtype=torch.uint8, device="cuda")
+        gfp.gfp_batched_prepare(arr, cnt, "auto", ws)
+        m = k = n = 0
+        flops_total = sum(2.0 * it[1].shape[0] ** 3 for it in items)
+        fn = lambda: gfp.gfp_batched_launch(ws)
     elif a.form == "mixed":
         d, Q, _ = gfp.gfp_params(p, m, k, n, "mixed", a.word)
         CB = gfp.gfp_pack(p, B, d, Q, "rows", a.word)
@@ -70,8 +83,9 @@ def main():
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = float(np.median(ts))
+    flops = flops_total if a.form == "batched" else 2.0 * m * n * k
     print(json.dumps({"form": a.form, "word": a.word, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
-                      "T_2mnk_per_s": round(2.0 * m * n * k / ms / 1e9, 3)}))
+                      "T_2mnk_per_s": round(flops / ms / 1e9, 3)}))
 
 
 if __name__ == "__main__":
