@@ -421,13 +421,18 @@ cudaError_t run_simt(const typename P::GA *A, int64_t lda, const typename P::GB 
                      typename P::GC *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                      const typename P::Params &prm, cudaStream_t s, bool allow_large = true,
                      int splits = 1) {
+    // k-slice depth: as deep as the 48 KB of static shared memory allows, so
+    // the register prefetch of the next slice covers the global-load latency
+    constexpr bool narrow = sizeof(typename P::SA) <= 4 && sizeof(typename P::SB) <= 4;
     switch (choose_tile<P>(M, N, allow_large)) {
         case Tile::L:
-            return simt_gemm_launch<P, 128, 128, 8, 8, 8>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
+            return simt_gemm_launch<P, 128, 128, narrow ? 16 : 8, 8, 8>(A, lda, B, ldb, C, ldc, M, N, K,
+                                                                       prm, s, splits);
         case Tile::XS:
-            return simt_gemm_launch<P, 32, 32, 8, 2, 2>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
+            return simt_gemm_launch<P, 32, 32, 16, 2, 2>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
         default:
-            return simt_gemm_launch<P, 64, 64, 8, 4, 4>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
+            return simt_gemm_launch<P, 64, 64, narrow ? 32 : 16, 4, 4>(A, lda, B, ldb, C, ldc, M, N, K,
+                                                                      prm, s, splits);
     }
 }
 
@@ -463,8 +468,8 @@ gfp_status run_redq_form(const typename PF::GA *A, int64_t lda, const typename P
     if (splits > 1) {
         e = cudaMemset2DAsync(C, (size_t)ldc * sizeof(W), 0, (size_t)N * sizeof(W), (size_t)M, s);
         if (e != cudaSuccess) return cuda_fail(e);
-        e = simt_gemm_launch<PP, 64, 64, 8, 4, 4>(A, lda, B, ldb, reinterpret_cast<typename PP::GC *>(C), ldc,
-                                                 M, N, K, prm, s, splits);
+        e = simt_gemm_launch<PP, 64, 64, 16, 4, 4>(A, lda, B, ldb, reinterpret_cast<typename PP::GC *>(C), ldc,
+                                                  M, N, K, prm, s, splits);
         if (e != cudaSuccess) return cuda_fail(e);
         dim3 grid((unsigned)((N + 255) / 256), (unsigned)(M < 65535 ? M : 65535));
         redq_inplace_kernel<W><<<grid, 256, 0, s>>>(C, ldc, M, N, prm);
@@ -566,11 +571,11 @@ gfp_status launch_mixed(uint32_t p, int64_t m, int64_t k, int64_t nc, int d, int
         e = cudaMemset2DAsync(CC, (size_t)ldc * wb, 0, (size_t)nc * wb, (size_t)m, s);
         if (e != cudaSuccess) return cuda_fail(e);
         if (word == GFP_WORD_U64)
-            e = simt_gemm_launch<MixedU64T<true>, 64, 64, 8, 4, 4>(
+            e = simt_gemm_launch<MixedU64T<true>, 64, 64, 16, 4, 4>(
                 A, lda, static_cast<const uint64_t *>(CB), ldb, static_cast<unsigned long long *>(CC),
                 ldc, m, nc, k, prm, s, splits);
         else if (word == GFP_WORD_F64)
-            e = simt_gemm_launch<MixedF64T<true>, 64, 64, 8, 4, 4>(
+            e = simt_gemm_launch<MixedF64T<true>, 64, 64, 16, 4, 4>(
                 A, lda, static_cast<const double *>(CB), ldb, static_cast<double *>(CC), ldc, m, nc, k,
                 prm, s, splits);
         if (e != cudaSuccess) return cuda_fail(e);

@@ -194,10 +194,12 @@ struct TcArgs {
     int *status;
 };
 
-// Tile order: groups of 8 tile-rows walk the tile-columns together, so the
-// B tiles a group shares stay in L2.
+// Tile order: groups of 16 tile-rows walk the tile-columns together, so the
+// B tiles a group shares stay in L2; B is then read from DRAM tiles_m / 16
+// times and A once (a group's A rows, 2048 x k, and the B tiles of the ~10
+// columns in flight fit the 129 MB L2 at k = 8192).
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
-    const int G = 8;
+    const int G = 16;
     const int group = t / (G * tiles_n);
     const int first_m = group * G;
     const int gsize = min(G, tiles_m - first_m);
@@ -450,6 +452,21 @@ __device__ __forceinline__ void put16(void *dst, const int (&c)[16]) {
     }
 }
 
+// 16 consecutive residues (zero outside [0, limit)): one 16-byte load when the
+// run is inside the row and aligned, else byte loads.
+__device__ __forceinline__ void load16(const uint8_t *src, int64_t c0, int64_t limit, bool row_ok,
+                                       uint32_t (&r)[16]) {
+    if (row_ok && c0 + 16 <= limit && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(src);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 16; ++e) r[e] = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) r[e] = (row_ok && c0 + e < limit) ? src[e] : 0u;
+}
+
 // out[i][l] = centre(A[i][l]) for i < m, l < k; zero elsewhere in mp x kp.
 // One thread per 16 consecutive values of a row.
 template <bool FP8>
@@ -460,10 +477,11 @@ __global__ void to_op_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, in
     const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
     if (l >= kp) return;
     for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
+        uint32_t r[16];
+        load16(A + i * lda + l, l, k, i < m, r);
         int c[16];
-        const uint8_t *a = A + i * lda + l;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) c[e] = (i < m && l + e < k) ? centre_i(a[e], p, h) : 0;
+        for (int e = 0; e < 16; ++e) c[e] = centre_i(r[e], p, h);
         put16<FP8>(out + (i * kp + l) * ES, c);
     }
 }
@@ -480,10 +498,10 @@ __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ld
     const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
     {
         const int64_t l = l0 + r;
-        const uint8_t *b = B + l * ldb + j0 + q;
+        uint32_t v[16];
+        load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-            tile[r][q + e] = (int8_t)((l < k && j0 + q + e < n) ? centre_i(b[e], p, h) : 0);
+        for (int e = 0; e < 16; ++e) tile[r][q + e] = (int8_t)centre_i(v[e], p, h);
     }
     __syncthreads();
     const int64_t j = j0 + r;
