@@ -257,6 +257,7 @@ def batched_measure(gfp, torch, flush):
     arr, cnt = gfp.make_problems(items)
     need = gfp.gfp_batched_workspace_size(arr, cnt)
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    table = gfp.gfp_batched_autotune(arr, cnt, workspace=ws)    # untimed: tile kind per size bucket
     gfp.gfp_batched_prepare(arr, cnt, "auto", ws)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -271,6 +272,7 @@ def batched_measure(gfp, torch, flush):
     ms = event_time(torch, graph.replay, 7, flush)
     return {"problems": cnt, "sum_2n3": flops, "ms": round(ms, 4), "value": round(flops / ms / 1e9, 3),
             "unit": UNIT, "launches_per_replay": 2,
+            "autotuned_kinds": [gfp.BATCHED_KINDS.get(v, None) for v in table],
             "note": "one graph replay = operand conversion kernel + one persistent grouped product kernel"}
 
 

@@ -348,7 +348,8 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  *                                   the tile kind gfp_batched_autotune chose;
  *                                   untuned buckets use fp16 tensor-core tiles;
  *                GFP_ALGO_TC_F16 -- warp-level fp16 tensor-core MMA tiles
- *                                   (64 x 64, or 32 x 32 for m, n <= 48) on
+ *                                   (128 x 128 above m, n = 160, 64 x 64,
+ *                                   32 x 32 for m, n <= 48) on
  *                                   centred residues, fp32 accumulation kept
  *                                   exact by k-blocks (kb h^2 + p < 2^24);
  *                GFP_ALGO_DOT32  -- the Q-adic dot form (Section 2) in 32-bit
@@ -383,7 +384,8 @@ GFP_API gfp_status gfp_batched_launch(void *workspace, size_t ws_bytes, void *st
  * (largest of m, k, n in (0,32], (32,64], (64,128], (128,256], (256,512],
  * (512,2048], above) it times one grouped launch of that bucket's problems
  * with each tile kind (0 = fp16 MMA 64 x 64, 1 = fp16 MMA 32 x 32, 2 = Q-adic
- * 32-bit words with per-problem Q and d) and keeps the fastest; the choice
+ * 32-bit words with per-problem Q and d, 3 = fp16 MMA 128 x 128) and keeps
+ * the fastest; the choice
  * is stored in the library (used by GFP_ALGO_AUTO from then on, process
  * wide) and, if `table` is not NULL, written to table[0 .. table_len) (-1 for
  * buckets without problems).  It writes the problems' C matrices and uses

@@ -9,13 +9,15 @@
 // ranges, operand-conversion jobs -- is copied into the caller's workspace
 // with one host-to-device copy.  gfp_batched_launch then runs, on the
 // prepared workspace only (so it can be captured in a CUDA graph):
-//   1. the operand conversion: every distinct (matrix, p) operand of a
+//   1. the operand conversion: every distinct (matrix, p, tile) operand of a
 //      tensor-core tile becomes centred fp16, row-major, zero padded to
-//      multiples of 64 in both dimensions (A^2 problems convert A once);
+//      multiples of the tile (64 or 128) in both dimensions (A^2 problems
+//      convert A once);
 //   2. the one persistent grouped kernel over all tiles.
 //
-// Tile kinds (all 128 threads):
-//   HMMA64 / HMMA32 : 64 x 64 / 32 x 32 output tiles on the warp-level fp16
+// Tile kinds (all 128 threads, 2 x 2 warps):
+//   HMMA128 / HMMA64 / HMMA32 : 128 x 128 / 64 x 64 / 32 x 32 output tiles
+//       (warp tiles 64 x 64 / 32 x 32 / 16 x 16) on the warp-level fp16
 //       tensor-core MMA (m16n8k16, fp32 accumulation), operands streamed from
 //       the converted copies with 16-byte cp.async through a 3-stage ring.
 //       Every partial sum is an integer below 2^24 within a k-block kb with
@@ -44,7 +46,7 @@
 namespace gfp {
 namespace {
 
-enum Kind : int32_t { KIND_HMMA64 = 0, KIND_HMMA32 = 1, KIND_DOT32 = 2, KIND_COUNT = 3 };
+enum Kind : int32_t { KIND_HMMA64 = 0, KIND_HMMA32 = 1, KIND_DOT32 = 2, KIND_HMMA128 = 3, KIND_COUNT = 4 };
 
 struct DevProblem {          // 96 bytes
     const uint8_t *A;
@@ -93,8 +95,8 @@ struct Header {              // 128 bytes at the start of the workspace
 static_assert(sizeof(Header) == 128, "layout");
 constexpr uint32_t kMagic = 0x47465042u;   // "GFPB"
 constexpr int NT = 128;
-constexpr int CTAS_PER_SM = 4;
-constexpr int PADQ = 64;                   // padding quantum of converted operands
+constexpr int CTAS_PER_SM = 2;
+constexpr int PADQ = 64;                   // smallest padding quantum of converted operands
 constexpr int HSTAGES = 3;
 
 __device__ __forceinline__ uint32_t fmod32(uint32_t a, uint64_t M, uint32_t p) {
@@ -348,13 +350,16 @@ __device__ void tile_dot32(const DevProblem &P, int tm, int tn, DotSmem &S) {
 }
 
 union BatchedSmem {
+    HmmaSmem<128> h128;
     HmmaSmem<64> h64;
     HmmaSmem<32> h32;
     DotSmem dot;
 };
+constexpr int SMEM_BATCHED = (int)sizeof(BatchedSmem);
 
 __global__ void __launch_bounds__(NT, CTAS_PER_SM) batched_kernel(const uint8_t *__restrict__ ws) {
-    __shared__ __align__(128) BatchedSmem S;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    BatchedSmem &S = *reinterpret_cast<BatchedSmem *>(dsm);
     const Header *H = reinterpret_cast<const Header *>(ws);
     const DevProblem *probs = reinterpret_cast<const DevProblem *>(ws + H->off_probs);
     const Item *items = reinterpret_cast<const Item *>(ws + H->off_items);
@@ -364,18 +369,20 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) batched_kernel(const uint8_t 
     for (int i = i0; i < i1; ++i) {
         const Item it = items[i];
         const DevProblem P = probs[it.prob];
-        if (P.kind == KIND_HMMA64) tile_hmma<64>(P, it.tm, it.tn, S.h64);
+        if (P.kind == KIND_HMMA128) tile_hmma<128>(P, it.tm, it.tn, S.h128);
+        else if (P.kind == KIND_HMMA64) tile_hmma<64>(P, it.tm, it.tn, S.h64);
         else if (P.kind == KIND_HMMA32) tile_hmma<32>(P, it.tm, it.tn, S.h32);
         else tile_dot32(P, it.tm, it.tn, S.dot);
     }
 }
 
 // ------------------------------------------------------------------ host side
-int tile_of(int kind) { return kind == KIND_HMMA32 ? 32 : 64; }
+int tile_of(int kind) { return kind == KIND_HMMA32 ? 32 : kind == KIND_HMMA128 ? 128 : 64; }
 
 double tile_cost(int kind, int64_t k, uint32_t p) {
     // relative cost of one tile: k steps of the tile's mainloop
     const double ksteps = (double)((k + 31) / 32);
+    if (kind == KIND_HMMA128) return 12.0 * ksteps + 6.0;
     if (kind == KIND_HMMA64) return 4.0 * ksteps + 2.0;
     if (kind == KIND_HMMA32) return 1.4 * ksteps + 1.0;
     (void)p;
@@ -402,7 +409,8 @@ int default_kind(int64_t m, int64_t k, int64_t n) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int b = bucket_of(m, k, n);
     if (g_tuned[b] >= 0) return g_tuned[b];
-    return std::max(m, n) <= 48 ? KIND_HMMA32 : KIND_HMMA64;
+    const int64_t s = std::max(m, n);
+    return s <= 48 ? KIND_HMMA32 : s <= 160 ? KIND_HMMA64 : KIND_HMMA128;
 }
 
 // (t, d, words per block) of the 32-bit dot form for (p, k): the chooser of
@@ -447,7 +455,7 @@ struct Plan {
     int grid = 0;
 };
 
-int64_t roundq(int64_t x) { return (x + PADQ - 1) / PADQ * PADQ; }
+int64_t round_to(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
 
 gfp_status validate_problem(const gfp_problem &q) {
     if (!is_prime_small(q.p)) return GFP_EPRIME;
@@ -463,7 +471,7 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
                      const int *forced_kind, Plan &plan) {
     gfp_status first_bad = GFP_OK;
     plan = Plan();
-    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, uint32_t>, int64_t> seen;
+    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, uint32_t, int>, int64_t> seen;
     std::vector<double> cost;
     for (int64_t i = 0; i < count; ++i) {
         const gfp_problem &q = probs[i];
@@ -472,7 +480,10 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         if (st == GFP_OK) {
             if (forced_kind) kind = *forced_kind;
             else if (algo == GFP_ALGO_AUTO) kind = default_kind(q.m, q.k, q.n);
-            else if (algo == GFP_ALGO_TC_F16) kind = std::max(q.m, q.n) <= 48 ? KIND_HMMA32 : KIND_HMMA64;
+            else if (algo == GFP_ALGO_TC_F16) {
+                const int64_t sz = std::max(q.m, q.n);
+                kind = sz <= 48 ? KIND_HMMA32 : sz <= 160 ? KIND_HMMA64 : KIND_HMMA128;
+            }
             else if (algo == GFP_ALGO_DOT32) kind = KIND_DOT32;
             else st = GFP_EUNSUPPORTED;
         }
@@ -513,8 +524,9 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         int64_t offA = -1, offB = -1;
         if (kind != KIND_DOT32 && q.k > 0) {
             // one converted copy per distinct (matrix, ld, shape, p); A^2 shares it
+            const int pad = std::max(PADQ, tile_of(kind));
             auto job_for = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld) -> int64_t {
-                const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, q.p);
+                const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, q.p, pad);
                 auto it = seen.find(key);
                 if (it != seen.end()) return it->second;
                 ConvJob J{};
@@ -522,8 +534,8 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
                 J.rows = rows;
                 J.cols = cols;
                 J.ld = ld;
-                J.dld = (int32_t)roundq(cols);
-                J.drows = (int32_t)roundq(rows);
+                J.dld = (int32_t)round_to(cols, pad);
+                J.drows = (int32_t)round_to(rows, pad);
                 J.p = q.p;
                 const int64_t off = plan.ops_bytes;
                 J.dst = reinterpret_cast<__half *>((uintptr_t)off);
@@ -536,8 +548,8 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             };
             offA = job_for(q.A, q.m, q.k, q.lda);
             offB = job_for(q.B, q.k, q.n, q.ldb);
-            P.ld16a = (int32_t)roundq(q.k);
-            P.ld16b = (int32_t)roundq(q.n);
+            P.ld16a = (int32_t)round_to(q.k, pad);
+            P.ld16b = (int32_t)round_to(q.n, pad);
         }
         plan.op_off.push_back({offA, offB});
         plan.probs.push_back(P);
@@ -600,8 +612,8 @@ size_t bound_bytes(int64_t count, const gfp_problem *probs) {
         const int64_t m = std::max<int64_t>(probs[i].m, 0), n = std::max<int64_t>(probs[i].n, 0);
         const int64_t k = std::max<int64_t>(probs[i].k, 0);
         items += ((m + 31) / 32) * ((n + 31) / 32);
-        ops += (roundq(m) * roundq(k) + roundq(k) * roundq(n)) * 2;
-        citems += (roundq(m) + roundq(k)) / 16;
+        ops += (round_to(m, 128) * round_to(k, 128) + round_to(k, 128) * round_to(n, 128)) * 2;
+        citems += (round_to(m, 128) + round_to(k, 128)) / 16;
     }
     return plan_bytes(count, items, std::max(1, num_sms() * CTAS_PER_SM), 2 * count, citems, ops);
 }
@@ -656,7 +668,13 @@ gfp_status launch_plan(void *ws, cudaStream_t s) {
     // operand conversion (a grid-stride loop over the jobs' 16-row items; it
     // reads their count from the workspace), then the grouped product
     convert_kernel<<<std::max(1, num_sms() * 4), 256, 0, s>>>(static_cast<const uint8_t *>(ws));
-    batched_kernel<<<std::max(1, num_sms() * CTAS_PER_SM), NT, 0, s>>>(static_cast<const uint8_t *>(ws));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BATCHED);
+        attr = true;
+    }
+    batched_kernel<<<std::max(1, num_sms() * CTAS_PER_SM), NT, SMEM_BATCHED, s>>>(
+        static_cast<const uint8_t *>(ws));
     return check_launch();
 }
 

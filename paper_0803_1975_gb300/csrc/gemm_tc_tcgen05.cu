@@ -191,6 +191,7 @@ struct TcArgs {
     int kblocks;       // ceil(ktiles / kb_tiles)
     uint32_t p, off;   // off = p ceil(2^24 / p): makes |x| < 2^24 non-negative
     uint64_t M;        // fastmod magic of p
+    float scale;       // 1, or 2^18 for raw e4m3 operands (values r 2^-9)
     int *status;
 };
 
@@ -382,7 +383,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         uint32_t packed = 0;
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
-                            const int x = __float2int_rn(__uint_as_float(v[e * 4 + b]));
+                            const int x = __float2int_rn(__uint_as_float(v[e * 4 + b]) * g.scale);
                             uint32_t r = fastmod((uint32_t)x + g.off, g.M, g.p);
                             if constexpr (BLOCKED) {
                                 r += (run[c * 8 + e] >> (8 * b)) & 0xffu;
@@ -488,7 +489,9 @@ __global__ void to_op_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, in
 
 // out[j][l] = centre(B[l][j]) for l < k, j < n; zero elsewhere in np x kp.
 // 64 x 64 tiles through shared memory; 256 threads, 16 values each way.
-template <bool FP8>
+// RAW: residues copied unchanged (for e4m3 operands of p < 16, the byte r is
+// the e4m3 code of r 2^-9, see launch_tc).
+template <bool FP8, bool RAW = false>
 __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k,
                                        int64_t n, uint8_t *__restrict__ out, int64_t kp, int64_t np,
                                        uint32_t p, uint32_t h) {
@@ -501,15 +504,22 @@ __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ld
         uint32_t v[16];
         load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) tile[r][q + e] = (int8_t)centre_i(v[e], p, h);
+        for (int e = 0; e < 16; ++e) tile[r][q + e] = (int8_t)(RAW ? (int)v[e] : centre_i(v[e], p, h));
     }
     __syncthreads();
     const int64_t j = j0 + r;
     if (j < np) {
-        int c[16];
+        if constexpr (RAW) {
+            uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int e = 0; e < 16; ++e) c[e] = tile[q + e][r];
-        put16<FP8>(out + (j * kp + l0 + q) * ES, c);
+            for (int e = 0; e < 16; ++e) w[e >> 2] |= (uint32_t)(uint8_t)tile[q + e][r] << (8 * (e & 3));
+            *reinterpret_cast<uint4 *>(out + j * kp + l0 + q) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            int c[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) c[e] = tile[q + e][r];
+            put16<FP8>(out + (j * kp + l0 + q) * ES, c);
+        }
     }
 }
 
@@ -533,12 +543,13 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int box_rows, bool fp8) {
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int box_rows, bool fp8,
+              int64_t ld_elems = 0) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const int es = fp8 ? 1 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * es};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld_elems > 0 ? ld_elems : kp) * es};
     cuuint32_t box[2] = {(cuuint32_t)(ROWB / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
@@ -564,6 +575,22 @@ int pick_bn(int64_t m, int64_t n) {
     return t256 >= num_sms() ? 256 : 128;
 }
 
+// Raw e4m3 operands: for p < 16 the residue bytes r in [0, 16) are, read as
+// e4m3 codes, exactly r 2^-9 (codes 0-7 are the subnormals m 2^-9, codes 8-15
+// the first binade (8 + m) 2^-9).  A is then read by TMA straight from the
+// caller's matrix and B needs only a byte transpose; products are
+// r r' 2^-18, their sums exact in fp32 while below 2^24 units, and the
+// epilogue multiplies by 2^18.  The residues are not centred, so the k-block
+// bound uses (p-1)^2.
+bool raw_fp8_ok(uint32_t p, const uint8_t *A, int64_t lda) {
+    return p < 16 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 15) == 0;
+}
+
+int64_t kblock_units(int64_t maxprod, uint32_t p) {
+    const int64_t kb = ((int64_t(1) << 24) - 1 - p) / maxprod;
+    return kb / 128 * 128;
+}
+
 gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
                      const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws, size_t ws_bytes,
                      cudaStream_t s, bool fp8) {
@@ -574,6 +601,7 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     if (256 + (size_t)(mp + np) * (size_t)kp * es > ws_bytes) return GFP_EWORKSPACE;
     if (mp / BM > (int64_t)1 << 30 || np / bn > (int64_t)1 << 30 || kp / bke > (int64_t)1 << 30)
         return GFP_EINVAL;
+    const bool raw = fp8 && raw_fp8_ok(p, A, lda);
     int *status = static_cast<int *>(ws);
     uint8_t *Aop = static_cast<uint8_t *>(ws) + 256;
     uint8_t *Bop = Aop + mp * kp * es;
@@ -583,7 +611,9 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     {
         dim3 grid((unsigned)((kp / 16 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
         dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64));
-        if (fp8) {
+        if (raw) {
+            to_op_transpose_kernel<true, true><<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
+        } else if (fp8) {
             to_op_rows_kernel<true><<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, p, h);
             to_op_transpose_kernel<true><<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
         } else {
@@ -592,7 +622,9 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
         }
     }
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Aop, mp, kp, BM, fp8) || !make_map(&mb, Bop, np, kp, bn, fp8)) return GFP_EUNSUPPORTED;
+    // raw: TMA over the caller's A (m x k, stride lda); out-of-range boxes read zeros
+    const bool ok_a = raw ? make_map(&ma, A, m, k, BM, true, lda) : make_map(&ma, Aop, mp, kp, BM, fp8);
+    if (!ok_a || !make_map(&mb, Bop, np, kp, bn, fp8)) return GFP_EUNSUPPORTED;
     TcArgs g;
     g.C = C;
     g.ldc = ldc;
@@ -601,12 +633,14 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     g.tiles_m = (int)(mp / BM);
     g.tiles_n = (int)((n + bn - 1) / bn);
     g.ktiles = (int)(kp / bke);
-    g.kb_tiles = (int)(tc_kblock_f32(p) / bke);
+    const int64_t kb = raw ? kblock_units((int64_t)(p - 1) * (p - 1), p) : tc_kblock_f32(p);
+    g.kb_tiles = (int)(kb / bke);
     if (g.kb_tiles < 1) g.kb_tiles = 1;
     g.kblocks = (g.ktiles + g.kb_tiles - 1) / g.kb_tiles;
     g.p = p;
     g.off = (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);
     g.M = fastmod_magic(p);
+    g.scale = raw ? 262144.0f : 1.0f;
     g.status = status;
     const int tiles = g.tiles_m * g.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();

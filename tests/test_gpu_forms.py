@@ -342,3 +342,19 @@ def test_full_worst_case(word):
     CB = gfp.gfp_pack(p, dev(B), dth, Q ** (dq + 1), "rows", word)
     CC = gfp.gfp_gemm_full(p, 30, k, 40, dq, dth, Q, word, CA, CB)
     assert (host(gfp.gfp_unpack_block(p, CC, 30, 40, dq, dth, Q, word)) == (k * 4) % 3).all()
+
+
+@pytest.mark.parametrize("p", [2, 5, 13])
+def test_tc_f8_raw_operands(p):
+    """fp8 form with p < 16 reads A straight from the caller's matrix (the byte
+    r is the e4m3 code of r 2^-9) when A and lda are 16-byte aligned: strided A
+    (lda = 160 > k = 150, k not a multiple of 128), m off the tile grid,
+    random and all-(p-1) entries."""
+    m, k, n = 200, 150, 300
+    g = inputs.rng(35, p)
+    for A in (inputs.residues(g, p, m, k), np.full((m, k), p - 1, np.uint8)):
+        B = inputs.residues(g, p, k, n)
+        Ad = torch.zeros((m, 160), dtype=torch.uint8, device="cuda")
+        Ad[:, :k] = dev(A)
+        C = host(gfp.gfp_gemm(p, Ad[:, :k], dev(B), "tc_f8"))
+        assert (C == oracle.gemm(p, A, B)).all()
