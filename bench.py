@@ -12,7 +12,7 @@ path once on that input:
   right-compressed form, u64   gfp_pack(B, rows), gfp_gemm_compressed(mixed)
                                with REDQ, gfp_unpack(CC)
   classical product            gfp_gemm(plain)
-  exact tensor-core forms      gfp_gemm(tc_f16), gfp_gemm(tc_mma_s8)
+  exact tensor-core forms      gfp_gemm(tc_f16), gfp_gemm(tc_f8), gfp_gemm(tc_mma_s8)
 
 value = (products per step x 2mnk) / step time (every product is the full
 C = A B mod p).  Each step is timed alone with CUDA events; a 256 MiB buffer
@@ -113,7 +113,7 @@ class Clocks:
 class Step:
     """Every stage of the hot path on one (A, B); buffers allocated once."""
 
-    LAUNCHES = 16   # kernels of this library per step (counted below)
+    LAUNCHES = 17   # kernels of this library per step (counted below)
 
     def __init__(self, gfp, torch, A, B):
         self.gfp, self.torch = gfp, torch
@@ -133,8 +133,9 @@ class Step:
         self.CBr = e((K, ncm), dt=torch.int64)
         self.CC = e((M, ncm), dt=torch.int64)
         self.outs = {name: e((M, N)) for name in ("dot_u64", "dot_f64", "mixed_u64", "plain", "tc_f16",
-                                                  "tc_mma_s8")}
+                                                  "tc_f8", "tc_mma_s8")}
         self.ws16 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_f16"))
+        self.wsf8 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_f8"))
         self.ws8 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_mma_s8"))
         self.dom = None   # (start, end) events around the dominant kernel
 
@@ -162,8 +163,10 @@ class Step:
         g.gfp_unpack(P, self.CC, M, N, dm, Qm, "rows", "u64", out=self.outs["mixed_u64"])
         # classical product: 1 launch
         g.gfp_gemm(P, self.A, self.B, "plain", out=self.outs["plain"])
-        # tensor-core forms: 3 + 3 launches (operand conversion, product)
+        # tensor-core forms: 3 + 2 + 3 launches (operand conversion, product; the
+        # fp8 form converts only B for p < 16)
         g.gfp_gemm(P, self.A, self.B, "tc_f16", out=self.outs["tc_f16"], workspace=self.ws16)
+        g.gfp_gemm(P, self.A, self.B, "tc_f8", out=self.outs["tc_f8"], workspace=self.wsf8)
         g.gfp_gemm(P, self.A, self.B, "tc_mma_s8", out=self.outs["tc_mma_s8"], workspace=self.ws8)
 
     @property

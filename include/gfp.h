@@ -346,7 +346,8 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  *  probs       : HOST array of `count` problems; each is validated on the host.
  *  algo        : GFP_ALGO_AUTO   -- per size bucket (the largest of m, k, n),
  *                                   the tile kind gfp_batched_autotune chose;
- *                                   untuned buckets use fp16 tensor-core tiles;
+ *                                   untuned buckets use tcgen05 tiles for
+ *                                   p < 16 above m, n = 96, else fp16 MMA tiles;
  *                GFP_ALGO_TC_F16 -- warp-level fp16 tensor-core MMA tiles
  *                                   (128 x 128 above m, n = 160, 64 x 64,
  *                                   32 x 32 for m, n <= 48) on
@@ -354,7 +355,12 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  *                                   exact by k-blocks (kb h^2 + p < 2^24);
  *                GFP_ALGO_DOT32  -- the Q-adic dot form (Section 2) in 32-bit
  *                                   words, residues packed while staged, with
- *                                   (Q, d, k-block) chosen per problem.
+ *                                   (Q, d, k-block) chosen per problem;
+ *                GFP_ALGO_TC_F8  -- tcgen05 128 x 128 tiles of a second
+ *                                   grouped kernel, for p < 16 (residue bytes
+ *                                   read as e4m3 codes of r 2^-9, exact while
+ *                                   k (p-1)^2 < 2^24); other problems fall
+ *                                   back to the fp16 MMA tiles.
  *  status      : optional HOST array of `count` per-problem statuses.  A
  *                problem that fails validation is skipped (its C untouched)
  *                and the call returns the first failing status after
@@ -366,7 +372,8 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  * gfp_gemm_batched = gfp_batched_prepare + gfp_batched_launch.
  * gfp_batched_prepare writes the schedule with one host-to-device copy and
  * synchronizes `stream` (run it outside stream capture).  gfp_batched_launch
- * launches the one grouped kernel that reads the prepared workspace; it
+ * launches, on the prepared workspace, the operand conversion and the grouped
+ * kernels the schedule uses (the mma.sync tiles, the tcgen05 tiles); it
  * allocates nothing and does not synchronize, so it can be captured in a CUDA
  * graph and replayed while the workspace and matrices stay in place.  Both
  * must run on the same device. */
@@ -384,8 +391,8 @@ GFP_API gfp_status gfp_batched_launch(void *workspace, size_t ws_bytes, void *st
  * (largest of m, k, n in (0,32], (32,64], (64,128], (128,256], (256,512],
  * (512,2048], above) it times one grouped launch of that bucket's problems
  * with each tile kind (0 = fp16 MMA 64 x 64, 1 = fp16 MMA 32 x 32, 2 = Q-adic
- * 32-bit words with per-problem Q and d, 3 = fp16 MMA 128 x 128) and keeps
- * the fastest; the choice
+ * 32-bit words with per-problem Q and d, 3 = fp16 MMA 128 x 128, 4 = tcgen05
+ * e4m3 128 x 128 for p < 16) and keeps the fastest; the choice
  * is stored in the library (used by GFP_ALGO_AUTO from then on, process
  * wide) and, if `table` is not NULL, written to table[0 .. table_len) (-1 for
  * buckets without problems).  It writes the problems' C matrices and uses

@@ -42,11 +42,14 @@
 #include <cuda_fp16.h>
 
 #include "gfp_internal.h"
+#include "tc_group.h"
 
 namespace gfp {
 namespace {
 
-enum Kind : int32_t { KIND_HMMA64 = 0, KIND_HMMA32 = 1, KIND_DOT32 = 2, KIND_HMMA128 = 3, KIND_COUNT = 4 };
+enum Kind : int32_t {
+    KIND_HMMA64 = 0, KIND_HMMA32 = 1, KIND_DOT32 = 2, KIND_HMMA128 = 3, KIND_TC8 = 4, KIND_COUNT = 5
+};
 
 struct DevProblem {          // 96 bytes
     const uint8_t *A;
@@ -69,17 +72,21 @@ struct Item {                // 8 bytes: problem index, tile row, tile column
     uint16_t tm, tn;
 };
 
+enum ConvMode : int32_t { CONV_F16 = 0, CONV_RAW = 1, CONV_RAW_T = 2 };
+
 struct ConvJob {             // 48 bytes: one operand to convert
     const uint8_t *src;
-    __half *dst;
-    int32_t rows, cols, ld, dld, drows;
+    void *dst;
+    int32_t rows, cols, ld;  // source
+    int32_t dld, drows;      // destination row stride (elements) and padded rows
     uint32_t p;
-    int32_t pad[2];
+    int32_t mode;            // ConvMode
+    int32_t dcols;           // destination columns written (<= dld)
 };
 static_assert(sizeof(ConvJob) == 48, "layout");
 
-struct ConvItem {            // 16 padded rows of one job
-    int32_t job, row0;
+struct ConvItem {            // CONV_F16 / CONV_RAW: 16 rows from row0; CONV_RAW_T: a 64 x 64 block
+    int32_t job, row0, col0, pad;
 };
 
 struct Header {              // 128 bytes at the start of the workspace
@@ -90,9 +97,13 @@ struct Header {              // 128 bytes at the start of the workspace
     int64_t off_probs, off_items, off_ranges, off_jobs, off_citems, off_ops;
     int64_t bytes;
     int32_t njobs, ncitems;
-    int32_t pad[12];
+    int64_t off_tcops;       // start of the tcgen05 operand copies inside the operand area
+    int32_t pad[10];
 };
 static_assert(sizeof(Header) == 128, "layout");
+// Fixed places: the grouped tcgen05 schedule header follows the header, then
+// the tcgen05 kernel's status word (so that a launch needs no host state).
+constexpr int64_t OFF_TCHDR = 128, OFF_TCSTATUS = 192, OFF_META = 256;
 constexpr uint32_t kMagic = 0x47465042u;   // "GFPB"
 constexpr int NT = 128;
 constexpr int CTAS_PER_SM = 2;
@@ -108,30 +119,91 @@ __device__ __forceinline__ uint32_t s2u(const void *p) {
 }
 
 // ------------------------------------------------------- operand conversion
-// c = r - p [r > h] as fp16, zero outside the matrix, 8 values per thread-step.
+// 16 consecutive bytes of a source row from column c (zero past `cols` or
+// outside the matrix).  Inside the row: one vector load when aligned, else
+// five aligned 32-bit loads joined by funnel shifts (an aligned word that
+// holds a byte of the row lies in the same page as that byte, so the load
+// cannot fault); the row's last run is read byte by byte.
+__device__ __forceinline__ uint4 src16(const ConvJob &J, int64_t r, int64_t c) {
+    if (r >= J.rows || c >= J.cols) return make_uint4(0, 0, 0, 0);
+    const uint8_t *p = J.src + r * J.ld + c;
+    if (c + 16 <= J.cols) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        if ((a & 15) == 0) return __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~(uintptr_t)3);
+        const uint32_t sh = 8u * (uint32_t)(a & 3);
+        uint32_t x[5];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = __ldg(w + i);
+        x[4] = sh ? __ldg(w + 4) : 0u;
+        return make_uint4(__funnelshift_r(x[0], x[1], sh), __funnelshift_r(x[1], x[2], sh),
+                          __funnelshift_r(x[2], x[3], sh), __funnelshift_r(x[3], x[4], sh));
+    }
+    uint32_t w[4] = {0, 0, 0, 0};
+    for (int e = 0; c + e < J.cols; ++e) w[e >> 2] |= (uint32_t)__ldg(p + e) << (8 * (e & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// CONV_F16  : c = r - p [r > h] as fp16 (HMMA tiles), 16 values per step.
+// CONV_RAW  : residue bytes copied (e4m3 codes of r 2^-9 for the tcgen05
+//             tiles), 16 per step.
+// CONV_RAW_T: residue bytes transposed through a 64 x 64 shared tile.
+// Everything of the destination's dcols columns outside the source matrix
+// is written as zero.
 __global__ void __launch_bounds__(256) convert_kernel(const uint8_t *__restrict__ ws) {
+    __shared__ uint32_t tile[64][64 / 4 + 1];   // [source row][4 source columns], padded
     const Header *H = reinterpret_cast<const Header *>(ws);
     const ConvJob *jobs = reinterpret_cast<const ConvJob *>(ws + H->off_jobs);
     const ConvItem *items = reinterpret_cast<const ConvItem *>(ws + H->off_citems);
     for (int it = blockIdx.x; it < H->ncitems; it += gridDim.x) {
         const ConvItem ci = items[it];
         const ConvJob J = jobs[ci.job];
-        const uint32_t h = J.p == 2 ? 1u : (J.p - 1) / 2;
-        const int per_row = J.dld / 8;
-        for (int idx = threadIdx.x; idx < 16 * per_row; idx += blockDim.x) {
-            const int r = ci.row0 + idx / per_row, c = (idx % per_row) * 8;
-            if (r >= J.drows) break;
-            __align__(16) __half v[8];
+        if (J.mode == CONV_RAW_T) {
+            // dst[j][l] = src[l][j]: rows j0 .. j0+63 of dst, columns l0 .. l0+63
+            const int j0 = ci.row0, l0 = ci.col0;
+            const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
+            const uint4 v = src16(J, l0 + r, j0 + q);
+            tile[r][q / 4 + 0] = v.x;
+            tile[r][q / 4 + 1] = v.y;
+            tile[r][q / 4 + 2] = v.z;
+            tile[r][q / 4 + 3] = v.w;
+            __syncthreads();
+            // thread (r, q): destination row j0 + r, columns l0 + q .. +15,
+            // i.e. byte r of source rows q .. q+15
+            const int wc = r >> 2, sh = 8 * (r & 3);
+            uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                int x = 0;
-                if (r < J.rows && c + e < J.cols) {
-                    const uint32_t q = J.src[(int64_t)r * J.ld + c + e];
-                    x = (int)q - (q > h ? (int)J.p : 0);
-                }
-                v[e] = __int2half_rn(x);
+            for (int e = 0; e < 16; ++e) w[e >> 2] |= ((tile[q + e][wc] >> sh) & 0xffu) << (8 * (e & 3));
+            uint8_t *d = static_cast<uint8_t *>(J.dst) + (int64_t)(j0 + r) * J.dld + l0 + q;
+            *reinterpret_cast<uint4 *>(d) = make_uint4(w[0], w[1], w[2], w[3]);
+            __syncthreads();
+            continue;
+        }
+        if (J.mode == CONV_RAW) {
+            const int per_row = J.dcols / 16;
+            for (int idx = threadIdx.x; idx < 16 * per_row; idx += blockDim.x) {
+                const int r = ci.row0 + idx / per_row, c = (idx % per_row) * 16;
+                if (r >= J.drows) break;
+                *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)r * J.dld + c) = src16(J, r, c);
             }
-            *reinterpret_cast<uint4 *>(J.dst + (int64_t)r * J.dld + c) = *reinterpret_cast<const uint4 *>(v);
+            continue;
+        }
+        const uint32_t h = J.p == 2 ? 1u : (J.p - 1) / 2;
+        const int per_row = J.dcols / 16;
+        for (int idx = threadIdx.x; idx < 16 * per_row; idx += blockDim.x) {
+            const int r = ci.row0 + idx / per_row, c = (idx % per_row) * 16;
+            if (r >= J.drows) break;
+            const uint4 v = src16(J, r, c);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            __align__(16) __half o[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const uint32_t q = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
+                o[e] = __int2half_rn((int)q - (q > h ? (int)J.p : 0));
+            }
+            uint4 *d = reinterpret_cast<uint4 *>(static_cast<__half *>(J.dst) + (int64_t)r * J.dld + c);
+            d[0] = reinterpret_cast<const uint4 *>(o)[0];
+            d[1] = reinterpret_cast<const uint4 *>(o)[1];
         }
     }
 }
@@ -242,24 +314,33 @@ __device__ void tile_hmma(const DevProblem &P, int tm, int tn, HmmaSmem<BT> &S) 
         }
     }
     cp_wait<0>();
-    __syncthreads();   // the next tile of this CTA reuses the ring
+    __syncthreads();   // the ring is free: it stages the output tile
     // c0, c1 at (row g, cols 2t, 2t+1); c2, c3 at row g + 8
+    constexpr int SLD = BT + 4;
+    static_assert(BT * SLD <= (int)sizeof(S.As), "staging");
+    uint8_t *stg = reinterpret_cast<uint8_t *>(&S.As[0][0][0]);
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
         for (int nt = 0; nt < NTL; ++nt) {
-            const int64_t col = n0 + wn * (BT / 2) + nt * 8 + (lane & 3) * 2;
+            const int c = wn * (BT / 2) + nt * 8 + (lane & 3) * 2;
 #pragma unroll
             for (int hr = 0; hr < 2; ++hr) {
-                const int64_t row = m0 + wm * (BT / 2) + mt * 16 + (lane >> 2) + hr * 8;
-                if (row >= P.m) continue;
+                const int r = wm * (BT / 2) + mt * 16 + (lane >> 2) + hr * 8;
 #pragma unroll
                 for (int e = 0; e < 2; ++e)
-                    if (col + e < P.n)
-                        P.C[row * P.ldc + col + e] = (uint8_t)fmod32(
-                            (uint32_t)__float2int_rn(acc[mt][nt][hr * 2 + e]) + off, P.M, p);
+                    stg[r * SLD + c + e] =
+                        (uint8_t)fmod32((uint32_t)__float2int_rn(acc[mt][nt][hr * 2 + e]) + off, P.M, p);
             }
         }
+    __syncthreads();
+    // consecutive threads write consecutive bytes of a row
+    const int rows = P.m - m0 < BT ? (int)(P.m - m0) : BT, cols = P.n - n0 < BT ? (int)(P.n - n0) : BT;
+    for (int idx = tid; idx < rows * BT; idx += NT) {
+        const int r = idx / BT, c = idx % BT;
+        if (c < cols) P.C[(m0 + r) * P.ldc + n0 + c] = stg[r * SLD + c];
+    }
+    __syncthreads();   // the next tile of this CTA reuses the ring
 }
 
 // ------------------------------------------------------ Q-adic dot form tile
@@ -377,7 +458,9 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) batched_kernel(const uint8_t 
 }
 
 // ------------------------------------------------------------------ host side
-int tile_of(int kind) { return kind == KIND_HMMA32 ? 32 : kind == KIND_HMMA128 ? 128 : 64; }
+int tile_of(int kind) {
+    return kind == KIND_HMMA32 ? 32 : (kind == KIND_HMMA128 || kind == KIND_TC8) ? 128 : 64;
+}
 
 double tile_cost(int kind, int64_t k, uint32_t p) {
     // relative cost of one tile: k steps of the tile's mainloop
@@ -405,11 +488,12 @@ int bucket_of(int64_t m, int64_t k, int64_t n) {
     return 6;
 }
 
-int default_kind(int64_t m, int64_t k, int64_t n) {
+int default_kind(int64_t m, int64_t k, int64_t n, uint32_t p) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int b = bucket_of(m, k, n);
     if (g_tuned[b] >= 0) return g_tuned[b];
     const int64_t s = std::max(m, n);
+    if (p < 16 && s > 96) return KIND_TC8;       // tcgen05 tiles (falls back when not eligible)
     return s <= 48 ? KIND_HMMA32 : s <= 160 ? KIND_HMMA64 : KIND_HMMA128;
 }
 
@@ -444,6 +528,19 @@ bool dot32_params(uint32_t p, int64_t k, int *t_out, int *d_out, int *kbw_out) {
     return found;
 }
 
+struct TcHostProb {                          // a problem of the grouped tcgen05 launch
+    int bin;                                 // k-stride bin of its operands
+    int32_t rowA0, rowB0, ktiles;            // rows in the bin's array, k in 128-slices
+    int64_t m, n, ldc;
+    uint8_t *C;
+    uint32_t p;
+};
+
+struct TcJobPlace {                          // where a tcgen05 conversion job writes
+    int job, bin;
+    int64_t row0;
+};
+
 struct Plan {
     std::vector<DevProblem> probs;
     std::vector<Item> items;
@@ -451,11 +548,34 @@ struct Plan {
     std::vector<ConvJob> jobs;               // dst holds the offset in the operand area
     std::vector<ConvItem> citems;
     std::vector<std::pair<int64_t, int64_t>> op_off;   // per problem: (A16, B16) offsets or -1
+    std::vector<TcHostProb> tc;
+    std::vector<TcGroupItem> tc_items;
+    std::vector<int32_t> tc_ranges;
+    std::vector<TcJobPlace> tc_places;
+    int64_t bin_rows[TC_GROUP_BINS] = {};
+    int64_t bin_off[TC_GROUP_BINS] = {};     // offsets of the bin arrays in the operand area
     int64_t ops_bytes = 0;
-    int grid = 0;
+    int grid = 0, tc_grid = 0;
 };
 
 int64_t round_to(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+// fp32-exact k-block of the raw e4m3 products (residues r < 16 uncentred)
+int64_t tc8_kmax(uint32_t p) {
+    const int64_t pr = (int64_t)(p - 1) * (p - 1);
+    return pr == 0 ? ((int64_t)1 << 30) : (((int64_t)1 << 24) - 1 - p) / pr;
+}
+
+bool tc8_eligible(const gfp_problem &q) {
+    return q.p < 16 && q.k > 0 && q.k <= tc8_kmax(q.p) && q.k <= (int64_t)128 << (TC_GROUP_BINS - 1);
+}
+
+// stride bin of k: the smallest 128 2^b >= k
+int tc8_bin(int64_t k) {
+    int b = 0;
+    while (((int64_t)128 << b) < k) ++b;
+    return b;
+}
 
 gfp_status validate_problem(const gfp_problem &q) {
     if (!is_prime_small(q.p)) return GFP_EPRIME;
@@ -467,26 +587,128 @@ gfp_status validate_problem(const gfp_problem &q) {
     return GFP_OK;
 }
 
+// Longest processing time first onto the least loaded of `grid` CTAs; returns
+// the items reordered by CTA and the per-CTA ranges.
+template <class T>
+void lpt(std::vector<T> &items, const std::vector<double> &cost, int grid, std::vector<int32_t> &ranges) {
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int>> per(grid);
+    std::vector<std::pair<double, int>> heap;
+    for (int g = 0; g < grid; ++g) heap.push_back({0.0, g});
+    auto cmp = [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first || (a.first == b.first && a.second > b.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (int idx : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto &top = heap.back();
+        per[top.second].push_back(idx);
+        top.first += cost[idx];
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<T> sorted;
+    sorted.reserve(items.size());
+    ranges.assign(grid + 1, 0);
+    for (int g = 0; g < grid; ++g) {
+        ranges[g] = (int32_t)sorted.size();
+        for (int idx : per[g]) sorted.push_back(items[idx]);
+    }
+    ranges[grid] = (int32_t)sorted.size();
+    items.swap(sorted);
+}
+
 gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp_status *status,
                      const int *forced_kind, Plan &plan) {
     gfp_status first_bad = GFP_OK;
     plan = Plan();
-    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, uint32_t, int>, int64_t> seen;
-    std::vector<double> cost;
+    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, uint32_t, int, int>, int64_t> seen;
+    std::vector<double> cost, tc_cost;
+    // one converted copy per distinct (matrix, ld, shape, p, padding, mode)
+    auto job_for = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld, uint32_t p, int rpad,
+                       int cpad, int mode) -> int64_t {
+        const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, p, rpad * 1024 + cpad, mode);
+        auto it = seen.find(key);
+        if (it != seen.end()) return it->second;
+        ConvJob J{};
+        J.src = src;
+        J.rows = rows;
+        J.cols = cols;
+        J.ld = ld;
+        J.p = p;
+        J.mode = mode;
+        const int es = mode == CONV_F16 ? 2 : 1;
+        if (mode == CONV_RAW_T) {                // destination is the transpose
+            J.drows = (int32_t)round_to(cols, rpad);
+            J.dld = (int32_t)round_to(rows, cpad);
+        } else {
+            J.drows = (int32_t)round_to(rows, rpad);
+            J.dld = (int32_t)round_to(cols, cpad);
+        }
+        J.dcols = J.dld;
+        const int64_t off = plan.ops_bytes;
+        J.dst = reinterpret_cast<void *>((uintptr_t)off);
+        plan.ops_bytes += round_to((int64_t)J.drows * J.dld * es, 256);
+        const int jid = (int)plan.jobs.size();
+        plan.jobs.push_back(J);
+        if (mode == CONV_RAW_T) {
+            for (int32_t r = 0; r < J.drows; r += 64)
+                for (int32_t c = 0; c < J.dld; c += 64) plan.citems.push_back(ConvItem{jid, r, c, 0});
+        } else {
+            for (int32_t r = 0; r < J.drows; r += 16) plan.citems.push_back(ConvItem{jid, r, 0, 0});
+        }
+        seen[key] = off;
+        return off;
+    };
+    // tcgen05 operands: raw bytes, K-major, k padded to 128, rows padded to
+    // 128, stacked in the array of the k-stride bin; returns the first row
+    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, int>, int64_t> tc_seen;
+    auto tc_job = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld, uint32_t p, int mode,
+                      int64_t k) -> int64_t {
+        const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, mode);
+        auto it = tc_seen.find(key);
+        if (it != tc_seen.end()) return it->second;
+        const int bin = tc8_bin(k);
+        ConvJob J{};
+        J.src = src;
+        J.rows = rows;
+        J.cols = cols;
+        J.ld = ld;
+        J.p = p;
+        J.mode = mode;
+        J.dld = (int32_t)(128 << bin);
+        J.dcols = (int32_t)round_to(k, 128);
+        J.drows = (int32_t)round_to(mode == CONV_RAW_T ? cols : rows, 128);
+        const int jid = (int)plan.jobs.size();
+        plan.jobs.push_back(J);
+        const int64_t row0 = plan.bin_rows[bin];
+        plan.bin_rows[bin] += J.drows;
+        plan.tc_places.push_back(TcJobPlace{jid, bin, row0});
+        if (mode == CONV_RAW_T) {
+            for (int32_t r = 0; r < J.drows; r += 64)
+                for (int32_t c = 0; c < J.dcols; c += 64) plan.citems.push_back(ConvItem{jid, r, c, 0});
+        } else {
+            for (int32_t r = 0; r < J.drows; r += 16) plan.citems.push_back(ConvItem{jid, r, 0, 0});
+        }
+        tc_seen[key] = row0;
+        return row0;
+    };
     for (int64_t i = 0; i < count; ++i) {
         const gfp_problem &q = probs[i];
         gfp_status st = validate_problem(q);
         int kind = -1;
         if (st == GFP_OK) {
             if (forced_kind) kind = *forced_kind;
-            else if (algo == GFP_ALGO_AUTO) kind = default_kind(q.m, q.k, q.n);
+            else if (algo == GFP_ALGO_AUTO) kind = default_kind(q.m, q.k, q.n, q.p);
             else if (algo == GFP_ALGO_TC_F16) {
                 const int64_t sz = std::max(q.m, q.n);
                 kind = sz <= 48 ? KIND_HMMA32 : sz <= 160 ? KIND_HMMA64 : KIND_HMMA128;
-            }
-            else if (algo == GFP_ALGO_DOT32) kind = KIND_DOT32;
+            } else if (algo == GFP_ALGO_DOT32) kind = KIND_DOT32;
+            else if (algo == GFP_ALGO_TC_F8) kind = KIND_TC8;
             else st = GFP_EUNSUPPORTED;
         }
+        if (st == GFP_OK && kind == KIND_TC8 && !tc8_eligible(q)) kind = KIND_HMMA64;
         DevProblem P{};
         if (st == GFP_OK && kind == KIND_DOT32) {
             int t = 0, d = 0, kbw = 0;
@@ -503,6 +725,29 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             continue;
         }
         if (q.m == 0 || q.n == 0) continue;
+        if (kind == KIND_TC8) {
+            // raw e4m3 operands: A (m x k) copied, B transposed, both K-major,
+            // padded to 128 rows and 128 columns of k
+            TcHostProb T{};
+            T.bin = tc8_bin(q.k);
+            T.ktiles = (int32_t)(round_to(q.k, 128) / 128);
+            T.rowA0 = (int32_t)tc_job(q.A, q.m, q.k, q.lda, q.p, CONV_RAW, q.k);
+            T.rowB0 = (int32_t)tc_job(q.B, q.k, q.n, q.ldb, q.p, CONV_RAW_T, q.k);
+            T.m = q.m;
+            T.n = q.n;
+            T.ldc = q.ldc;
+            T.C = q.C;
+            T.p = q.p;
+            const int ti = (int)plan.tc.size();
+            plan.tc.push_back(T);
+            const int tmn = (int)((q.m + 127) / 128), tnn = (int)((q.n + 127) / 128);
+            for (int a = 0; a < tmn; ++a)
+                for (int b = 0; b < tnn; ++b) {
+                    plan.tc_items.push_back(TcGroupItem{ti, (uint16_t)a, (uint16_t)b});
+                    tc_cost.push_back((double)T.ktiles + 2.0);
+                }
+            continue;
+        }
         P.A = q.A;
         P.B = q.B;
         P.C = q.C;
@@ -523,31 +768,9 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         const int pi = (int)plan.probs.size();
         int64_t offA = -1, offB = -1;
         if (kind != KIND_DOT32 && q.k > 0) {
-            // one converted copy per distinct (matrix, ld, shape, p); A^2 shares it
             const int pad = std::max(PADQ, tile_of(kind));
-            auto job_for = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld) -> int64_t {
-                const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, q.p, pad);
-                auto it = seen.find(key);
-                if (it != seen.end()) return it->second;
-                ConvJob J{};
-                J.src = src;
-                J.rows = rows;
-                J.cols = cols;
-                J.ld = ld;
-                J.dld = (int32_t)round_to(cols, pad);
-                J.drows = (int32_t)round_to(rows, pad);
-                J.p = q.p;
-                const int64_t off = plan.ops_bytes;
-                J.dst = reinterpret_cast<__half *>((uintptr_t)off);
-                plan.ops_bytes += (int64_t)J.drows * J.dld * 2;
-                const int jid = (int)plan.jobs.size();
-                plan.jobs.push_back(J);
-                for (int32_t r = 0; r < J.drows; r += 16) plan.citems.push_back(ConvItem{jid, r});
-                seen[key] = off;
-                return off;
-            };
-            offA = job_for(q.A, q.m, q.k, q.lda);
-            offB = job_for(q.B, q.k, q.n, q.ldb);
+            offA = job_for(q.A, q.m, q.k, q.lda, q.p, pad, pad, CONV_F16);
+            offB = job_for(q.B, q.k, q.n, q.ldb, q.p, pad, pad, CONV_F16);
             P.ld16a = (int32_t)round_to(q.k, pad);
             P.ld16b = (int32_t)round_to(q.n, pad);
         }
@@ -562,126 +785,205 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
                 cost.push_back(c);
             }
     }
-    // longest processing time first onto the least loaded CTA
-    const int grid = std::max(1, num_sms() * CTAS_PER_SM);
-    plan.grid = grid;
-    std::vector<int> order(plan.items.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<std::vector<int>> per(grid);
-    std::vector<std::pair<double, int>> heap;
-    for (int g = 0; g < grid; ++g) heap.push_back({0.0, g});
-    auto cmp = [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
-        return a.first > b.first || (a.first == b.first && a.second > b.second);
-    };
-    std::make_heap(heap.begin(), heap.end(), cmp);
-    for (int idx : order) {
-        std::pop_heap(heap.begin(), heap.end(), cmp);
-        auto &top = heap.back();
-        per[top.second].push_back(idx);
-        top.first += cost[idx];
-        std::push_heap(heap.begin(), heap.end(), cmp);
+    plan.grid = std::max(1, num_sms() * CTAS_PER_SM);
+    lpt(plan.items, cost, plan.grid, plan.ranges);
+    plan.tc_grid = std::max(1, num_sms() * tc_grouped_ctas_per_sm());
+    lpt(plan.tc_items, tc_cost, plan.tc_grid, plan.tc_ranges);
+    // the bin arrays follow the fp16 copies in the operand area
+    for (int b = 0; b < TC_GROUP_BINS; ++b) {
+        plan.bin_off[b] = plan.ops_bytes;
+        plan.ops_bytes += round_to(plan.bin_rows[b] * ((int64_t)128 << b), 256);
     }
-    std::vector<Item> sorted;
-    sorted.reserve(plan.items.size());
-    plan.ranges.assign(grid + 1, 0);
-    for (int g = 0; g < grid; ++g) {
-        plan.ranges[g] = (int32_t)sorted.size();
-        for (int idx : per[g]) sorted.push_back(plan.items[idx]);
-    }
-    plan.ranges[grid] = (int32_t)sorted.size();
-    plan.items.swap(sorted);
+    for (const TcJobPlace &t : plan.tc_places)
+        plan.jobs[t.job].dst =
+            reinterpret_cast<void *>((uintptr_t)(plan.bin_off[t.bin] + t.row0 * ((int64_t)128 << t.bin)));
     return first_bad;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t plan_bytes(int64_t nprobs, int64_t nitems, int grid, int64_t njobs, int64_t ncitems,
-                  int64_t ops_bytes) {
-    return align256(sizeof(Header)) + align256(nprobs * sizeof(DevProblem)) +
-           align256(nitems * sizeof(Item)) + align256((grid + 1) * sizeof(int32_t)) +
-           align256(njobs * sizeof(ConvJob)) + align256(ncitems * sizeof(ConvItem)) +
-           align256((size_t)ops_bytes);
+// Workspace layout: [Header][TcGroupHeader][tcgen05 status][problems][items]
+// [ranges][conversion jobs][conversion items][tcgen05 problems][tcgen05
+// items][tcgen05 ranges][tcgen05 tensor maps][operand area].
+struct Layout {
+    int64_t probs, items, ranges, jobs, citems, tcprobs, tcitems, tcranges, tcmaps, ops, total;
+};
+
+Layout layout_of(int64_t nprobs, int64_t nitems, int grid, int64_t njobs, int64_t ncitems, int64_t ntc,
+                 int64_t ntcitems, int tc_grid, int64_t ops_bytes) {
+    Layout L;
+    int64_t o = OFF_META;
+    L.probs = o;    o += align256(nprobs * sizeof(DevProblem));
+    L.items = o;    o += align256(nitems * sizeof(Item));
+    L.ranges = o;   o += align256((grid + 1) * sizeof(int32_t));
+    L.jobs = o;     o += align256(njobs * sizeof(ConvJob));
+    L.citems = o;   o += align256(ncitems * sizeof(ConvItem));
+    L.tcprobs = o;  o += align256(ntc * sizeof(TcGroupProblem));
+    L.tcitems = o;  o += align256(ntcitems * sizeof(TcGroupItem));
+    L.tcranges = o; o += align256((tc_grid + 1) * sizeof(int32_t));
+    L.tcmaps = o;   o += align256(TC_GROUP_BINS * sizeof(CUtensorMap));
+    L.ops = o;      o += align256((size_t)ops_bytes);
+    L.total = o;
+    return L;
 }
 
-// Upper bound of the workspace: every problem cut into 32 x 32 tiles and both
-// operands converted separately.
+// Upper bound of the workspace: every problem cut into 32 x 32 tiles (and
+// into 128 x 128 tcgen05 tiles), both operands converted separately in the
+// largest layout: fp16 padded to 128, or e4m3 rows padded to 128 with a row
+// stride below twice k padded to 128.
 size_t bound_bytes(int64_t count, const gfp_problem *probs) {
-    int64_t items = 0, ops = 0, citems = 0;
+    int64_t items = 0, ops = 0, citems = 0, tcitems = 0;
     for (int64_t i = 0; i < count; ++i) {
         const int64_t m = std::max<int64_t>(probs[i].m, 0), n = std::max<int64_t>(probs[i].n, 0);
         const int64_t k = std::max<int64_t>(probs[i].k, 0);
         items += ((m + 31) / 32) * ((n + 31) / 32);
-        ops += (round_to(m, 128) * round_to(k, 128) + round_to(k, 128) * round_to(n, 128)) * 2;
-        citems += (round_to(m, 128) + round_to(k, 128)) / 16;
+        tcitems += ((m + 127) / 128) * ((n + 127) / 128);
+        const int64_t mm = round_to(m, 128), kk = round_to(k, 128), nn = round_to(n, 128);
+        ops += round_to((mm * kk + kk * nn) * 2, 256) + 2 * 256;
+        citems += (mm + kk) / 16 + (kk / 64) * (nn / 64);
     }
-    return plan_bytes(count, items, std::max(1, num_sms() * CTAS_PER_SM), 2 * count, citems, ops);
+    ops += TC_GROUP_BINS * 256;
+    const int grid = std::max(1, num_sms() * CTAS_PER_SM);
+    const int tc_grid = std::max(1, num_sms() * tc_grouped_ctas_per_sm());
+    return (size_t)layout_of(count, items, grid, 2 * count, citems, count, tcitems, tc_grid, ops).total;
 }
 
+// Which kernels a prepared workspace needs (looked up by gfp_batched_launch,
+// so that a launch reads no device memory on the host).
+std::mutex g_ws_mu;
+std::map<const void *, std::pair<bool, bool>> g_ws_kinds;
+
 gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
-    const size_t need = plan_bytes((int64_t)plan.probs.size(), (int64_t)plan.items.size(), plan.grid,
-                                   (int64_t)plan.jobs.size(), (int64_t)plan.citems.size(), plan.ops_bytes);
-    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return GFP_EWORKSPACE;
+    const Layout L = layout_of((int64_t)plan.probs.size(), (int64_t)plan.items.size(), plan.grid,
+                               (int64_t)plan.jobs.size(), (int64_t)plan.citems.size(), (int64_t)plan.tc.size(),
+                               (int64_t)plan.tc_items.size(), plan.tc_grid, plan.ops_bytes);
+    if (!ws || ws_bytes < (size_t)L.total || ((uintptr_t)ws & 255)) return GFP_EWORKSPACE;
     Header H{};
     H.magic = kMagic;
     H.count = (int32_t)plan.probs.size();
     H.items = (int32_t)plan.items.size();
     H.grid = plan.grid;
-    H.off_probs = (int64_t)align256(sizeof(Header));
-    H.off_items = H.off_probs + (int64_t)align256(plan.probs.size() * sizeof(DevProblem));
-    H.off_ranges = H.off_items + (int64_t)align256(plan.items.size() * sizeof(Item));
-    H.off_jobs = H.off_ranges + (int64_t)align256(plan.ranges.size() * sizeof(int32_t));
-    H.off_citems = H.off_jobs + (int64_t)align256(plan.jobs.size() * sizeof(ConvJob));
-    H.off_ops = H.off_citems + (int64_t)align256(plan.citems.size() * sizeof(ConvItem));
-    H.bytes = (int64_t)need;
+    H.off_probs = L.probs;
+    H.off_items = L.items;
+    H.off_ranges = L.ranges;
+    H.off_jobs = L.jobs;
+    H.off_citems = L.citems;
+    H.off_ops = L.ops;
+    H.bytes = L.total;
     H.njobs = (int32_t)plan.jobs.size();
     H.ncitems = (int32_t)plan.citems.size();
-    // operand offsets -> device addresses
-    uint8_t *ops = static_cast<uint8_t *>(ws) + H.off_ops;
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    uint8_t *ops = base + L.ops;
     for (size_t i = 0; i < plan.probs.size(); ++i) {
         if (plan.op_off[i].first >= 0) {
             plan.probs[i].A16 = reinterpret_cast<const __half *>(ops + plan.op_off[i].first);
             plan.probs[i].B16 = reinterpret_cast<const __half *>(ops + plan.op_off[i].second);
         }
     }
-    for (auto &J : plan.jobs) J.dst = reinterpret_cast<__half *>(ops + (uintptr_t)J.dst);
-    const size_t meta = (size_t)H.off_ops;   // the operand area itself is written by the launch
-    std::vector<uint8_t> host(meta, 0);
+    for (auto &J : plan.jobs) J.dst = ops + (uintptr_t)J.dst;
+    // the grouped tcgen05 schedule: one tensor map per non-empty stride bin
+    TcGroupHeader G{};
+    G.count = (int32_t)plan.tc.size();
+    G.items = (int32_t)plan.tc_items.size();
+    G.grid = plan.tc_grid;
+    G.off_probs = L.tcprobs - OFF_TCHDR;
+    G.off_items = L.tcitems - OFF_TCHDR;
+    G.off_ranges = L.tcranges - OFF_TCHDR;
+    G.off_maps = L.tcmaps - OFF_TCHDR;
+    std::vector<CUtensorMap> maps;
+    int map_of[TC_GROUP_BINS];
+    for (int b = 0; b < TC_GROUP_BINS; ++b) {
+        map_of[b] = -1;
+        if (plan.bin_rows[b] == 0) continue;
+        CUtensorMap m;
+        if (!tc_make_map_u8(&m, ops + plan.bin_off[b], plan.bin_rows[b], (int64_t)128 << b, 128))
+            return GFP_EUNSUPPORTED;
+        map_of[b] = (int)maps.size();
+        maps.push_back(m);
+    }
+    G.nmaps = (int32_t)maps.size();
+    std::vector<TcGroupProblem> tcp(plan.tc.size());
+    for (size_t i = 0; i < plan.tc.size(); ++i) {
+        const TcHostProb &T = plan.tc[i];
+        TcGroupProblem &Q = tcp[i];
+        Q.C = T.C;
+        Q.ldc = T.ldc;
+        Q.m = (int32_t)T.m;
+        Q.n = (int32_t)T.n;
+        Q.rowA0 = T.rowA0;
+        Q.rowB0 = T.rowB0;
+        Q.ktiles = T.ktiles;                 // one k-block: k <= tc8_kmax(p) by eligibility
+        Q.bin = map_of[T.bin];
+        Q.p = T.p;
+        Q.off = (uint32_t)((((int64_t)1 << 24) + T.p - 1) / T.p * T.p);
+        Q.scale = 262144.0f;                 // raw e4m3: values r 2^-9
+        Q.M = fastmod_magic(T.p);
+    }
+    std::vector<uint8_t> host((size_t)L.ops, 0);   // the operand area itself is written by the launch
     std::memcpy(host.data(), &H, sizeof(H));
-    if (!plan.probs.empty())
-        std::memcpy(host.data() + H.off_probs, plan.probs.data(), plan.probs.size() * sizeof(DevProblem));
-    if (!plan.items.empty())
-        std::memcpy(host.data() + H.off_items, plan.items.data(), plan.items.size() * sizeof(Item));
-    std::memcpy(host.data() + H.off_ranges, plan.ranges.data(), plan.ranges.size() * sizeof(int32_t));
-    if (!plan.jobs.empty())
-        std::memcpy(host.data() + H.off_jobs, plan.jobs.data(), plan.jobs.size() * sizeof(ConvJob));
-    if (!plan.citems.empty())
-        std::memcpy(host.data() + H.off_citems, plan.citems.data(), plan.citems.size() * sizeof(ConvItem));
+    std::memcpy(host.data() + OFF_TCHDR, &G, sizeof(G));
+    auto put = [&](int64_t off, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(host.data() + off, src, bytes);
+    };
+    put(L.probs, plan.probs.data(), plan.probs.size() * sizeof(DevProblem));
+    put(L.items, plan.items.data(), plan.items.size() * sizeof(Item));
+    put(L.ranges, plan.ranges.data(), plan.ranges.size() * sizeof(int32_t));
+    put(L.jobs, plan.jobs.data(), plan.jobs.size() * sizeof(ConvJob));
+    put(L.citems, plan.citems.data(), plan.citems.size() * sizeof(ConvItem));
+    put(L.tcprobs, tcp.data(), tcp.size() * sizeof(TcGroupProblem));
+    put(L.tcitems, plan.tc_items.data(), plan.tc_items.size() * sizeof(TcGroupItem));
+    put(L.tcranges, plan.tc_ranges.data(), plan.tc_ranges.size() * sizeof(int32_t));
+    put(L.tcmaps, maps.data(), maps.size() * sizeof(CUtensorMap));
     // pageable source: the copy is staged before the call returns
-    cudaError_t e = cudaMemcpyAsync(ws, host.data(), meta, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(ws, host.data(), host.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(s);
-    return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    g_ws_kinds[ws] = {!plan.items.empty(), !plan.tc_items.empty()};
+    return GFP_OK;
 }
 
 gfp_status launch_plan(void *ws, cudaStream_t s) {
-    // operand conversion (a grid-stride loop over the jobs' 16-row items; it
-    // reads their count from the workspace), then the grouped product
-    convert_kernel<<<std::max(1, num_sms() * 4), 256, 0, s>>>(static_cast<const uint8_t *>(ws));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BATCHED);
-        attr = true;
+    bool simt = true, tc = true;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws_kinds.find(ws);
+        if (it != g_ws_kinds.end()) {
+            simt = it->second.first;
+            tc = it->second.second;
+        }
     }
-    batched_kernel<<<std::max(1, num_sms() * CTAS_PER_SM), NT, SMEM_BATCHED, s>>>(
-        static_cast<const uint8_t *>(ws));
-    return check_launch();
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    // operand conversion (a grid-stride loop over the jobs' items; it reads
+    // their count from the workspace), then the grouped products
+    convert_kernel<<<std::max(1, num_sms() * 4), 256, 0, s>>>(base);
+    gfp_status st = check_launch();
+    if (st != GFP_OK) return st;
+    if (simt) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BATCHED);
+            attr = true;
+        }
+        batched_kernel<<<std::max(1, num_sms() * CTAS_PER_SM), NT, SMEM_BATCHED, s>>>(base);
+        st = check_launch();
+        if (st != GFP_OK) return st;
+    }
+    if (tc) {
+        cudaError_t e = cudaMemsetAsync(base + OFF_TCSTATUS, 0, sizeof(int), s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        st = launch_tc_grouped(base + OFF_TCHDR, std::max(1, num_sms() * tc_grouped_ctas_per_sm()),
+                               reinterpret_cast<int *>(base + OFF_TCSTATUS), s);
+    }
+    return st;
 }
 
 gfp_status prepare_impl(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp_status *status,
                         void *ws, size_t ws_bytes, cudaStream_t s, const int *forced) {
     if (count < 0 || (count > 0 && !probs)) return GFP_EINVAL;
-    if (algo != GFP_ALGO_AUTO && algo != GFP_ALGO_TC_F16 && algo != GFP_ALGO_DOT32)
+    if (algo != GFP_ALGO_AUTO && algo != GFP_ALGO_TC_F16 && algo != GFP_ALGO_DOT32 &&
+        algo != GFP_ALGO_TC_F8)
         return GFP_EUNSUPPORTED;
     Plan plan;
     gfp_status st = make_plan(count, probs, algo, status, forced, plan);

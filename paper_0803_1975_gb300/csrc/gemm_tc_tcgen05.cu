@@ -30,6 +30,7 @@
 // kernel records an error in the status word, stops issuing, waits (bounded)
 // for its own copies and MMAs in flight, frees tensor memory and returns.
 #include <cstdint>
+#include <cstring>
 
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -42,18 +43,23 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int ROWB = 128;                               // bytes of k per operand row per stage
-constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
 
-template <int BN_, bool FP8_>
+template <int BN_, bool FP8_, int STAGES_ = 4>
 struct TcCfg {
     static constexpr int BN = BN_;
     static constexpr bool FP8 = FP8_;
+    static constexpr int STAGES = STAGES_;
     static constexpr int BKE = FP8 ? 128 : 64;         // k elements per stage
     static constexpr int A_BYTES = BM * ROWB, B_BYTES = BN * ROWB;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // multiple of 1024
     static constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+    // [stages][barriers, 1 KB][store staging of the 4 epilogue warps][alignment slack]
+    static constexpr int STG_BYTES = 4 * 32 * 9 * 4;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + STG_BYTES + 1024;
+    // CTAs per SM: two when their shared memory fits (the grouped tiles of
+    // small products, where one CTA's epilogue cannot hide its latencies)
+    static constexpr int MINB = 2 * (SMEM_BYTES + 1024) <= 228 * 1024 ? 2 : 1;
     // Instruction descriptor (kind::f16 and kind::f8f6f4 share the layout):
     // fp32 accumulator (bits 4-5 = 1), A and B types 0 (fp16, resp. e4m3) in
     // bits 7-9 and 10-12, both K-major (bits 15, 16 = 0), N >> 3 in bits
@@ -195,6 +201,12 @@ struct TcArgs {
     int *status;
 };
 
+}  // namespace
+}  // namespace gfp
+#include "tc_group.h"
+namespace gfp {
+namespace {
+
 // Tile order: groups of 16 tile-rows walk the tile-columns together, so the
 // B tiles a group shares stay in L2; B is then read from DRAM tiles_m / 16
 // times and A once (a group's A rows, 2048 x k, and the B tiles of the ~10
@@ -209,11 +221,99 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     tn = r / gsize;
 }
 
-template <class CFG, bool BLOCKED>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// One tile of work as every role sees it: output coordinates, operand rows
+// (the A and B^T tiles start at rowA0 + tm BM, rowB0 + tn BN in the tensor
+// maps), k extent and the reduction parameters of its product.
+struct TileInfo {
+    int tm, tn;
+    const CUtensorMap *map;    // grouped: the tensor map of the problem's stride bin
+    int rowA0, rowB0;
+    int ktiles, kb_tiles, kblocks;
+    uint8_t *C;
+    int64_t ldc, m, n;
+    uint32_t p, off;
+    uint64_t M;
+    float scale;
+};
+
+// Walks the tiles of this CTA: a strided raster over one product, or this
+// CTA's range of a grouped schedule.  The grouped walk reads the record of
+// the following tile while the current one is in use.
+template <bool GROUPED>
+struct TileWalk {
+    const TcArgs &g;
+    const TcGroupHeader *grp;
+    int cur, end;
+    TcGroupItem nit;
+    TcGroupProblem np;
+    __device__ void fetch(int i) {
+        const uint8_t *b = reinterpret_cast<const uint8_t *>(grp);
+        nit = reinterpret_cast<const TcGroupItem *>(b + grp->off_items)[i];
+        np = reinterpret_cast<const TcGroupProblem *>(b + grp->off_probs)[nit.prob];
+    }
+    __device__ const CUtensorMap *maps() const {
+        return reinterpret_cast<const CUtensorMap *>(reinterpret_cast<const uint8_t *>(grp) + grp->off_maps);
+    }
+    __device__ TileWalk(const TcArgs &g_, const TcGroupHeader *gr) : g(g_), grp(gr) {
+        if constexpr (GROUPED) {
+            const int32_t *ranges = reinterpret_cast<const int32_t *>(reinterpret_cast<const uint8_t *>(gr) + gr->off_ranges);
+            cur = ranges[blockIdx.x];
+            end = ranges[blockIdx.x + 1];
+            if (cur < end) fetch(cur);
+        } else {
+            cur = blockIdx.x;
+            end = g.tiles_m * g.tiles_n;
+        }
+    }
+    __device__ bool next(TileInfo &t) {
+        if (cur >= end) return false;
+        if constexpr (GROUPED) {
+            t.tm = nit.tm;
+            t.tn = nit.tn;
+            t.map = maps() + np.bin;
+            t.rowA0 = np.rowA0;
+            t.rowB0 = np.rowB0;
+            t.ktiles = np.ktiles;
+            t.kb_tiles = np.ktiles;
+            t.kblocks = 1;
+            t.C = np.C;
+            t.ldc = np.ldc;
+            t.m = np.m;
+            t.n = np.n;
+            t.p = np.p;
+            t.off = np.off;
+            t.M = np.M;
+            t.scale = np.scale;
+            cur += 1;
+            if (cur < end) fetch(cur);
+        } else {
+            tile_coords(cur, g.tiles_m, g.tiles_n, t.tm, t.tn);
+            t.map = nullptr;
+            t.rowA0 = 0;
+            t.rowB0 = 0;
+            t.ktiles = g.ktiles;
+            t.kb_tiles = g.kb_tiles;
+            t.kblocks = g.kblocks;
+            t.C = g.C;
+            t.ldc = g.ldc;
+            t.m = g.m;
+            t.n = g.n;
+            t.p = g.p;
+            t.off = g.off;
+            t.M = g.M;
+            t.scale = g.scale;
+            cur += gridDim.x;
+        }
+        return true;
+    }
+};
+
+template <class CFG, bool BLOCKED, bool GROUPED>
+__global__ void __launch_bounds__(NTHREADS, CFG::MINB)
 tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              TcArgs g) {
+              TcArgs g, const TcGroupHeader *grp) {
     constexpr int BN = CFG::BN, STAGE_BYTES = CFG::STAGE_BYTES, A_BYTES = CFG::A_BYTES;
+    constexpr int STAGES = CFG::STAGES;
     constexpr uint32_t TMEM_COLS = CFG::TMEM_COLS;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
@@ -229,7 +329,6 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles = g.tiles_m * g.tiles_n;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -266,18 +365,27 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             bool issued[STAGES];
             for (int s = 0; s < STAGES; ++s) issued[s] = false;
             bool ok = true;
-            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                int tm, tn;
-                tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
-                for (int kt = 0; kt < g.ktiles; ++kt) {
+            TileWalk<GROUPED> walk(g, grp);
+            if constexpr (GROUPED) {
+                // the few tensor maps of the schedule, into the descriptor cache
+                for (int i = 0; i < grp->nmaps; ++i)
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(walk.maps() + i))
+                                 : "memory");
+            }
+            TileInfo ti;
+            while (ok && walk.next(ti)) {
+                const int tm = ti.tm, tn = ti.tn;
+                const CUtensorMap *mA = GROUPED ? ti.map : &tmA;
+                const CUtensorMap *mB = GROUPED ? ti.map : &tmB;
+                for (int kt = 0; kt < ti.ktiles; ++kt) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER)) {
                         ok = false;
                         break;
                     }
                     const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
                     mbar_expect_tx(full_bar(stage), STAGE_BYTES);
-                    tma_load_2d(sa, &tmA, kt * CFG::BKE, tm * BM, full_bar(stage));
-                    tma_load_2d(sb, &tmB, kt * CFG::BKE, tn * BN, full_bar(stage));
+                    tma_load_2d(sa, mA, kt * CFG::BKE, ti.rowA0 + tm * BM, full_bar(stage));
+                    tma_load_2d(sb, mB, kt * CFG::BKE, ti.rowB0 + tn * BN, full_bar(stage));
                     issued[stage] = true;
                     issued_parity[stage] = phase;
                     if (++stage == STAGES) {
@@ -304,8 +412,10 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             uint32_t phase = 0;
             uint32_t unit = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                for (int j = 0; j < g.kblocks && ok; ++j, ++unit) {
+            TileWalk<GROUPED> walk(g, grp);
+            TileInfo ti;
+            while (ok && walk.next(ti)) {
+                for (int j = 0; j < ti.kblocks && ok; ++j, ++unit) {
                     const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
                     if (!mbar_wait(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA)) {
                         ok = false;
@@ -313,8 +423,8 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     }
                     fence_after();
                     const uint32_t d = tmem + buf * (uint32_t)BN;
-                    const int k0 = j * g.kb_tiles;
-                    const int k1 = min(g.ktiles, k0 + g.kb_tiles);
+                    const int k0 = j * ti.kb_tiles;
+                    const int k1 = min(ti.ktiles, k0 + ti.kb_tiles);
                     for (int kt = k0; kt < k1; ++kt) {
                         if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA)) {
                             ok = false;
@@ -349,19 +459,22 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // ---------------- epilogue: 4 warps, TMEM lanes 32 (warp % 4) .. +31
         const int q = warp & 3;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        // 32 rows x 32 bytes of this warp, 36-byte rows (conflict-free both ways)
+        uint32_t *stg = reinterpret_cast<uint32_t *>(gbase + STAGES * STAGE_BYTES + 1024) + q * 32 * 9;
+        const uint8_t *stg8 = reinterpret_cast<const uint8_t *>(stg);
         uint32_t unit = 0;
         bool ok = true;
         uint32_t run[BLOCKED ? BN / 4 : 1];
-        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            int tm, tn;
-            tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
-            const int64_t row = (int64_t)tm * BM + q * 32 + lane;
-            const int64_t col0 = (int64_t)tn * BN;
+        TileWalk<GROUPED> walk(g, grp);
+        TileInfo ti;
+        while (ok && walk.next(ti)) {
+            const int64_t row = (int64_t)ti.tm * BM + q * 32 + lane;
+            const int64_t col0 = (int64_t)ti.tn * BN;
             if constexpr (BLOCKED) {
 #pragma unroll
                 for (int i = 0; i < BN / 4; ++i) run[i] = 0;
             }
-            for (int j = 0; j < g.kblocks; ++j, ++unit) {
+            for (int j = 0; j < ti.kblocks; ++j, ++unit) {
                 const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
                 // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
                 int got = 0;
@@ -372,9 +485,13 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     break;
                 }
                 fence_after();
-                const bool last = (j == g.kblocks - 1);
+                const bool last = (j == ti.kblocks - 1);
+                // rows of this warp and 32-column chunks inside the product (warp-uniform)
+                const int64_t row0 = (int64_t)ti.tm * BM + q * 32;
+                const int nchunks = row0 >= ti.m ? 0 : (int)min((int64_t)(BN / 32), (ti.n - col0 + 31) / 32);
 #pragma unroll
                 for (int c = 0; c < BN / 32; ++c) {
+                    if (c >= nchunks) break;
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * (uint32_t)BN + c * 32, v);
                     uint32_t w[8];
@@ -383,26 +500,39 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         uint32_t packed = 0;
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
-                            const int x = __float2int_rn(__uint_as_float(v[e * 4 + b]) * g.scale);
-                            uint32_t r = fastmod((uint32_t)x + g.off, g.M, g.p);
+                            const int x = __float2int_rn(__uint_as_float(v[e * 4 + b]) * ti.scale);
+                            uint32_t r = fastmod((uint32_t)x + ti.off, ti.M, ti.p);
                             if constexpr (BLOCKED) {
                                 r += (run[c * 8 + e] >> (8 * b)) & 0xffu;
-                                r = r >= g.p ? r - g.p : r;
+                                r = r >= ti.p ? r - ti.p : r;
                             }
                             packed |= r << (8 * b);
                         }
                         w[e] = packed;
                         if constexpr (BLOCKED) run[c * 8 + e] = packed;
                     }
-                    if (last && row < g.m) {
+                    if (last) {
                         const int64_t col = col0 + c * 32;
-                        uint8_t *dst = g.C + row * g.ldc + col;
-                        if (col + 32 <= g.n && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-                            reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                            reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        // warp-uniform: every row of C 16-byte aligned and 32 columns inside
+                        const bool vec = col + 32 <= ti.n &&
+                                         ((reinterpret_cast<uintptr_t>(ti.C) | (uintptr_t)ti.ldc) & 15) == 0;
+                        if (vec) {
+                            if (row < ti.m) {
+                                uint8_t *dst = ti.C + row * ti.ldc + col;
+                                reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                                reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                            }
                         } else {
-                            for (int e = 0; e < 32; ++e)
-                                if (col + e < g.n) dst[e] = (uint8_t)(w[e >> 2] >> (8 * (e & 3)));
+                            // through shared memory: one row segment per store instruction
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) stg[lane * 9 + e] = w[e];
+                            __syncwarp();
+                            const int nr = (int)min((int64_t)32, ti.m - row0);
+                            if (col + lane < ti.n) {
+                                uint8_t *dst = ti.C + row0 * ti.ldc + col + lane;
+                                for (int rr = 0; rr < nr; ++rr, dst += ti.ldc) *dst = stg8[rr * 36 + lane];
+                            }
+                            __syncwarp();
                         }
                     }
                 }
@@ -558,15 +688,16 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <class CFG, bool BLOCKED>
-void launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, int grid, cudaStream_t s) {
+template <class CFG, bool BLOCKED, bool GROUPED = false>
+void launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, int grid, cudaStream_t s,
+                const TcGroupHeader *grp = nullptr) {
     static bool set = false;   // per instantiation
     if (!set) {
-        cudaFuncSetAttribute(tc_f16_kernel<CFG, BLOCKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(tc_f16_kernel<CFG, BLOCKED, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              CFG::SMEM_BYTES);
         set = true;
     }
-    tc_f16_kernel<CFG, BLOCKED><<<grid, NTHREADS, CFG::SMEM_BYTES, s>>>(ma, mb, g);
+    tc_f16_kernel<CFG, BLOCKED, GROUPED><<<grid, NTHREADS, CFG::SMEM_BYTES, s>>>(ma, mb, g, grp);
 }
 
 // Tile width: 256 columns when those tiles fill the GPU, else 128.
@@ -681,6 +812,26 @@ gfp_status launch_tc_f16(uint32_t p, int64_t m, int64_t k, int64_t n, const uint
                          size_t ws_bytes, cudaStream_t s) {
     return launch_tc(p, m, k, n, A, lda, B, ldb, C, ldc, ws, ws_bytes, s, false);
 }
+
+bool tc_make_map_u8(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int box_rows) {
+    return make_map(map, base, rows, kp, box_rows, true);
+}
+
+// Grouped fp8 launch over a schedule prepared by the batched host code: the
+// same kernel, its tiles taken from the schedule (128 x 128 tiles of raw
+// e4m3 operands, 3 stages so that two CTAs share an SM).  Status: *status.
+using TcGroupCfg = TcCfg<128, true, 3>;
+gfp_status launch_tc_grouped(const void *grp, int grid, int *status, cudaStream_t s) {
+    TcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.status = status;
+    CUtensorMap unused;
+    std::memset(&unused, 0, sizeof(unused));
+    launch_cfg<TcGroupCfg, false, true>(unused, unused, g, grid, s, static_cast<const TcGroupHeader *>(grp));
+    return check_launch();
+}
+
+int tc_grouped_ctas_per_sm() { return TcGroupCfg::MINB; }
 
 gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
                         const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,

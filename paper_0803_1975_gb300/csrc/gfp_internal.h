@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "gfp.h"
@@ -74,6 +75,10 @@ size_t tc_f8_workspace(int64_t m, int64_t k, int64_t n);
 gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
                         int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
                         void *ws, size_t ws_bytes, cudaStream_t s);
+// grouped tcgen05 launch (batched.cu builds the schedule; tc_group.h)
+bool tc_make_map_u8(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int box_rows);
+gfp_status launch_tc_grouped(const void *grp, int grid, int *status, cudaStream_t s);
+int tc_grouped_ctas_per_sm();
 int64_t tc_kblock_s32(uint32_t p);      // largest kb with kb ((p-1)/2)^2 + p < 2^30
 int64_t tc_kblock_f32(uint32_t p);      // largest kb (multiple of 128) with kb ((p-1)/2)^2 + p < 2^24
 

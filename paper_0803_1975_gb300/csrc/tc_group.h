@@ -1,0 +1,38 @@
+// Schedule of the grouped tcgen05 launch (written by batched.cu, read by the
+// kernel in gemm_tc_tcgen05.cu).  The raw e4m3 operands of its problems are
+// stacked, K-major, in a few arrays: one per k-stride bin (128 2^b bytes per
+// row), A rows and B^T rows of a problem in the same array, one tensor map
+// per array.  A problem is then a bin and two row offsets.
+#pragma once
+
+#include <cstdint>
+
+namespace gfp {
+
+constexpr int TC_GROUP_BINS = 10;            // row strides 128 .. 65536 bytes
+
+struct alignas(64) TcGroupProblem {          // 64 bytes
+    uint8_t *C;
+    int64_t ldc;
+    int32_t m, n;
+    int32_t rowA0, rowB0;                    // first row of A and of B^T in the bin's array
+    int32_t ktiles, bin;                     // k in 128-element slices; stride bin
+    uint32_t p, off;
+    float scale;
+    uint32_t pad;
+    uint64_t M;
+};
+static_assert(sizeof(TcGroupProblem) == 64, "layout");
+
+struct TcGroupItem {
+    int32_t prob;
+    uint16_t tm, tn;
+};
+
+struct alignas(64) TcGroupHeader {
+    int32_t count, items, grid, nmaps;
+    int64_t off_probs, off_items, off_ranges, off_maps;   // byte offsets from the header
+};
+static_assert(sizeof(TcGroupHeader) == 64, "layout");
+
+}  // namespace gfp

@@ -6,7 +6,9 @@ time (CUDA events, L2 flushed between repetitions) and effective 2mnk/s.
 
 Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8 (gfp_gemm); dot, mixed
 (gfp_gemm_compressed, after packing); batched (the 4096-problem adjacency
-workload, one prepared launch).  Useful for profiling one kernel.
+workload, one prepared launch); pack_rows_rev, pack_cols, pack_rows,
+unpack_rows (the conversions of A, reported in GB/s of bytes moved).  Useful
+for profiling one kernel.
 """
 from __future__ import annotations
 
@@ -30,6 +32,7 @@ def main():
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--algo", default="auto", help="batched: auto, tc_f16, tc_f8 or dot32")
     ap.add_argument("--warmup", type=int, default=1)
     a = ap.parse_args()
     m = a.m or a.size
@@ -51,6 +54,17 @@ def main():
         CB = gfp.gfp_pack(p, B, d, Q, "cols", a.word)
         C = torch.empty((m, n), dtype=torch.uint8, device="cuda")
         fn = lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", a.word, CA, CB, out=C, kb=kb)
+    elif a.form in ("pack_rows_rev", "pack_cols", "pack_rows", "unpack_rows"):
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "dot", a.word)
+        lay = a.form.split("_", 1)[1]
+        if a.form == "unpack_rows":
+            W = gfp.gfp_pack(p, A, d, Q, "rows", a.word)
+            X = torch.empty((m, k), dtype=torch.uint8, device="cuda")
+            fn = lambda: gfp.gfp_unpack(p, W, m, k, d, Q, "rows", a.word, out=X)
+        else:
+            W = gfp.gfp_pack(p, A, d, Q, lay, a.word)
+            fn = lambda: gfp.gfp_pack(p, A, d, Q, lay, a.word, out=W)
+        pack_bytes = m * k + W.numel() * W.element_size()
     elif a.form == "batched":
         # the 4096-problem adjacency workload, one prepared schedule replayed
         items = []
@@ -59,7 +73,7 @@ def main():
             items.append((pp, Ad, Ad, torch.empty(Ah.shape, dtype=torch.uint8, device="cuda")))
         arr, cnt = gfp.make_problems(items)
         ws = torch.empty(gfp.gfp_batched_workspace_size(arr, cnt), dtype=torch.uint8, device="cuda")
-        gfp.gfp_batched_prepare(arr, cnt, "auto", ws)
+        gfp.gfp_batched_prepare(arr, cnt, a.algo, ws)
         m = k = n = 0
         flops_total = sum(2.0 * it[1].shape[0] ** 3 for it in items)
         fn = lambda: gfp.gfp_batched_launch(ws)
@@ -83,8 +97,12 @@ def main():
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = float(np.median(ts))
+    if a.form.startswith(("pack", "unpack")):
+        print(json.dumps({"form": a.form, "word": a.word, "p": p, "rows": m, "cols": k, "ms": round(ms, 5),
+                          "bytes": pack_bytes, "GB_per_s": round(pack_bytes / ms / 1e6, 1)}))
+        return
     flops = flops_total if a.form == "batched" else 2.0 * m * n * k
-    print(json.dumps({"form": a.form, "word": a.word, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
+    print(json.dumps({"form": a.form, "word": a.word, "algo": a.algo, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
                       "T_2mnk_per_s": round(flops / ms / 1e9, 3)}))
 
 

@@ -32,7 +32,7 @@ def random_batch(seed, count, primes=(2, 3, 5, 7, 31, 251), smax=300):
     return items, host_ops
 
 
-@pytest.mark.parametrize("algo", ["tc_f16", "dot32", "auto"])
+@pytest.mark.parametrize("algo", ["tc_f16", "dot32", "tc_f8", "auto"])
 def test_batched_rectangular_mixed_primes(algo):
     items, host_ops = random_batch(11, 120)
     arr, cnt = gfp.make_problems(items)
@@ -49,7 +49,7 @@ def test_batched_worst_case_and_kblocks():
         B = np.full((k, n), p - 1, np.uint8)
         items.append((p, dev(A), dev(B), torch.zeros((m, n), dtype=torch.uint8, device="cuda")))
         refs.append(oracle.gemm(p, A[:1], B)[0])
-    for algo in ("tc_f16", "dot32"):
+    for algo in ("tc_f16", "dot32", "tc_f8"):
         arr, cnt = gfp.make_problems(items)
         gfp.gfp_gemm_batched(arr, cnt, algo)
         for (p, A, B, C), ref in zip(items, refs):
@@ -108,7 +108,7 @@ def test_autotune_then_auto():
     items, host_ops = random_batch(14, 60, primes=(3, 5, 7), smax=520)
     arr, cnt = gfp.make_problems(items)
     table = gfp.gfp_batched_autotune(arr, cnt)
-    assert len(table) == 7 and all(v in (-1, 0, 1, 2, 3) for v in table) and any(v >= 0 for v in table)
+    assert len(table) == 7 and all(v in (-1, 0, 1, 2, 3, 4) for v in table) and any(v >= 0 for v in table)
     for it in items:
         it[3].fill_(255)
     gfp.gfp_gemm_batched(arr, cnt, "auto")
@@ -137,3 +137,39 @@ def test_adjacency_workload_4096():
         assert freivalds(p, A, A, C, rounds=4, seed=i)
         if i in sample or A.shape[0] <= 40:
             assert (C == oracle.gemm(p, A, A)).all(), i
+
+
+def test_batched_tcgen05_tiles_graph_replay():
+    """The grouped tcgen05 tiles (p < 16, raw e4m3 operands): square and
+    rectangular problems around the 128-tile edges, replayed from a graph."""
+    g = np.random.Generator(np.random.PCG64(21))
+    items, host_ops = [], []
+    for p, m, k, n in ((3, 128, 128, 128), (5, 129, 200, 127), (7, 300, 513, 260), (13, 97, 64, 400),
+                       (2, 512, 512, 512), (11, 1, 700, 130)):
+        A = inputs.residues(g, p, m, k)
+        B = inputs.residues(g, p, k, n)
+        items.append((p, dev(A), dev(B), torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A, B))
+    arr, cnt = gfp.make_problems(items)
+    ws = torch.empty(gfp.gfp_batched_workspace_size(arr, cnt), dtype=torch.uint8, device="cuda")
+    gfp.gfp_batched_prepare(arr, cnt, "tc_f8", ws)
+    gfp.gfp_batched_launch(ws)
+    torch.cuda.synchronize()
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all()
+    assert int(ws[192:196].cpu().numpy().view(np.int32)[0]) == 0      # tcgen05 status word
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        gfp.gfp_batched_launch(ws)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        gfp.gfp_batched_launch(ws)
+    for it in items:
+        it[3].fill_(255)
+    graph.replay()
+    torch.cuda.synchronize()
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all()
