@@ -85,9 +85,15 @@ struct ConvJob {             // 48 bytes: one operand to convert
 };
 static_assert(sizeof(ConvJob) == 48, "layout");
 
-struct ConvItem {            // CONV_F16 / CONV_RAW: 16 rows from row0; CONV_RAW_T: a 64 x 64 block
-    int32_t job, row0, col0, pad;
+struct ConvItem {            // CONV_F16 / CONV_RAW: nrows rows from row0; CONV_RAW_T: 128 x 128 of dst
+    int32_t job, row0, col0, nrows;
 };
+
+struct ConvTask {            // 64 bytes: an item with its job, read in one piece by the kernel
+    ConvJob J;
+    int32_t row0, col0, nrows, pad;
+};
+static_assert(sizeof(ConvTask) == 64, "layout");
 
 struct Header {              // 128 bytes at the start of the workspace
     uint32_t magic;
@@ -119,91 +125,180 @@ __device__ __forceinline__ uint32_t s2u(const void *p) {
 }
 
 // ------------------------------------------------------- operand conversion
-// 16 consecutive bytes of a source row from column c (zero past `cols` or
-// outside the matrix).  Inside the row: one vector load when aligned, else
-// five aligned 32-bit loads joined by funnel shifts (an aligned word that
-// holds a byte of the row lies in the same page as that byte, so the load
-// cannot fault); the row's last run is read byte by byte.
-__device__ __forceinline__ uint4 src16(const ConvJob &J, int64_t r, int64_t c) {
-    if (r >= J.rows || c >= J.cols) return make_uint4(0, 0, 0, 0);
-    const uint8_t *p = J.src + r * J.ld + c;
-    if (c + 16 <= J.cols) {
-        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-        if ((a & 15) == 0) return __ldg(reinterpret_cast<const uint4 *>(p));
-        const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~(uintptr_t)3);
-        const uint32_t sh = 8u * (uint32_t)(a & 3);
-        uint32_t x[5];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = __ldg(w + i);
-        x[4] = sh ? __ldg(w + 4) : 0u;
-        return make_uint4(__funnelshift_r(x[0], x[1], sh), __funnelshift_r(x[1], x[2], sh),
-                          __funnelshift_r(x[2], x[3], sh), __funnelshift_r(x[3], x[4], sh));
-    }
-    uint32_t w[4] = {0, 0, 0, 0};
-    for (int e = 0; c + e < J.cols; ++e) w[e >> 2] |= (uint32_t)__ldg(p + e) << (8 * (e & 3));
-    return make_uint4(w[0], w[1], w[2], w[3]);
+// Two residues (bytes b and b+1 of w, selector 0x4140 or 0x4342) as centred
+// fp16 values c = r - p [r > h]: bits 0x6600 + r encode 1536 + r exactly
+// (unit spacing in [1024, 2048)), so subtracting 1536 gives r; the mask of
+// r > h (1 or 0) then takes p off in one fused multiply-add, all exact.
+__device__ __forceinline__ uint32_t centre2(uint32_t w, uint32_t sel, __half2 c1536, __half2 hh, __half2 mp) {
+    const uint32_t bits = __byte_perm(w, 0u, sel) + 0x66006600u;
+    const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&bits), c1536);
+    const __half2 c = __hfma2(__hgt2(r, hh), mp, r);
+    return *reinterpret_cast<const uint32_t *>(&c);
 }
 
-// CONV_F16  : c = r - p [r > h] as fp16 (HMMA tiles), 16 values per step.
+__device__ __forceinline__ void cp_async16_zfill(uint32_t saddr, const void *g, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(g), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// Bytes 16 ch .. 16 ch + 15 of a staged row run whose first byte is buf[d]
+// (the run staged as aligned 16-byte blocks from floor16 of its start), zero
+// from the nvalid-th byte on.
+__device__ __forceinline__ uint4 staged16(const uint8_t *buf, uint32_t d, int ch, int64_t nvalid) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(buf) + (d >> 2) + 4 * ch;
+    const uint32_t sh = 8u * (d & 3u);
+    uint32_t o[4] = {__funnelshift_r(w[0], w[1], sh), __funnelshift_r(w[1], w[2], sh),
+                     __funnelshift_r(w[2], w[3], sh), __funnelshift_r(w[3], w[4], sh)};
+    if (nvalid < 16) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t k = nvalid - 4 * e;
+            o[e] = k <= 0 ? 0u : k >= 4 ? o[e] : (o[e] & ((1u << (8 * k)) - 1u));
+        }
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// CONV_F16  : c = r - p [r > h] as fp16 (HMMA tiles).
 // CONV_RAW  : residue bytes copied (e4m3 codes of r 2^-9 for the tcgen05
-//             tiles), 16 per step.
-// CONV_RAW_T: residue bytes transposed through a 64 x 64 shared tile.
-// Everything of the destination's dcols columns outside the source matrix
-// is written as zero.
-__global__ void __launch_bounds__(256) convert_kernel(const uint8_t *__restrict__ ws) {
-    __shared__ uint32_t tile[64][64 / 4 + 1];   // [source row][4 source columns], padded
+//             tiles).
+//             Both: warp w takes rows row0 + w + 8 g (g < nrows / 8) of the
+//             item and stages runs of up to 512 source bytes of all of them
+//             at once (aligned 16-byte blocks by cp.async, zero-filled where
+//             a block holds no byte of the row -- a block that does cannot
+//             fault), so that one round trip moves up to 2 KB; lanes then
+//             take the (row, 16-byte chunk) pairs in turn.
+// CONV_RAW_T: residue bytes transposed: a 128 x 128 source block is staged
+//             (aligned 16-byte blocks by cp.async, rows keep their
+//             misalignment) and written 4 destination rows x 16 bytes per
+//             thread through 4 x 4 byte transposes.
+// Destination rows below drows, columns below dcols; what lies outside the
+// source matrix is written as zero.
+constexpr int CONV_CTAS_PER_SM = 4;
+constexpr int CONV_WBUF = 2048;            // staging bytes per warp (row runs)
+constexpr int TT_BLK = 9;                  // 16-byte blocks per staged row: 128 bytes from any offset
+constexpr int TT_PITCH = TT_BLK * 16;      // bytes per staged row
+
+__global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(const uint8_t *__restrict__ ws) {
+    // two staging buffers so that one barrier per transposed block suffices
+    __shared__ __align__(16) uint8_t stage[2][128 * TT_PITCH];
+    __shared__ __align__(16) uint8_t dstage[2][128];      // misalignment of each staged row
+    __shared__ __align__(16) uint8_t wbuf[8][CONV_WBUF];  // per warp: staged row runs
+    int tb = 0;
     const Header *H = reinterpret_cast<const Header *>(ws);
-    const ConvJob *jobs = reinterpret_cast<const ConvJob *>(ws + H->off_jobs);
-    const ConvItem *items = reinterpret_cast<const ConvItem *>(ws + H->off_citems);
-    for (int it = blockIdx.x; it < H->ncitems; it += gridDim.x) {
-        const ConvItem ci = items[it];
-        const ConvJob J = jobs[ci.job];
+    const ConvTask *tasks = reinterpret_cast<const ConvTask *>(ws + H->off_citems);
+    const int ntasks = H->ncitems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the next task is read while the current one is converted
+    ConvTask nx;
+    if ((int)blockIdx.x < ntasks) nx = tasks[blockIdx.x];
+    for (int it = blockIdx.x; it < ntasks; it += gridDim.x) {
+        const ConvTask ci = nx;
+        if (it + (int)gridDim.x < ntasks) nx = tasks[it + gridDim.x];
+        const ConvJob &J = ci.J;
         if (J.mode == CONV_RAW_T) {
-            // dst[j][l] = src[l][j]: rows j0 .. j0+63 of dst, columns l0 .. l0+63
+            // dst[j][l] = src[l][j]: dst rows j0 .. j0+127, dst columns l0 .. l0+127
             const int j0 = ci.row0, l0 = ci.col0;
-            const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
-            const uint4 v = src16(J, l0 + r, j0 + q);
-            tile[r][q / 4 + 0] = v.x;
-            tile[r][q / 4 + 1] = v.y;
-            tile[r][q / 4 + 2] = v.z;
-            tile[r][q / 4 + 3] = v.w;
+            uint8_t *st = stage[tb];
+            uint8_t *dst_d = dstage[tb];
+            tb ^= 1;
+            for (int idx = threadIdx.x; idx < 128 * TT_BLK; idx += 256) {
+                const int row = idx / TT_BLK, blk = idx - row * TT_BLK;
+                const int64_t l = l0 + row;
+                const bool row_ok = l < J.rows;
+                const uint8_t *rowp = J.src + (row_ok ? l : 0) * (int64_t)J.ld;
+                const uintptr_t s0 = reinterpret_cast<uintptr_t>(rowp) + (uintptr_t)j0;
+                const uintptr_t ba = (s0 & ~(uintptr_t)15) + 16u * (uint32_t)blk;
+                const bool ok = row_ok && ba < reinterpret_cast<uintptr_t>(rowp) + (uintptr_t)J.cols;
+                cp_async16_zfill(s2u(st + row * TT_PITCH + blk * 16), ok ? reinterpret_cast<const void *>(ba) : J.src,
+                                 ok);
+                if (blk == 0) dst_d[row] = (uint8_t)(s0 & 15);
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncthreads();
-            // thread (r, q): destination row j0 + r, columns l0 + q .. +15,
-            // i.e. byte r of source rows q .. q+15
-            const int wc = r >> 2, sh = 8 * (r & 3);
-            uint32_t w[4] = {0, 0, 0, 0};
+            // thread: dst rows j0 + 4 wc .. +3, dst columns l0 + 16 qg .. +15
+            const int wc = threadIdx.x & 31, qg = threadIdx.x >> 5;
+            if (l0 + 16 * qg < J.dcols && j0 + 4 * wc < J.drows) {
+                uint32_t S[16];
+                const uint4 dv = *reinterpret_cast<const uint4 *>(dst_d + 16 * qg);
+                const uint32_t dw[4] = {dv.x, dv.y, dv.z, dv.w};
 #pragma unroll
-            for (int e = 0; e < 16; ++e) w[e >> 2] |= ((tile[q + e][wc] >> sh) & 0xffu) << (8 * (e & 3));
-            uint8_t *d = static_cast<uint8_t *>(J.dst) + (int64_t)(j0 + r) * J.dld + l0 + q;
-            *reinterpret_cast<uint4 *>(d) = make_uint4(w[0], w[1], w[2], w[3]);
-            __syncthreads();
-            continue;
-        }
-        if (J.mode == CONV_RAW) {
-            const int per_row = J.dcols / 16;
-            for (int idx = threadIdx.x; idx < 16 * per_row; idx += blockDim.x) {
-                const int r = ci.row0 + idx / per_row, c = (idx % per_row) * 16;
-                if (r >= J.drows) break;
-                *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)r * J.dld + c) = src16(J, r, c);
+                for (int e = 0; e < 16; ++e) {
+                    const uint32_t d = (dw[e >> 2] >> (8 * (e & 3))) & 15u;
+                    const uint32_t o = d + 4u * (uint32_t)wc;
+                    const uint32_t *rw = reinterpret_cast<const uint32_t *>(st + (16 * qg + e) * TT_PITCH) + (o >> 2);
+                    S[e] = __funnelshift_r(rw[0], rw[1], 8u * (o & 3u));
+                }
+                uint32_t D[4][4];    // [dst row b][4-column group g]
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const uint32_t t0 = __byte_perm(S[4 * g], S[4 * g + 1], 0x5140);
+                    const uint32_t t1 = __byte_perm(S[4 * g + 2], S[4 * g + 3], 0x5140);
+                    const uint32_t t2 = __byte_perm(S[4 * g], S[4 * g + 1], 0x7362);
+                    const uint32_t t3 = __byte_perm(S[4 * g + 2], S[4 * g + 3], 0x7362);
+                    D[0][g] = __byte_perm(t0, t1, 0x5410);
+                    D[1][g] = __byte_perm(t0, t1, 0x7632);
+                    D[2][g] = __byte_perm(t2, t3, 0x5410);
+                    D[3][g] = __byte_perm(t2, t3, 0x7632);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int j = j0 + 4 * wc + b;
+                    if (j < J.drows)
+                        *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)j * J.dld + l0 + 16 * qg) =
+                            make_uint4(D[b][0], D[b][1], D[b][2], D[b][3]);
+                }
             }
             continue;
         }
-        const uint32_t h = J.p == 2 ? 1u : (J.p - 1) / 2;
-        const int per_row = J.dcols / 16;
-        for (int idx = threadIdx.x; idx < 16 * per_row; idx += blockDim.x) {
-            const int r = ci.row0 + idx / per_row, c = (idx % per_row) * 16;
-            if (r >= J.drows) break;
-            const uint4 v = src16(J, r, c);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-            __align__(16) __half o[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const uint32_t q = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
-                o[e] = __int2half_rn((int)q - (q > h ? (int)J.p : 0));
+        // CONV_RAW and CONV_F16
+        const int rend = min(J.drows, ci.row0 + ci.nrows);
+        uint8_t *buf = wbuf[warp];
+        const bool f16 = J.mode == CONV_F16;
+        const float hf = J.p == 2 ? 1.f : (float)((J.p - 1) / 2);
+        const __half2 c1536 = __floats2half2_rn(1536.f, 1536.f);
+        const __half2 hh = __floats2half2_rn(hf, hf);
+        const __half2 mp = __floats2half2_rn(-(float)J.p, -(float)J.p);
+        const int L = min(J.dcols, 512), cpr = L / 16, nb = cpr + 1;   // chunks and blocks per run
+        const int G = ci.nrows / 8;                                    // rows of this warp
+        const uint32_t mnb = 0xFFFFFFFFu / (uint32_t)nb + 1u, mcpr = 0xFFFFFFFFu / (uint32_t)cpr + 1u;
+        for (int c0 = 0; c0 < J.dcols; c0 += 512) {
+            for (int b = lane; b < G * nb; b += 32) {
+                const int g = (int)__umulhi((uint32_t)b, mnb), blk = b - g * nb;
+                const int64_t r = ci.row0 + warp + 8 * g;
+                const bool row_ok = r < rend && r < J.rows;
+                const uint8_t *rowp = J.src + (row_ok ? r : 0) * (int64_t)J.ld;
+                const uintptr_t ba = ((reinterpret_cast<uintptr_t>(rowp) + (uintptr_t)c0) & ~(uintptr_t)15) +
+                                     16u * (uint32_t)blk;
+                const bool ok = row_ok && ba < reinterpret_cast<uintptr_t>(rowp) + (uintptr_t)J.cols;
+                cp_async16_zfill(s2u(buf + 16 * b), ok ? reinterpret_cast<const void *>(ba) : J.src, ok);
             }
-            uint4 *d = reinterpret_cast<uint4 *>(static_cast<__half *>(J.dst) + (int64_t)r * J.dld + c);
-            d[0] = reinterpret_cast<const uint4 *>(o)[0];
-            d[1] = reinterpret_cast<const uint4 *>(o)[1];
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncwarp();
+            for (int q = lane; q < G * cpr; q += 32) {
+                const int g = (int)__umulhi((uint32_t)q, mcpr), ch = q - g * cpr;
+                const int r = ci.row0 + warp + 8 * g;
+                const int c = c0 + 16 * ch;
+                if (r >= rend || c >= J.dcols) continue;
+                const uint32_t d =
+                    (uint32_t)((reinterpret_cast<uintptr_t>(J.src) + (uintptr_t)((int64_t)r * J.ld + c0)) & 15);
+                const uint4 v = staged16(buf + 16 * nb * g, d, ch, (int64_t)J.cols - c);
+                if (!f16) {
+                    *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)r * J.dld + c) = v;
+                } else {
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        o[2 * e] = centre2(w[e], 0x4140u, c1536, hh, mp);
+                        o[2 * e + 1] = centre2(w[e], 0x4342u, c1536, hh, mp);
+                    }
+                    uint4 *dp = reinterpret_cast<uint4 *>(static_cast<__half *>(J.dst) + (int64_t)r * J.dld + c);
+                    dp[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                    dp[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            __syncwarp();   // the next step reuses the buffer
         }
     }
 }
@@ -493,7 +588,7 @@ int default_kind(int64_t m, int64_t k, int64_t n, uint32_t p) {
     const int b = bucket_of(m, k, n);
     if (g_tuned[b] >= 0) return g_tuned[b];
     const int64_t s = std::max(m, n);
-    if (p < 16 && s > 96) return KIND_TC8;       // tcgen05 tiles (falls back when not eligible)
+    if (p < 16) return KIND_TC8;                 // tcgen05 tiles (falls back when not eligible)
     return s <= 48 ? KIND_HMMA32 : s <= 160 ? KIND_HMMA64 : KIND_HMMA128;
 }
 
@@ -530,8 +625,9 @@ bool dot32_params(uint32_t p, int64_t k, int *t_out, int *d_out, int *kbw_out) {
 
 struct TcHostProb {                          // a problem of the grouped tcgen05 launch
     int bin;                                 // k-stride bin of its operands
-    int32_t rowA0, rowB0, ktiles;            // rows in the bin's array, k in 128-slices
-    int64_t m, n, ldc;
+    int32_t rowA0, rowB0, ktiles, klast;     // rows in the bin's array, k in 128-slices,
+                                             // 32-wide MMAs of the last slice
+    int64_t m, n, k, ldc;
     uint8_t *C;
     uint32_t p;
 };
@@ -559,6 +655,13 @@ struct Plan {
 };
 
 int64_t round_to(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+// Rows of a row-wise conversion item: 8 warps, each staging as many runs of
+// up to 512 bytes (plus one alignment block) as fit its buffer, 16 at most.
+int conv_rows_per_item(int32_t dcols) {
+    const int nb = std::min<int32_t>(dcols, 512) / 16 + 1;
+    return 8 * std::max(1, std::min(16, CONV_WBUF / (16 * nb)));
+}
 
 // fp32-exact k-block of the raw e4m3 products (residues r < 16 uncentred)
 int64_t tc8_kmax(uint32_t p) {
@@ -638,31 +741,24 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         J.ld = ld;
         J.p = p;
         J.mode = mode;
-        const int es = mode == CONV_F16 ? 2 : 1;
-        if (mode == CONV_RAW_T) {                // destination is the transpose
-            J.drows = (int32_t)round_to(cols, rpad);
-            J.dld = (int32_t)round_to(rows, cpad);
-        } else {
-            J.drows = (int32_t)round_to(rows, rpad);
-            J.dld = (int32_t)round_to(cols, cpad);
-        }
+        J.drows = (int32_t)round_to(rows, rpad);
+        J.dld = (int32_t)round_to(cols, cpad);
         J.dcols = J.dld;
         const int64_t off = plan.ops_bytes;
         J.dst = reinterpret_cast<void *>((uintptr_t)off);
-        plan.ops_bytes += round_to((int64_t)J.drows * J.dld * es, 256);
+        plan.ops_bytes += round_to((int64_t)J.drows * J.dld * 2, 256);
         const int jid = (int)plan.jobs.size();
         plan.jobs.push_back(J);
-        if (mode == CONV_RAW_T) {
-            for (int32_t r = 0; r < J.drows; r += 64)
-                for (int32_t c = 0; c < J.dld; c += 64) plan.citems.push_back(ConvItem{jid, r, c, 0});
-        } else {
-            for (int32_t r = 0; r < J.drows; r += 16) plan.citems.push_back(ConvItem{jid, r, 0, 0});
-        }
+        const int nr = conv_rows_per_item(J.dcols);
+        for (int32_t r = 0; r < J.drows; r += nr) plan.citems.push_back(ConvItem{jid, r, 0, nr});
         seen[key] = off;
         return off;
     };
-    // tcgen05 operands: raw bytes, K-major, k padded to 128, rows padded to
-    // 128, stacked in the array of the k-stride bin; returns the first row
+    // tcgen05 operands: raw bytes, K-major, k padded to 32, stacked row after
+    // row in the array of the k-stride bin; returns the first row.  Rows are
+    // not padded: an output entry depends on one row of A and one row of B^T
+    // only, so the rows of a neighbour that a 128-row tile also covers reach
+    // only outputs outside the product, which are never stored.
     std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, int>, int64_t> tc_seen;
     auto tc_job = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld, uint32_t p, int mode,
                       int64_t k) -> int64_t {
@@ -678,18 +774,19 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         J.p = p;
         J.mode = mode;
         J.dld = (int32_t)(128 << bin);
-        J.dcols = (int32_t)round_to(k, 128);
-        J.drows = (int32_t)round_to(mode == CONV_RAW_T ? cols : rows, 128);
+        J.dcols = (int32_t)round_to(k, 32);
+        J.drows = mode == CONV_RAW_T ? cols : rows;
         const int jid = (int)plan.jobs.size();
         plan.jobs.push_back(J);
         const int64_t row0 = plan.bin_rows[bin];
         plan.bin_rows[bin] += J.drows;
         plan.tc_places.push_back(TcJobPlace{jid, bin, row0});
         if (mode == CONV_RAW_T) {
-            for (int32_t r = 0; r < J.drows; r += 64)
-                for (int32_t c = 0; c < J.dcols; c += 64) plan.citems.push_back(ConvItem{jid, r, c, 0});
+            for (int32_t r = 0; r < J.drows; r += 128)
+                for (int32_t c = 0; c < J.dcols; c += 128) plan.citems.push_back(ConvItem{jid, r, c, 128});
         } else {
-            for (int32_t r = 0; r < J.drows; r += 16) plan.citems.push_back(ConvItem{jid, r, 0, 0});
+            const int nr = conv_rows_per_item(J.dcols);
+        for (int32_t r = 0; r < J.drows; r += nr) plan.citems.push_back(ConvItem{jid, r, 0, nr});
         }
         tc_seen[key] = row0;
         return row0;
@@ -731,10 +828,12 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             TcHostProb T{};
             T.bin = tc8_bin(q.k);
             T.ktiles = (int32_t)(round_to(q.k, 128) / 128);
+            T.klast = (int32_t)((round_to(q.k, 32) - 128 * (T.ktiles - 1)) / 32);
             T.rowA0 = (int32_t)tc_job(q.A, q.m, q.k, q.lda, q.p, CONV_RAW, q.k);
             T.rowB0 = (int32_t)tc_job(q.B, q.k, q.n, q.ldb, q.p, CONV_RAW_T, q.k);
             T.m = q.m;
             T.n = q.n;
+            T.k = q.k;
             T.ldc = q.ldc;
             T.C = q.C;
             T.p = q.p;
@@ -817,7 +916,7 @@ Layout layout_of(int64_t nprobs, int64_t nitems, int grid, int64_t njobs, int64_
     L.items = o;    o += align256(nitems * sizeof(Item));
     L.ranges = o;   o += align256((grid + 1) * sizeof(int32_t));
     L.jobs = o;     o += align256(njobs * sizeof(ConvJob));
-    L.citems = o;   o += align256(ncitems * sizeof(ConvItem));
+    L.citems = o;   o += align256(ncitems * sizeof(ConvTask));
     L.tcprobs = o;  o += align256(ntc * sizeof(TcGroupProblem));
     L.tcitems = o;  o += align256(ntcitems * sizeof(TcGroupItem));
     L.tcranges = o; o += align256((tc_grid + 1) * sizeof(int32_t));
@@ -913,11 +1012,14 @@ gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
         Q.rowA0 = T.rowA0;
         Q.rowB0 = T.rowB0;
         Q.ktiles = T.ktiles;                 // one k-block: k <= tc8_kmax(p) by eligibility
+        Q.klast = T.klast;
+        // sums below 2^23 units: the epilogue reads them from a mantissa
+        Q.red = (int64_t)T.k * (T.p - 1) * (T.p - 1) < ((int64_t)1 << 23) ? 1 : 0;
         Q.bin = map_of[T.bin];
         Q.p = T.p;
-        Q.off = (uint32_t)((((int64_t)1 << 24) + T.p - 1) / T.p * T.p);
+        Q.off = 0;                           // raw residues: every sum is >= 0
         Q.scale = 262144.0f;                 // raw e4m3: values r 2^-9
-        Q.M = fastmod_magic(T.p);
+        Q.m32 = (uint32_t)(0xFFFFFFFFull / T.p + 1);
     }
     std::vector<uint8_t> host((size_t)L.ops, 0);   // the operand area itself is written by the launch
     std::memcpy(host.data(), &H, sizeof(H));
@@ -929,7 +1031,16 @@ gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
     put(L.items, plan.items.data(), plan.items.size() * sizeof(Item));
     put(L.ranges, plan.ranges.data(), plan.ranges.size() * sizeof(int32_t));
     put(L.jobs, plan.jobs.data(), plan.jobs.size() * sizeof(ConvJob));
-    put(L.citems, plan.citems.data(), plan.citems.size() * sizeof(ConvItem));
+    std::vector<ConvTask> tasks(plan.citems.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const ConvItem &c = plan.citems[i];
+        tasks[i].J = plan.jobs[c.job];
+        tasks[i].row0 = c.row0;
+        tasks[i].col0 = c.col0;
+        tasks[i].nrows = c.nrows;
+        tasks[i].pad = 0;
+    }
+    put(L.citems, tasks.data(), tasks.size() * sizeof(ConvTask));
     put(L.tcprobs, tcp.data(), tcp.size() * sizeof(TcGroupProblem));
     put(L.tcitems, plan.tc_items.data(), plan.tc_items.size() * sizeof(TcGroupItem));
     put(L.tcranges, plan.tc_ranges.data(), plan.tc_ranges.size() * sizeof(int32_t));
@@ -957,7 +1068,7 @@ gfp_status launch_plan(void *ws, cudaStream_t s) {
     uint8_t *base = static_cast<uint8_t *>(ws);
     // operand conversion (a grid-stride loop over the jobs' items; it reads
     // their count from the workspace), then the grouped products
-    convert_kernel<<<std::max(1, num_sms() * 4), 256, 0, s>>>(base);
+    convert_kernel<<<std::max(1, num_sms() * CONV_CTAS_PER_SM), 256, 0, s>>>(base);
     gfp_status st = check_launch();
     if (st != GFP_OK) return st;
     if (simt) {

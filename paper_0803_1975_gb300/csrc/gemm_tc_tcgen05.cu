@@ -184,8 +184,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t fastmod(uint32_t a, uint64_t M, uint32_t p) {
-    return (uint32_t)__umul64hi(M * (uint64_t)a, (uint64_t)p);
+// x mod p for an accumulated integer x, |x| < 2^24.  a = x + off >= 0, off
+// a multiple of p (0 when x >= 0), a < 2^25 + p.  With m32 = ceil(2^32 / p)
+// = (2^32 + e) / p, 0 <= e < p, umulhi(a, m32) = floor(a / p + a e / (p 2^32))
+// and a e / (p 2^32) < 2^-7, so the quotient estimate is floor(a / p) or one
+// more, and a single correction of the remainder suffices.
+__device__ __forceinline__ uint32_t mod_acc(int x, uint32_t off, uint32_t m32, uint32_t p) {
+    const int a = x + (int)off;
+    const int r = a - (int)(__umulhi((uint32_t)a, m32) * p);
+    return (uint32_t)(r < 0 ? r + (int)p : r);
 }
 
 struct TcArgs {
@@ -195,8 +202,9 @@ struct TcArgs {
     int ktiles;        // k in stage slices (128 bytes of k)
     int kb_tiles;      // k-block in stage slices
     int kblocks;       // ceil(ktiles / kb_tiles)
-    uint32_t p, off;   // off = p ceil(2^24 / p): makes |x| < 2^24 non-negative
-    uint64_t M;        // fastmod magic of p
+    uint32_t p, off;   // off = p ceil(2^24 / p) makes |x| < 2^24 non-negative (0: x >= 0)
+    uint32_t m32;      // ceil(2^32 / p)
+    int red;           // 1: raw operands and every k-block sum < 2^23 units of 2^-18
     float scale;       // 1, or 2^18 for raw e4m3 operands (values r 2^-9)
     int *status;
 };
@@ -229,10 +237,11 @@ struct TileInfo {
     const CUtensorMap *map;    // grouped: the tensor map of the problem's stride bin
     int rowA0, rowB0;
     int ktiles, kb_tiles, kblocks;
+    int klast;                 // 32-byte MMAs of the last k slice (the others take ROWB / 32)
+    int red;                   // reduction of the accumulator: see TcArgs::red
     uint8_t *C;
     int64_t ldc, m, n;
-    uint32_t p, off;
-    uint64_t M;
+    uint32_t p, off, m32;
     float scale;
 };
 
@@ -276,13 +285,15 @@ struct TileWalk {
             t.ktiles = np.ktiles;
             t.kb_tiles = np.ktiles;
             t.kblocks = 1;
+            t.klast = np.klast;
+            t.red = np.red;
             t.C = np.C;
             t.ldc = np.ldc;
             t.m = np.m;
             t.n = np.n;
             t.p = np.p;
             t.off = np.off;
-            t.M = np.M;
+            t.m32 = np.m32;
             t.scale = np.scale;
             cur += 1;
             if (cur < end) fetch(cur);
@@ -294,13 +305,15 @@ struct TileWalk {
             t.ktiles = g.ktiles;
             t.kb_tiles = g.kb_tiles;
             t.kblocks = g.kblocks;
+            t.klast = ROWB / 32;
+            t.red = g.red;
             t.C = g.C;
             t.ldc = g.ldc;
             t.m = g.m;
             t.n = g.n;
             t.p = g.p;
             t.off = g.off;
-            t.M = g.M;
+            t.m32 = g.m32;
             t.scale = g.scale;
             cur += gridDim.x;
         }
@@ -432,10 +445,13 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         }
                         fence_after();
                         const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+                        // the last slice of a grouped product may hold fewer written columns
+                        const int nkk = kt == ti.ktiles - 1 ? ti.klast : ROWB / 32;
 #pragma unroll
                         for (int kk = 0; kk < ROWB / 32; ++kk)   // 32 bytes of k per MMA
-                            mma_issue<CFG::FP8>(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
-                                                CFG::IDESC, (kt > k0 || kk > 0) ? 1u : 0u);
+                            if (kk < nkk)
+                                mma_issue<CFG::FP8>(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
+                                                    CFG::IDESC, (kt > k0 || kk > 0) ? 1u : 0u);
                         mma_commit(empty_bar(stage));
                         if (++stage == STAGES) {
                             stage = 0;
@@ -495,19 +511,34 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * (uint32_t)BN + c * 32, v);
                     uint32_t w[8];
+                    uint32_t rr32[32];
+                    if (ti.red) {
+                        // raw sums x < 2^23 held as v = x 2^-18: v + 32 lies in [32, 64),
+                        // where the mantissa counts units of 2^-18, so it is x exactly
+                        // (0x42000000 encodes 32); the quotient estimate is exact for x < 2^32 / p
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u;
+                            rr32[i] = x - __umulhi(x, ti.m32) * ti.p;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * ti.scale), ti.off, ti.m32, ti.p);
+                    }
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        uint32_t packed = 0;
+                        uint32_t r[4];
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
-                            const int x = __float2int_rn(__uint_as_float(v[e * 4 + b]) * ti.scale);
-                            uint32_t r = fastmod((uint32_t)x + ti.off, ti.M, ti.p);
+                            r[b] = rr32[e * 4 + b];
                             if constexpr (BLOCKED) {
-                                r += (run[c * 8 + e] >> (8 * b)) & 0xffu;
-                                r = r >= ti.p ? r - ti.p : r;
+                                r[b] += (run[c * 8 + e] >> (8 * b)) & 0xffu;
+                                r[b] = r[b] >= ti.p ? r[b] - ti.p : r[b];
                             }
-                            packed |= r << (8 * b);
                         }
+                        const uint32_t packed =
+                            __byte_perm(__byte_perm(r[0], r[1], 0x0040), __byte_perm(r[2], r[3], 0x0040), 0x5410);
                         w[e] = packed;
                         if constexpr (BLOCKED) run[c * 8 + e] = packed;
                     }
@@ -530,6 +561,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             const int nr = (int)min((int64_t)32, ti.m - row0);
                             if (col + lane < ti.n) {
                                 uint8_t *dst = ti.C + row0 * ti.ldc + col + lane;
+#pragma unroll 4
                                 for (int rr = 0; rr < nr; ++rr, dst += ti.ldc) *dst = stg8[rr * 36 + lane];
                             }
                             __syncwarp();
@@ -769,8 +801,11 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     if (g.kb_tiles < 1) g.kb_tiles = 1;
     g.kblocks = (g.ktiles + g.kb_tiles - 1) / g.kb_tiles;
     g.p = p;
-    g.off = (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);
-    g.M = fastmod_magic(p);
+    g.off = raw ? 0u : (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);   // raw products are >= 0
+    g.m32 = (uint32_t)(0xFFFFFFFFull / p + 1);
+    // raw sums of a k-block below 2^23 units: read from a mantissa in the epilogue
+    const int64_t kb_elems = std::min<int64_t>(kp, (int64_t)g.kb_tiles * bke);
+    g.red = raw && kb_elems * (int64_t)(p - 1) * (p - 1) < ((int64_t)1 << 23) ? 1 : 0;
     g.scale = raw ? 262144.0f : 1.0f;
     g.status = status;
     const int tiles = g.tiles_m * g.tiles_n;

@@ -2,7 +2,8 @@
 // kernel in gemm_tc_tcgen05.cu).  The raw e4m3 operands of its problems are
 // stacked, K-major, in a few arrays: one per k-stride bin (128 2^b bytes per
 // row), A rows and B^T rows of a problem in the same array, one tensor map
-// per array.  A problem is then a bin and two row offsets.
+// per array.  A problem is then a bin and two row offsets; only its first
+// k (rounded up to 32) columns are written.
 #pragma once
 
 #include <cstdint>
@@ -17,10 +18,11 @@ struct alignas(64) TcGroupProblem {          // 64 bytes
     int32_t m, n;
     int32_t rowA0, rowB0;                    // first row of A and of B^T in the bin's array
     int32_t ktiles, bin;                     // k in 128-element slices; stride bin
-    uint32_t p, off;
+    uint32_t p, off;                         // off: 0 (raw products are non-negative)
     float scale;
-    uint32_t pad;
-    uint64_t M;
+    uint32_t m32;                            // ceil(2^32 / p)
+    int32_t klast;                           // 32-wide MMAs in the last k slice (1-4)
+    int32_t red;                             // 1: every sum < 2^23 units (mantissa read)
 };
 static_assert(sizeof(TcGroupProblem) == 64, "layout");
 

@@ -173,3 +173,33 @@ def test_batched_tcgen05_tiles_graph_replay():
     torch.cuda.synchronize()
     for (p, A, B), (_, _, _, C) in zip(host_ops, items):
         assert (host(C) == oracle.gemm(p, A, B)).all()
+
+
+def test_batched_tcgen05_garbage_workspace():
+    """Stacked tcgen05 operands are not padded: rows of neighbouring
+    problems and unwritten columns share the 128 x 128 boxes.  A workspace
+    filled with 0xFF (an e4m3 NaN code) before preparation must not change
+    any stored output: k around multiples of 32 and 128, m and n around the
+    tile edges, shared operands, several stride bins."""
+    g = np.random.Generator(np.random.PCG64(22))
+    items, host_ops = [], []
+    shared = inputs.residues(g, 7, 140, 33)
+    for p, m, k, n in ((3, 97, 1, 200), (5, 130, 31, 99), (7, 140, 33, 150), (13, 200, 129, 129),
+                       (11, 255, 257, 97), (2, 128, 1000, 300), (3, 300, 96, 101), (5, 101, 160, 400)):
+        A = inputs.residues(g, p, m, k)
+        B = inputs.residues(g, p, k, n)
+        items.append((p, dev(A), dev(B), torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A, B))
+    Sd = dev(shared)
+    for n in (97, 250):                               # one A, two products
+        B = inputs.residues(g, 7, 33, n)
+        items.append((7, Sd, dev(B), torch.full((140, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((7, shared, B))
+    arr, cnt = gfp.make_problems(items)
+    ws = torch.full((gfp.gfp_batched_workspace_size(arr, cnt),), 255, dtype=torch.uint8, device="cuda")
+    gfp.gfp_batched_prepare(arr, cnt, "tc_f8", ws)
+    gfp.gfp_batched_launch(ws)
+    torch.cuda.synchronize()
+    assert int(ws[192:196].cpu().numpy().view(np.int32)[0]) == 0
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all(), (p, A.shape, B.shape)
