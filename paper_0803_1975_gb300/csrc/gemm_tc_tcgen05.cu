@@ -171,6 +171,31 @@ __device__ __forceinline__ void fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// tcgen05.ld without the wait: the registers are written asynchronously and
+// must not be read before tmem_wait(v), which names them as operands so that
+// the compiler keeps every use of them after it.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
+                   "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]),
+                   "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]),
+                   "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -505,12 +530,47 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 // rows of this warp and 32-column chunks inside the product (warp-uniform)
                 const int64_t row0 = (int64_t)ti.tm * BM + q * 32;
                 const int nchunks = row0 >= ti.m ? 0 : (int)min((int64_t)(BN / 32), (ti.n - col0 + 31) / 32);
+                // the load of chunk c + 1 is in flight while chunk c is reduced and stored
+                auto store_chunk = [&](int c, const uint32_t(&w)[8]) {
+                    const int64_t col = col0 + c * 32;
+                    // warp-uniform: every row of C 16-byte aligned and 32 columns inside
+                    const bool vec = col + 32 <= ti.n &&
+                                     ((reinterpret_cast<uintptr_t>(ti.C) | (uintptr_t)ti.ldc) & 15) == 0;
+                    if (vec) {
+                        if (row < ti.m) {
+                            uint8_t *dst = ti.C + row * ti.ldc + col;
+                            reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
+                    } else {
+                        // through shared memory: one row segment per store instruction
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) stg[lane * 9 + e] = w[e];
+                        __syncwarp();
+                        const int nr = (int)min((int64_t)32, ti.m - row0);
+                        if (col + lane < ti.n) {
+                            // all 32 shared loads first, then the stores
+                            uint8_t bt[32];
+#pragma unroll
+                            for (int rr = 0; rr < 32; ++rr) bt[rr] = stg8[rr * 36 + lane];
+                            uint8_t *dst = ti.C + row0 * ti.ldc + col + lane;
+#pragma unroll
+                            for (int rr = 0; rr < 32; ++rr, dst += ti.ldc)
+                                if (rr < nr) *dst = bt[rr];
+                        }
+                        __syncwarp();
+                    }
+                };
+                uint32_t vn[32];
+                if (nchunks > 0) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN, vn);
 #pragma unroll
                 for (int c = 0; c < BN / 32; ++c) {
                     if (c >= nchunks) break;
                     uint32_t v[32];
-                    tmem_ld32(tmem + lane_addr + buf * (uint32_t)BN + c * 32, v);
-                    uint32_t w[8];
+                    tmem_wait(vn);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = vn[i];
+                    if (c + 1 < nchunks) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN + (c + 1) * 32, vn);
                     uint32_t rr32[32];
                     if (ti.red) {
                         // raw sums x < 2^23 held as v = x 2^-18: v + 32 lies in [32, 64),
@@ -526,6 +586,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         for (int i = 0; i < 32; ++i)
                             rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * ti.scale), ti.off, ti.m32, ti.p);
                     }
+                    uint32_t w[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         uint32_t r[4];
@@ -542,31 +603,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         w[e] = packed;
                         if constexpr (BLOCKED) run[c * 8 + e] = packed;
                     }
-                    if (last) {
-                        const int64_t col = col0 + c * 32;
-                        // warp-uniform: every row of C 16-byte aligned and 32 columns inside
-                        const bool vec = col + 32 <= ti.n &&
-                                         ((reinterpret_cast<uintptr_t>(ti.C) | (uintptr_t)ti.ldc) & 15) == 0;
-                        if (vec) {
-                            if (row < ti.m) {
-                                uint8_t *dst = ti.C + row * ti.ldc + col;
-                                reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                                reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                            }
-                        } else {
-                            // through shared memory: one row segment per store instruction
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) stg[lane * 9 + e] = w[e];
-                            __syncwarp();
-                            const int nr = (int)min((int64_t)32, ti.m - row0);
-                            if (col + lane < ti.n) {
-                                uint8_t *dst = ti.C + row0 * ti.ldc + col + lane;
-#pragma unroll 4
-                                for (int rr = 0; rr < nr; ++rr, dst += ti.ldc) *dst = stg8[rr * 36 + lane];
-                            }
-                            __syncwarp();
-                        }
-                    }
+                    if (last) store_chunk(c, w);
                 }
                 fence_before();
                 __syncwarp();
