@@ -273,10 +273,19 @@ def batched_measure(gfp, torch, flush):
     with torch.cuda.graph(graph):
         gfp.gfp_batched_launch(ws)
     ms = event_time(torch, graph.replay, 7, flush)
+    # kinds in use: the tuned kind of every size bucket that holds a problem
+    kinds = set()
+    for p, A in probs:
+        n = A.shape[0]
+        b = 0 if n <= 32 else 1 if n <= 64 else 2 if n <= 128 else 3 if n <= 256 else 4 if n <= 512 else 5
+        k = table[b]
+        kinds.add(k if k >= 0 else (4 if p < 16 else 0))
+    kernels = 1 + (1 if kinds & {0, 1, 2, 3} else 0) + (1 if 4 in kinds else 0)
     return {"problems": cnt, "sum_2n3": flops, "ms": round(ms, 4), "value": round(flops / ms / 1e9, 3),
-            "unit": UNIT, "launches_per_replay": 2,
+            "unit": UNIT, "kernels_per_replay": kernels,
             "autotuned_kinds": [gfp.BATCHED_KINDS.get(v, None) for v in table],
-            "note": "one graph replay = operand conversion kernel + one persistent grouped product kernel"}
+            "note": "one graph replay = operand conversion kernel, then one persistent grouped kernel per "
+                    "engine in use: tcgen05 e4m3 tiles (p < 16) and/or mma.sync / Q-adic SIMT tiles"}
 
 
 # ---------------------------------------------------------------------------
