@@ -182,6 +182,29 @@ GFP_API gfp_status gfp_params(uint32_t p, int64_t m, int64_t k, int64_t n,
                               gfp_form form, gfp_word word,
                               int *d, uint64_t *Q, int64_t *kb);
 
+/* Value-aware parameters (Section 2.4 with the operands' largest entries in
+ * place of p-1).  The bound of eq. (lower) comes from the largest product of
+ * two entries: with entries of A at most amax_a and of B at most amax_b it
+ * reads k amax_a amax_b < Q (0/1 adjacency matrices: k < Q), and packed
+ * words hold digits up to max(amax_a, amax_b).  A smaller Q leaves room for
+ * more coefficients per word.  amax_a, amax_b <= p - 1 (gfp_params is the
+ * case amax_a = amax_b = p - 1); that the entries respect them is a
+ * precondition of the products made with the result, like entries < p for
+ * every call (gfp_amax measures it).  Otherwise as gfp_params; additionally
+ * GFP_EINVAL when amax_a or amax_b exceeds p - 1. */
+GFP_API gfp_status gfp_params_vb(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                 gfp_form form, gfp_word word,
+                                 uint32_t amax_a, uint32_t amax_b,
+                                 int *d, uint64_t *Q, int64_t *kb);
+
+/* Largest entry of a uint8 matrix X (rows x cols, leading dimension ldx
+ * bytes), written to *out, a DEVICE pointer to one uint32 (0 for an empty
+ * matrix).  Asynchronous on `stream`; no library counterpart in the paper:
+ * it measures the amax bounds of gfp_params_vb.  Errors: GFP_EINVAL (null
+ * pointer with a non-empty matrix, ldx < cols), GFP_ECUDA. */
+GFP_API gfp_status gfp_amax(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx,
+                            uint32_t *out, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Conversions (Section 2.1 INIT, Table 2 INIT_e / EXTRACT_e)                */
 /* ------------------------------------------------------------------------ */
@@ -197,6 +220,13 @@ GFP_API gfp_status gfp_pack(uint32_t p, int64_t rows, int64_t cols,
                             const uint8_t *X, int64_t ldx,
                             int d, uint64_t Q, gfp_layout lay, gfp_word word,
                             void *W, int64_t ldw, void *stream);
+
+/* gfp_pack for entries at most amax (<= p - 1): the word bound becomes
+ * amax (1+...+Q^d) and amax < Q (the parameters of gfp_params_vb). */
+GFP_API gfp_status gfp_pack_vb(uint32_t p, uint32_t amax, int64_t rows, int64_t cols,
+                               const uint8_t *X, int64_t ldx,
+                               int d, uint64_t Q, gfp_layout lay, gfp_word word,
+                               void *W, int64_t ldw, void *stream);
 
 /* Inverse of gfp_pack: rows x cols residues X from the words W.  Every
  * coefficient of every word must be < Q (true of gfp_pack output and of the
@@ -287,6 +317,17 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
                                        const void *CB, int64_t ldb,
                                        void *C, int64_t ldc, int64_t kb,
                                        void *stream);
+
+/* gfp_gemm_compressed with (d, Q, kb) validated against the value-aware bound
+ * k amax_a amax_b < Q of gfp_params_vb (entries of A at most amax_a, of B at
+ * most amax_b, a precondition).  The kernels are the same. */
+GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                          int d, uint64_t Q, gfp_form form, gfp_word word,
+                                          uint32_t amax_a, uint32_t amax_b,
+                                          const void *CA_or_A, int64_t lda,
+                                          const void *CB, int64_t ldb,
+                                          void *C, int64_t ldc, int64_t kb,
+                                          void *stream);
 
 /* Full compression (Section 4): both outer dimensions packed.  With
  * Theta = Q^(dq+1) (the smallest Theta of eq. (qtheta)):

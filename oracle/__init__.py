@@ -256,13 +256,20 @@ def unpack_block(W: np.ndarray, rows: int, cols: int, dq: int, dth: int, Q: int)
 # --------------------------------------------------------------------------
 # Bounds of the paper
 # --------------------------------------------------------------------------
-def lower_bound_holds(p: int, k: int, Q: int) -> bool:
+def lower_bound_holds(p: int, k: int, Q: int, amax_a: int | None = None, amax_b: int | None = None) -> bool:
     """Equation (lower), Section 2.4: with delayed reduction every
     coefficient of the accumulated word products stays below Q iff
     k (p-1)^2 < Q.  The inequality is strict, as the equation prints it
     (Table 1 prints the dimensions with <=; the strict form is the one that
-    holds, see tests/test_oracle_dqt.py)."""
-    return k * (p - 1) ** 2 < Q
+    holds, see tests/test_oracle_dqt.py).
+
+    The argument uses only that every entry lies in [0, p-1]; with entries
+    of A at most amax_a and of B at most amax_b (value-aware reading, e.g.
+    0/1 adjacency matrices) a coefficient is at most k amax_a amax_b, and
+    the bound reads k amax_a amax_b < Q."""
+    a = p - 1 if amax_a is None else amax_a
+    b = p - 1 if amax_b is None else amax_b
+    return k * a * b < Q
 
 
 def upper_bound_holds(Q: int, d: int, beta: int = 53) -> bool:
@@ -283,9 +290,10 @@ def full_bounds_hold(p: int, k: int, Q: int, dq: int, Theta: int, dth: int,
             and Q ** ((dq + 1) * (dth + 1)) < 2 ** beta)
 
 
-def amax(p: int, Q: int, d: int) -> int:
-    """Largest packed word: all d+1 residues equal to p-1."""
-    return (p - 1) * sum(Q ** s for s in range(d + 1))
+def amax(p: int, Q: int, d: int, v: int | None = None) -> int:
+    """Largest packed word: all d+1 residues equal to p-1 (or to v, the
+    largest entry of the packed matrix when it is known to be smaller)."""
+    return (p - 1 if v is None else v) * sum(Q ** s for s in range(d + 1))
 
 
 # Machine words offered by the library.  The paper gives the bounds for a
@@ -315,28 +323,33 @@ WORDS_MIXED = ("u64", "f64")
 
 
 def word_admissible(form: str, word: str, p: int, k: int, d: int, Q: int,
-                    kb: int | None = None) -> bool:
+                    kb: int | None = None, amax_a: int | None = None, amax_b: int | None = None) -> bool:
     """True when (p, k, d, Q) gives exact results for `form` ('dot' or
     'mixed') in `word`.  kb, when given, is the k-block after which the dot
     form extracts the coefficient of Q^d and restarts the word sum; the lower
     bound then applies to kb and the extracted coefficients are summed in
-    32 bits, which needs k (p-1)^2 < 2^32."""
+    32 bits, which needs k (p-1)^2 < 2^32.  amax_a, amax_b: the largest
+    entries of A and B when known to be below p-1 (see lower_bound_holds);
+    the packed words then hold digits up to max(amax_a, amax_b)."""
     if p < 2 or d < 0 or Q < 2 or Q & (Q - 1):
         return False
+    a = p - 1 if amax_a is None else amax_a
+    b = p - 1 if amax_b is None else amax_b
+    v = max(a, b)
     t = Q.bit_length() - 1
     kk = k if kb is None else kb
     if kb is not None:
-        if form != "dot" or kb < 1 or k * (p - 1) ** 2 >= 2 ** 32:
+        if form != "dot" or kb < 1 or k * a * b >= 2 ** 32:
             return False
-    if not lower_bound_holds(p, kk, Q):
+    if not lower_bound_holds(p, kk, Q, a, b):
         return False
     if form == "dot":
         if word == "u64":
-            return t * (d + 1) <= 64 and amax(p, Q, d) < 2 ** 64
+            return t * (d + 1) <= 64 and amax(p, Q, d, v) < 2 ** 64
         if word == "u64x128":
-            return amax(p, Q, d) < 2 ** 64 and t * (d + 1) <= 128
+            return amax(p, Q, d, v) < 2 ** 64 and t * (d + 1) <= 128
         if word == "u32w":
-            return amax(p, Q, d) < 2 ** 32 and t * (d + 1) <= 64
+            return amax(p, Q, d, v) < 2 ** 32 and t * (d + 1) <= 64
         if word == "u32":
             return t * (d + 1) <= 32
         if word == "f64":
@@ -366,19 +379,23 @@ def full_admissible(word: str, p: int, k: int, dq: int, dth: int, Q: int) -> boo
     return False
 
 
-def choose(form: str, word: str, p: int, k: int, kb: int | None = None):
-    """Smallest Q = 2^t that satisfies (lower) for k (or kb), then the largest
-    d the word admits for that Q.  Returns (d, Q) or None."""
+def choose(form: str, word: str, p: int, k: int, kb: int | None = None,
+           amax_a: int | None = None, amax_b: int | None = None):
+    """Smallest Q = 2^t that satisfies (lower) for k (or kb) and holds every
+    entry as a digit, then the largest d the word admits for that Q.
+    Returns (d, Q) or None."""
+    a = p - 1 if amax_a is None else amax_a
+    b = p - 1 if amax_b is None else amax_b
     kk = k if kb is None else kb
     t = 1
-    while not lower_bound_holds(p, kk, 2 ** t):
+    while not lower_bound_holds(p, max(kk, 1), 2 ** t, a, b) or max(a, b) >= 2 ** t:
         t += 1
         if t > 64:
             return None
     Q = 2 ** t
     best = None
     for d in range(0, 64):
-        if word_admissible(form, word, p, k, d, Q, kb):
+        if word_admissible(form, word, p, k, d, Q, kb, a, b):
             best = d
     return None if best is None else (best, Q)
 

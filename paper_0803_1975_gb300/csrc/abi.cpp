@@ -55,8 +55,14 @@ GFP_API int gfp_last_cuda_error(void) { return g_last_cuda_error; }
 GFP_API gfp_status gfp_pack(uint32_t p, int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx,
                             int d, uint64_t Q, gfp_layout lay, gfp_word word, void *W, int64_t ldw,
                             void *stream) {
+    return gfp_pack_vb(p, p - 1, rows, cols, X, ldx, d, Q, lay, word, W, ldw, stream);
+}
+
+GFP_API gfp_status gfp_pack_vb(uint32_t p, uint32_t amax, int64_t rows, int64_t cols, const uint8_t *X,
+                               int64_t ldx, int d, uint64_t Q, gfp_layout lay, gfp_word word, void *W,
+                               int64_t ldw, void *stream) {
     if (rows < 0 || cols < 0 || !valid_layout(lay) || word_bytes(word) == 0) return GFP_EINVAL;
-    gfp_status st = check_pack(p, d, Q, word);
+    gfp_status st = check_pack_vb(p, amax, d, Q, word);
     if (st != GFP_OK) return st;
     if (rows == 0 || cols == 0) return GFP_OK;
     int64_t wr, wc;
@@ -157,10 +163,26 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
                                        const void *CA_or_A, int64_t lda, const void *CB,
                                        int64_t ldb, void *C, int64_t ldc, int64_t kb,
                                        void *stream) {
+    return gfp_gemm_compressed_vb(p, m, k, n, d, Q, form, word, p - 1, p - 1, CA_or_A, lda, CB, ldb, C,
+                                  ldc, kb, stream);
+}
+
+GFP_API gfp_status gfp_amax(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, uint32_t *out,
+                            void *stream) {
+    if (rows < 0 || cols < 0 || !out) return GFP_EINVAL;
+    if (rows > 0 && cols > 0 && (!X || ldx < cols)) return GFP_EINVAL;
+    return launch_amax(rows, cols, X, ldx, out, (cudaStream_t)stream);
+}
+
+GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int64_t n, int d,
+                                          uint64_t Q, gfp_form form, gfp_word word, uint32_t amax_a,
+                                          uint32_t amax_b, const void *CA_or_A, int64_t lda,
+                                          const void *CB, int64_t ldb, void *C, int64_t ldc, int64_t kb,
+                                          void *stream) {
     if (m < 0 || k < 0 || n < 0 || kb < 0) return GFP_EINVAL;
     if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED && form != GFP_FORM_LEFT) return GFP_EINVAL;
     if (word_bytes(word) == 0) return GFP_EINVAL;
-    gfp_status st = check_dqt(p, k, d, Q, form, word, kb);
+    gfp_status st = check_dqt_vb(p, k, d, Q, form, word, kb, amax_a, amax_b);
     if (st != GFP_OK) return st;
     if (m == 0 || n == 0) return GFP_OK;
     const int t = log2_exact(Q);

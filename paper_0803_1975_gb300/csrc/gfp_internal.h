@@ -24,9 +24,16 @@ bool is_prime_small(uint32_t p);       // p prime and 2 <= p <= 251
 int log2_exact(uint64_t Q);            // t with Q = 2^t, or -1
 // Largest packed word (p-1)(1+Q+...+Q^d) compared with 2^bits: true when < 2^bits.
 bool amax_below(uint32_t p, int t, int d, int bits);
+bool amax_below_v(uint32_t v, int t, int d, int bits);   // v (1+Q+...+Q^d) < 2^bits
 gfp_status check_dqt(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gfp_word word,
                      int64_t kb);
+// The same with entries of A at most va and of B at most vb (both <= p - 1).
+gfp_status check_dqt_vb(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gfp_word word,
+                        int64_t kb, uint32_t va, uint32_t vb);
 gfp_status check_pack(uint32_t p, int d, uint64_t Q, gfp_word word);
+gfp_status check_pack_vb(uint32_t p, uint32_t v, int d, uint64_t Q, gfp_word word);
+gfp_status launch_amax(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, uint32_t *out,
+                       cudaStream_t s);
 size_t word_bytes(gfp_word w);
 
 // Lemire, Kaser, Kurz, "Faster remainder by direct computation" (2019):

@@ -250,4 +250,28 @@ gfp_status launch_block(bool pack, int64_t rows, int64_t cols, const uint8_t *X,
     return check_launch();
 }
 
+// Largest entry of a uint8 matrix (the amax bounds of the value-aware
+// parameters): rows in a grid-stride loop, a warp maximum, one atomicMax per
+// warp on the zeroed result.
+__global__ void amax_kernel(const uint8_t *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                            uint32_t *out) {
+    uint32_t mx = 0;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const uint8_t *row = X + r * ldx;
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) mx = max(mx, (uint32_t)row[c]);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+gfp_status launch_amax(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, uint32_t *out,
+                       cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (rows == 0 || cols == 0) return GFP_OK;
+    const int64_t grid = rows < (int64_t)num_sms() * 8 ? rows : (int64_t)num_sms() * 8;
+    amax_kernel<<<(unsigned)grid, 256, 0, s>>>(X, rows, cols, ldx, out);
+    return check_launch();
+}
+
 }  // namespace gfp

@@ -3,7 +3,10 @@
 // Bounds (Dumas, Fousse, Salvy, arXiv 0803.1975):
 //  * eq. (lower), Section 2.4: with delayed reduction every coefficient of
 //    the accumulated word products stays below Q when k (p-1)^2 < Q (strict).
-//    With a k-block kb the same bound applies to kb.
+//    With a k-block kb the same bound applies to kb.  The argument only uses
+//    that entries lie in [0, p-1]; with entries of A at most a and of B at
+//    most b (0/1 adjacency matrices: a = b = 1) it gives k a b < Q, and the
+//    packed words hold digits up to max(a, b).
 //  * eq. (upper), Section 2.5: Q^(d+1) < 2^beta for a beta-bit mantissa.
 //  * integer words: the coefficient of Q^d occupies bits [t d, t(d+1)); it
 //    is exact when the accumulator keeps those bits (t(d+1) <= 64 for a
@@ -34,8 +37,8 @@ int log2_exact(uint64_t Q) {
 // (p-1)(1 + Q + ... + Q^d) < 2^bits, with Q = 2^t, computed without overflow:
 // the sum has its top set bit at t d + bitlen(p-1) - 1 at most, and equals
 // (p-1) 2^(t d) + lower terms < (p-1) 2^(t d) + 2^(t d) = p 2^(t d).
-bool amax_below(uint32_t p, int t, int d, int bits) {
-    // exact test: (p-1) * sum_{s<=d} 2^(t s) < 2^bits
+bool amax_below_v(uint32_t v, int t, int d, int bits) {
+    // exact test: v * sum_{s<=d} 2^(t s) < 2^bits
     // iterate with 128-bit integers while the value is small enough
     unsigned __int128 lim = 0;
     if (bits >= 128) return (int64_t)t * d + 9 <= 127;
@@ -44,10 +47,12 @@ bool amax_below(uint32_t p, int t, int d, int bits) {
     for (int s = 0; s <= d; ++s) {
         if ((int64_t)t * s >= bits) return false;
         sum += (unsigned __int128)1 << (t * s);
-        if (sum * (p - 1) >= lim) return false;
+        if (sum * v >= lim) return false;
     }
-    return sum * (p - 1) < lim;
+    return sum * v < lim;
 }
+
+bool amax_below(uint32_t p, int t, int d, int bits) { return amax_below_v(p - 1, t, d, bits); }
 
 size_t word_bytes(gfp_word w) {
     switch (w) {
@@ -60,30 +65,48 @@ size_t word_bytes(gfp_word w) {
     return 0;
 }
 
-static bool lower_ok(uint32_t p, int64_t k, int t) {
-    // k (p-1)^2 < 2^t
+// k a b < 2^t with a b = prod
+static bool lower_ok_prod(uint64_t prod, int64_t k, int t) {
     if (k < 0) return false;
-    unsigned __int128 lhs = (unsigned __int128)k * (p - 1) * (p - 1);
+    unsigned __int128 lhs = (unsigned __int128)k * prod;
     if (t >= 100) return true;
     return lhs < ((unsigned __int128)1 << t);
 }
 
-// Storage bound of a packed word (needed by pack/unpack as well).
-gfp_status check_pack(uint32_t p, int d, uint64_t Q, gfp_word word) {
+static bool lower_ok(uint32_t p, int64_t k, int t) {   // k (p-1)^2 < 2^t
+    return lower_ok_prod((uint64_t)(p - 1) * (p - 1), k, t);
+}
+
+// Storage bound of a packed word whose digits are at most v (needed by
+// pack/unpack as well).
+gfp_status check_pack_vb(uint32_t p, uint32_t v, int d, uint64_t Q, gfp_word word) {
     if (!is_prime_small(p)) return GFP_EPRIME;
+    if (v > p - 1) return GFP_EINVAL;
     int t = log2_exact(Q);
     if (t < 0) return GFP_EQ;
     if (d < 0 || d > 255) return GFP_EINVAL;
     if (word_bytes(word) == 0) return GFP_EINVAL;
-    if ((uint64_t)(p - 1) >= Q) return GFP_EBOUND;   // a residue must be a digit
+    if ((uint64_t)v >= Q) return GFP_EBOUND;   // an entry must be a digit
     int bits = word == GFP_WORD_F64 ? 53 : (int)(8 * word_bytes(word));
-    if (!amax_below(p, t, d, bits)) return GFP_EBOUND;
+    if (!amax_below_v(v, t, d, bits)) return GFP_EBOUND;
     return GFP_OK;
+}
+
+gfp_status check_pack(uint32_t p, int d, uint64_t Q, gfp_word word) {
+    return check_pack_vb(p, p - 1, d, Q, word);
 }
 
 gfp_status check_dqt(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gfp_word word,
                      int64_t kb) {
+    return check_dqt_vb(p, k, d, Q, form, word, kb, p - 1, p - 1);
+}
+
+gfp_status check_dqt_vb(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gfp_word word,
+                        int64_t kb, uint32_t va, uint32_t vb) {
     if (!is_prime_small(p)) return GFP_EPRIME;
+    if (va > p - 1 || vb > p - 1) return GFP_EINVAL;
+    const uint64_t prod = (uint64_t)va * vb;
+    const uint32_t vmax = va > vb ? va : vb;
     int t = log2_exact(Q);
     if (t < 0) return GFP_EQ;
     if (k < 0 || d < 0 || d > 255 || kb < 0) return GFP_EINVAL;
@@ -98,21 +121,21 @@ gfp_status check_dqt(uint32_t p, int64_t k, int d, uint64_t Q, gfp_form form, gf
     }
     if (blocked) {
         // the extracted coefficients are summed in 32 bits
-        unsigned __int128 tot = (unsigned __int128)k * (p - 1) * (p - 1);
+        unsigned __int128 tot = (unsigned __int128)k * prod;
         if (tot >= ((unsigned __int128)1 << 32)) return GFP_EBOUND;
     }
-    if (!lower_ok(p, blocked ? kb : k, t)) return GFP_EBOUND;
+    if (!lower_ok_prod(prod, blocked ? kb : k, t)) return GFP_EBOUND;
     const int64_t td1 = (int64_t)t * (d + 1);
     if (form == GFP_FORM_DOT) {
         switch (word) {
             case GFP_WORD_U64:
-                if (td1 > 64 || !amax_below(p, t, d, 64)) return GFP_EBOUND;
+                if (td1 > 64 || !amax_below_v(vmax, t, d, 64)) return GFP_EBOUND;
                 break;
             case GFP_WORD_U64X128:
-                if (td1 > 128 || !amax_below(p, t, d, 64)) return GFP_EBOUND;
+                if (td1 > 128 || !amax_below_v(vmax, t, d, 64)) return GFP_EBOUND;
                 break;
             case GFP_WORD_U32W:
-                if (td1 > 64 || !amax_below(p, t, d, 32)) return GFP_EBOUND;
+                if (td1 > 64 || !amax_below_v(vmax, t, d, 32)) return GFP_EBOUND;
                 break;
             case GFP_WORD_U32:
                 if (td1 > 32) return GFP_EBOUND;
@@ -170,17 +193,26 @@ GFP_API size_t gfp_word_bytes(gfp_word word) { return word_bytes(word); }
 
 GFP_API gfp_status gfp_params(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_form form,
                               gfp_word word, int *d, uint64_t *Q, int64_t *kb) {
+    return gfp_params_vb(p, m, k, n, form, word, p - 1, p - 1, d, Q, kb);
+}
+
+GFP_API gfp_status gfp_params_vb(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_form form,
+                                 gfp_word word, uint32_t amax_a, uint32_t amax_b, int *d, uint64_t *Q,
+                                 int64_t *kb) {
     if (!d || !Q || !kb) return GFP_EINVAL;
     if (m < 0 || k < 0 || n < 0) return GFP_EINVAL;
     if (form != GFP_FORM_DOT && form != GFP_FORM_MIXED && form != GFP_FORM_LEFT) return GFP_EINVAL;
     if (word_bytes(word) == 0) return GFP_EINVAL;
     if (!is_prime_small(p)) return GFP_EPRIME;
-    if (*d >= 0) return check_dqt(p, k, *d, *Q, form, word, *kb);
+    if (amax_a > p - 1 || amax_b > p - 1) return GFP_EINVAL;
+    if (*d >= 0) return check_dqt_vb(p, k, *d, *Q, form, word, *kb, amax_a, amax_b);
     if (form != GFP_FORM_DOT && *kb > 0) return GFP_EUNSUPPORTED;
-    // choose
+    // choose: the smallest Q for (lower), then the largest d the word admits
+    const uint64_t prod = (uint64_t)amax_a * amax_b;
+    const uint32_t vmax = amax_a > amax_b ? amax_a : amax_b;
     const int64_t kreq = (*kb > 0 && *kb < k) ? *kb : k;
     int t = 1;
-    while (!lower_ok(p, kreq > 0 ? kreq : 1, t) || (uint64_t)(p - 1) >= (1ull << t)) {
+    while (!lower_ok_prod(prod, kreq > 0 ? kreq : 1, t) || (uint64_t)vmax >= (1ull << t)) {
         if (++t > 62) return GFP_EBOUND;
     }
     const uint64_t QQ = 1ull << t;
@@ -191,7 +223,7 @@ GFP_API gfp_status gfp_params(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_f
             kbb = (*kb / (dd + 1)) * (dd + 1);
             if (kbb == 0) break;
         }
-        if (check_dqt(p, k, dd, QQ, form, word, kbb) == GFP_OK) best = dd;
+        if (check_dqt_vb(p, k, dd, QQ, form, word, kbb, amax_a, amax_b) == GFP_OK) best = dd;
     }
     if (best < 0) return form != GFP_FORM_DOT && word != GFP_WORD_U64 && word != GFP_WORD_F64
                              ? GFP_EUNSUPPORTED

@@ -36,7 +36,7 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_batched_workspace_size", "gfp_gemm_batched", "gfp_batched_prepare",
            "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table",
            "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
-           "gfp_unpack_block")
+           "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax")
 
 
 class GfpError(RuntimeError):
@@ -83,6 +83,16 @@ def load():
     L.gfp_params.restype = st
     L.gfp_pack.argtypes = [u32, i64, i64, vp, i64, ip, u64, ip, ip, vp, i64, vp]
     L.gfp_pack.restype = st
+    L.gfp_params_vb.argtypes = [u32, i64, i64, i64, ip, ip, u32, u32, ctypes.POINTER(ip), ctypes.POINTER(u64),
+                                ctypes.POINTER(i64)]
+    L.gfp_params_vb.restype = st
+    L.gfp_pack_vb.argtypes = [u32, u32, i64, i64, vp, i64, ip, u64, ip, ip, vp, i64, vp]
+    L.gfp_pack_vb.restype = st
+    L.gfp_gemm_compressed_vb.argtypes = [u32, i64, i64, i64, ip, u64, ip, ip, u32, u32, vp, i64, vp, i64, vp,
+                                         i64, i64, vp]
+    L.gfp_gemm_compressed_vb.restype = st
+    L.gfp_amax.argtypes = [i64, i64, vp, i64, vp, vp]
+    L.gfp_amax.restype = st
     L.gfp_unpack.argtypes = [u32, i64, i64, vp, i64, ip, u64, ip, ip, vp, i64, vp]
     L.gfp_unpack.restype = st
     L.gfp_gemm_workspace_size.argtypes = [u32, i64, i64, i64, ip, ctypes.POINTER(ctypes.c_size_t)]
@@ -135,7 +145,8 @@ def _stream(t: torch.Tensor | None = None, stream=None):
 def _mat(t: torch.Tensor, dtype, name: str):
     if t.dtype != dtype:
         raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
-    if t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+    # the column stride matters only when a row holds more than one entry
+    if t.dim() != 2 or not t.is_cuda or (t.numel() > 0 and t.shape[1] > 1 and t.stride(1) != 1):
         raise ValueError("%s must be a 2-D CUDA tensor with unit column stride" % name)
     return ctypes.c_void_p(t.data_ptr()), max(t.stride(0), t.shape[1], 1)
 
@@ -157,6 +168,30 @@ def gfp_params(p: int, m: int, k: int, n: int, form: str = "dot", word: str = "u
     return dd.value, QQ.value, kk.value
 
 
+def gfp_params_vb(p: int, m: int, k: int, n: int, amax_a: int, amax_b: int, form: str = "dot",
+                  word: str = "u64", d: int | None = None, Q: int | None = None, kb: int = 0):
+    """gfp_params with entries of A at most amax_a and of B at most amax_b."""
+    L = load()
+    dd = ctypes.c_int(-1 if d is None else d)
+    QQ = ctypes.c_uint64(0 if Q is None else Q)
+    kk = ctypes.c_int64(kb)
+    _check(L.gfp_params_vb(p, m, k, n, FORMS[form], WORDS[word], amax_a, amax_b, ctypes.byref(dd),
+                           ctypes.byref(QQ), ctypes.byref(kk)), "gfp_params_vb")
+    return dd.value, QQ.value, kk.value
+
+
+def gfp_amax(X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Largest entry of a uint8 matrix, as a one-element int32 CUDA tensor
+    (written asynchronously)."""
+    L = load()
+    rows, cols = X.shape
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=X.device)
+    xp, ldx = _mat(X, torch.uint8, "X")
+    _check(L.gfp_amax(rows, cols, xp, ldx, out.data_ptr(), _stream(X, stream)), "gfp_amax")
+    return out
+
+
 def packed_shape(layout: str, rows: int, cols: int, d: int):
     if layout == "cols":
         return cdiv(rows, d + 1), cols
@@ -164,7 +199,8 @@ def packed_shape(layout: str, rows: int, cols: int, d: int):
 
 
 def gfp_pack(p: int, X: torch.Tensor, d: int, Q: int, layout: str, word: str = "u64",
-             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+             out: torch.Tensor | None = None, stream=None, amax: int | None = None) -> torch.Tensor:
+    """Pack X; with amax (<= p - 1) the word bounds of gfp_pack_vb apply."""
     L = load()
     rows, cols = X.shape
     wr, wc = packed_shape(layout, rows, cols, d)
@@ -172,8 +208,12 @@ def gfp_pack(p: int, X: torch.Tensor, d: int, Q: int, layout: str, word: str = "
         out = torch.empty((wr, wc), dtype=WORD_DTYPE[word], device=X.device)
     xp, ldx = _mat(X, torch.uint8, "X")
     wp, ldw = _mat(out, WORD_DTYPE[word], "W")
-    _check(L.gfp_pack(p, rows, cols, xp, ldx, d, Q, LAYOUTS[layout], WORDS[word], wp, ldw,
-                      _stream(X, stream)), "gfp_pack")
+    if amax is None:
+        _check(L.gfp_pack(p, rows, cols, xp, ldx, d, Q, LAYOUTS[layout], WORDS[word], wp, ldw,
+                          _stream(X, stream)), "gfp_pack")
+    else:
+        _check(L.gfp_pack_vb(p, amax, rows, cols, xp, ldx, d, Q, LAYOUTS[layout], WORDS[word], wp, ldw,
+                             _stream(X, stream)), "gfp_pack_vb")
     return out
 
 
@@ -288,17 +328,23 @@ def gfp_gemm_noalloc(p: int, A: torch.Tensor, B: torch.Tensor, out: torch.Tensor
     bp, ldb = _mat(B, torch.uint8, "B")
     cp, ldc = _mat(out, torch.uint8, "C")
     _check(L.gfp_gemm_noalloc(p, m, k, n, ap, lda, bp, ldb, cp, ldc, _stream(A, stream)),
-           "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
-           "gfp_unpack_block")
+           "gfp_gemm_noalloc")
     return out
 
 
 def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: str, word: str,
                         CA_or_A: torch.Tensor, CB: torch.Tensor, out: torch.Tensor | None = None,
-                        kb: int = 0, stream=None) -> torch.Tensor:
+                        kb: int = 0, stream=None, amax=None) -> torch.Tensor:
     """form 'dot': CA (ROWS_REV words) x CB (COLS words) -> uint8 C (m x n).
-    form 'mixed': uint8 A x CB (ROWS words) -> CC words (m x ceil(n/(d+1)))."""
+    form 'mixed': uint8 A x CB (ROWS words) -> CC words (m x ceil(n/(d+1))).
+    amax = (amax_a, amax_b): validate against the value-aware bound
+    (gfp_gemm_compressed_vb)."""
     L = load()
+    if amax is not None:
+        va, vb = amax
+        fn = lambda *a: L.gfp_gemm_compressed_vb(*a[:8], va, vb, *a[8:])
+    else:
+        fn = L.gfp_gemm_compressed
     wdt = WORD_DTYPE[word]
     if form == "dot":
         ap, lda = _mat(CA_or_A, wdt, "CA")
@@ -311,8 +357,8 @@ def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: st
             out = torch.empty((cdiv(m, d + 1), n), dtype=wdt, device=CB.device)
         cp, ldc = _mat(out, wdt, "CC")
         bp, ldb = _mat(CB, torch.uint8, "B")
-        _check(L.gfp_gemm_compressed(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
-                                     ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
+        _check(fn(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
+                  ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
         return out
     else:
         ap, lda = _mat(CA_or_A, torch.uint8, "A")
@@ -320,8 +366,8 @@ def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: st
             out = torch.empty((m, cdiv(n, d + 1)), dtype=wdt, device=CB.device)
         cp, ldc = _mat(out, wdt, "CC")
     bp, ldb = _mat(CB, wdt, "CB")
-    _check(L.gfp_gemm_compressed(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
-                                 ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
+    _check(fn(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
+              ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
     return out
 
 

@@ -171,3 +171,34 @@ def test_full_params_match_oracle(L):
                             assert e.status == 3
                             got = False
                         assert got == ok, (word, p, k, a, b)
+
+
+def test_value_aware_chooser_and_validator_match_oracle(L):
+    """gfp_params_vb chooses what the oracle chooses for every (form, word,
+    p, k, amax_a, amax_b) of a sweep and accepts exactly what it admits;
+    amax = p - 1 is gfp_params; amax above p - 1 is GFP_EINVAL."""
+    for form, words in (("dot", oracle.WORDS_DOT), ("mixed", oracle.WORDS_MIXED)):
+        for word in words:
+            for p in (3, 7, 31):
+                for k in (1, 17, 1024, 8192):
+                    for a, b in ((1, 1), (p - 1, 1), (1, p - 1), (p - 1, p - 1), (2, 2)):
+                        ref = oracle.choose(form, word, p, k, amax_a=a, amax_b=b)
+                        d, Q, kb = gfp.gfp_params_vb(p, 8, k, 8, a, b, form, word)
+                        assert ref == (d, Q), (form, word, p, k, a, b)
+                        for dd in (d - 1, d, d + 1):
+                            for QQ in (Q // 2, Q, 2 * Q):
+                                if dd < 0 or QQ < 2:
+                                    continue
+                                ok = oracle.word_admissible(form, word, p, k, dd, QQ, amax_a=a, amax_b=b)
+                                try:
+                                    gfp.gfp_params_vb(p, 8, k, 8, a, b, form, word, d=dd, Q=QQ)
+                                    got = True
+                                except gfp.GfpError as e:
+                                    assert e.status == 3
+                                    got = False
+                                assert got == ok, (form, word, p, k, a, b, dd, QQ)
+    assert gfp.gfp_params_vb(5, 8, 1000, 8, 4, 4) == gfp.gfp_params(5, 8, 1000, 8)
+    for a, b in ((5, 1), (1, 5)):
+        with pytest.raises(gfp.GfpError) as e:
+            gfp.gfp_params_vb(5, 8, 1000, 8, a, b)
+        assert e.value.status == 1

@@ -404,3 +404,66 @@ def test_full_word_product_equals_block_of_C():
             assert w == int(want[u, v])
             assert w < 2 ** 64
     assert not oracle.full_admissible("u64", p, 200, dq, dth + 1, Q)     # 10 * 2 * 4 = 80 bits
+
+
+# ---- value-aware bounds (Section 2.4 with the entries' largest values) ----
+
+def test_value_aware_bound_is_tight_for_0_1_inputs():
+    """All-ones vectors (the largest 0/1 inputs): every coefficient of the
+    accumulated word products is at most k, so k < Q is exact and k = Q
+    carries into the next coefficient -- the bound k amax_a amax_b < Q is
+    the tight one for amax = 1, where k (p-1)^2 < Q would ask for a Q
+    (p-1)^2 times larger."""
+    for p in (3, 5, 7):
+        for t, d in ((6, 2), (9, 4), (11, 4)):
+            Q = 2 ** t
+            ones = np.ones(Q - 1, dtype=np.int64)
+            assert oracle.lower_bound_holds(p, Q - 1, Q, 1, 1)
+            assert not oracle.lower_bound_holds(p, Q - 1, Q)
+            assert oracle.dqt_dot(ones, ones, p, d, Q) == (Q - 1) % p
+            over = np.ones(Q, dtype=np.int64)
+            assert not oracle.lower_bound_holds(p, Q, Q, 1, 1)
+            assert oracle.dqt_dot(over, over, p, d, Q) != Q % p
+
+
+def test_value_aware_bound_closed_form_and_mixed_bounds():
+    """lower_bound_holds with amax_a, amax_b is k amax_a amax_b < Q; with
+    amax = p - 1 it is eq. (lower); a matrix of (p-1) times a 0/1 matrix
+    (the second product of a chain) needs k (p-1) < Q."""
+    for p in (3, 7, 31):
+        for k in (1, 5, 100, 1000):
+            for t in range(1, 24):
+                Q = 2 ** t
+                assert oracle.lower_bound_holds(p, k, Q, 1, 1) == (k < Q)
+                assert oracle.lower_bound_holds(p, k, Q, p - 1, 1) == (k * (p - 1) < Q)
+                assert oracle.lower_bound_holds(p, k, Q, p - 1, p - 1) == oracle.lower_bound_holds(p, k, Q)
+    # worst case of a residue matrix times a 0/1 matrix, exact at the bound
+    p, t, d = 7, 12, 3
+    Q = 2 ** t
+    kmax = (Q - 1) // (p - 1)
+    a = np.full(kmax, p - 1)
+    b = np.ones(kmax, dtype=np.int64)
+    assert oracle.dqt_dot(a, b, p, d, Q) == (kmax * (p - 1)) % p
+    a2 = np.full(kmax + 1, p - 1)
+    b2 = np.ones(kmax + 1, dtype=np.int64)
+    assert kmax * (p - 1) < Q <= (kmax + 1) * (p - 1)
+    assert oracle.dqt_dot(a2, b2, p, d, Q) != ((kmax + 1) * (p - 1)) % p
+
+
+def test_value_aware_chooser_gains_compression():
+    """0/1 inputs at p = 7, k = 1024: the smallest Q is 2^11 (k < Q) instead
+    of 2^16 (36 k < Q), so 64-bit words hold 5 residues instead of 4 and
+    FP64 words 4 instead of 3 (Q^(d+1) < 2^53)."""
+    assert oracle.choose("dot", "u64", 7, 1024) == (3, 2 ** 16)
+    assert oracle.choose("dot", "u64", 7, 1024, amax_a=1, amax_b=1) == (4, 2 ** 11)
+    assert oracle.choose("dot", "f64", 7, 1024) == (2, 2 ** 16)
+    assert oracle.choose("dot", "f64", 7, 1024, amax_a=1, amax_b=1) == (3, 2 ** 11)
+    # brute force: the chosen Q is the smallest power of two above k amax_a amax_b
+    for k in (1, 2, 3, 100, 1023, 1024, 5000):
+        for a, b in ((1, 1), (6, 1), (1, 6), (2, 3)):
+            d, Q = oracle.choose("dot", "u64", 7, k, amax_a=a, amax_b=b)
+            t = Q.bit_length() - 1
+            assert k * a * b < Q and max(a, b) < Q
+            assert t == 1 or not (k * a * b < Q // 2 and max(a, b) < Q // 2)
+            assert oracle.word_admissible("dot", "u64", 7, k, d, Q, amax_a=a, amax_b=b)
+            assert not oracle.word_admissible("dot", "u64", 7, k, d + 1, Q, amax_a=a, amax_b=b)

@@ -51,3 +51,17 @@ def test_noalloc_rejects_problems_beyond_the_scratch():
     A = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
     C = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
     assert call_noalloc(L, 3, A, A, C) == 7
+
+
+def test_noalloc_python_binding():
+    """The binding's wrapper of the same entry point (argument marshalling
+    only) returns the oracle's product and raises on a rejected size."""
+    ensure_built()
+    g = inputs.rng(60, 7)
+    A_h = inputs.residues(g, 5, 70, 90)
+    B_h = inputs.residues(g, 5, 90, 33)
+    C = gfp.gfp_gemm_noalloc(5, dev(A_h), dev(B_h))
+    assert (host(C) == oracle.gemm(5, A_h, B_h)).all()
+    A = torch.zeros((4096, 4096), dtype=torch.uint8, device="cuda")
+    with pytest.raises(gfp.GfpError):
+        gfp.gfp_gemm_noalloc(3, A, A)
