@@ -329,6 +329,32 @@ GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int6
                                           void *C, int64_t ldc, int64_t kb,
                                           void *stream);
 
+/* Strassen-Winograd over the packed words of the dot form (the paper's
+ * remark on fast matrix multiplication, Section 5).  With 64-bit words
+ * (t(d+1) <= 64) the coefficient of Q^d is exact modulo 2^64, so only the
+ * word product mod 2^64 matters, and Winograd's 7-multiplication scheme is
+ * an identity over the ring Z/2^64: `levels` levels of it (stopping early
+ * once a side falls below 512 words) on the words, with wrapping additions,
+ * give the classical product's words and digits exactly.  Operands as
+ * gfp_gemm_compressed(GFP_FORM_DOT, GFP_WORD_U64): CA m x ceil(k/(d+1))
+ * words (ROWS_REV of A, lda words), CB ceil(k/(d+1)) x n words (COLS of B,
+ * ldb words), C m x n uint8 (ldc bytes).  (d, Q) must satisfy the bounds of
+ * gfp_params for (DOT, U64) without k-blocking.  The workspace (device,
+ * caller-owned, gfp_winograd_workspace_size bytes) holds the m x n result
+ * words and each level's sums and products; nothing is allocated, so the
+ * call can be captured in a CUDA graph.  levels = 0 is the classical word
+ * product with one digit pass.  Errors: GFP_EINVAL, GFP_EPRIME, GFP_EQ,
+ * GFP_EBOUND, GFP_EWORKSPACE, GFP_ECUDA. */
+GFP_API gfp_status gfp_winograd_workspace_size(int64_t m, int64_t k, int64_t n, int d, int levels,
+                                               size_t *bytes);
+GFP_API gfp_status gfp_gemm_compressed_winograd(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                                int d, uint64_t Q,
+                                                const void *CA, int64_t lda,
+                                                const void *CB, int64_t ldb,
+                                                uint8_t *C, int64_t ldc, int levels,
+                                                void *workspace, size_t ws_bytes,
+                                                void *stream);
+
 /* Full compression (Section 4): both outer dimensions packed.  With
  * Theta = Q^(dq+1) (the smallest Theta of eq. (qtheta)):
  *  CA : ceil(m/(dq+1)) x k words, layout COLS of A in base Q (degree dq),

@@ -207,6 +207,33 @@ GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int6
     return launch_mixed(p, m, k, nc, d, t, word, (const uint8_t *)CA_or_A, lda, CB, ldb, C, ldc, s);
 }
 
+GFP_API gfp_status gfp_winograd_workspace_size(int64_t m, int64_t k, int64_t n, int d, int levels,
+                                               size_t *bytes) {
+    if (!bytes || m < 0 || k < 0 || n < 0 || d < 0 || levels < 0 || levels > 16) return GFP_EINVAL;
+    *bytes = winograd_workspace_bytes(m, cdiv(k, d + 1), n, levels);
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gemm_compressed_winograd(uint32_t p, int64_t m, int64_t k, int64_t n, int d, uint64_t Q,
+                                                const void *CA, int64_t lda, const void *CB, int64_t ldb,
+                                                uint8_t *C, int64_t ldc, int levels, void *workspace,
+                                                size_t ws_bytes, void *stream) {
+    if (m < 0 || k < 0 || n < 0 || levels < 0 || levels > 16) return GFP_EINVAL;
+    gfp_status st = check_dqt(p, k, d, Q, GFP_FORM_DOT, GFP_WORD_U64, 0);
+    if (st != GFP_OK) return st;
+    if (m == 0 || n == 0) return GFP_OK;
+    const int64_t kc = cdiv(k, d + 1);
+    if (!C || ldc < n) return GFP_EINVAL;
+    if (kc > 0 && (!CA || !CB || lda < kc || ldb < n)) return GFP_EINVAL;
+    if (kc == 0) {
+        const cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc, 0, (size_t)n, (size_t)m, (cudaStream_t)stream);
+        return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+    }
+    return launch_winograd_u64(p, m, kc, n, d, log2_exact(Q), static_cast<const uint64_t *>(CA), lda,
+                               static_cast<const uint64_t *>(CB), ldb, C, ldc, levels, workspace, ws_bytes,
+                               (cudaStream_t)stream);
+}
+
 GFP_API gfp_status gfp_gemm_full(uint32_t p, int64_t m, int64_t k, int64_t n, int dq, int dth,
                                  uint64_t Q, gfp_word word, const void *CA, int64_t lda,
                                  const void *CB, int64_t ldb, void *CC, int64_t ldc, void *stream) {

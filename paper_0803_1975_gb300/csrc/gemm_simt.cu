@@ -134,6 +134,16 @@ struct DotU64 : DotBase<uint64_t, uint64_t, BLK> {
     }
 };
 
+// 64-bit words, the raw word sums mod 2^64 as the result (the products of a
+// Strassen-Winograd recursion over the ring Z/2^64, whose digits are read
+// once at the end).
+struct DotU64Raw : DotBase<uint64_t, uint64_t, false> {
+    using GC = uint64_t;
+    __device__ static void mac(uint64_t &acc, uint64_t a, uint64_t b) { acc += a * b; }
+    __device__ static uint32_t extract(uint64_t, const DotParams &) { return 0; }
+    __device__ static uint64_t finish(uint64_t acc, uint32_t, const DotParams &) { return acc; }
+};
+
 // 64-bit words, 128-bit accumulator (largest word < 2^64, t(d+1) <= 128).
 template <bool BLK>
 struct DotU64x128 : DotBase<uint64_t, unsigned __int128, BLK> {
@@ -538,6 +548,14 @@ gfp_status launch_dot(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t
         case GFP_WORD_U32: e = run_dot<DotU32>(CA, lda, CB, ldb, C, ldc, m, n, kc, prm, blocked, s); break;
         case GFP_WORD_F64: e = run_dot<DotF64>(CA, lda, CB, ldb, C, ldc, m, n, kc, prm, blocked, s); break;
     }
+    return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+}
+
+gfp_status launch_word_product_u64(const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb,
+                                   uint64_t *C, int64_t ldc, int64_t m, int64_t kc, int64_t n,
+                                   cudaStream_t s) {
+    const DotParams prm = dot_params(2, 0, 1, 0);
+    const cudaError_t e = run_simt<DotU64Raw>(A, lda, B, ldb, C, ldc, m, n, kc, prm, s);
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
 }
 

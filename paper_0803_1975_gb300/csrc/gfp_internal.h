@@ -34,6 +34,16 @@ gfp_status check_pack(uint32_t p, int d, uint64_t Q, gfp_word word);
 gfp_status check_pack_vb(uint32_t p, uint32_t v, int d, uint64_t Q, gfp_word word);
 gfp_status launch_amax(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, uint32_t *out,
                        cudaStream_t s);
+// C = A B over Z/2^64 for word matrices (A m x kc, B kc x n, C m x n, leading
+// dimensions in words): the raw sums of the dot form, no digit extracted.
+gfp_status launch_word_product_u64(const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb,
+                                   uint64_t *C, int64_t ldc, int64_t m, int64_t kc, int64_t n,
+                                   cudaStream_t s);
+// Strassen-Winograd over Z/2^64 on the dot form's words (winograd.cu).
+size_t winograd_workspace_bytes(int64_t m, int64_t kc, int64_t n, int levels);
+gfp_status launch_winograd_u64(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t, const uint64_t *CA,
+                               int64_t lda, const uint64_t *CB, int64_t ldb, uint8_t *C, int64_t ldc, int levels,
+                               void *ws, size_t ws_bytes, cudaStream_t s);
 size_t word_bytes(gfp_word w);
 
 // Lemire, Kaser, Kurz, "Faster remainder by direct computation" (2019):

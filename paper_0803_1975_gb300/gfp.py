@@ -36,7 +36,8 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_batched_workspace_size", "gfp_gemm_batched", "gfp_batched_prepare",
            "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table",
            "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
-           "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax")
+           "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax",
+           "gfp_winograd_workspace_size", "gfp_gemm_compressed_winograd")
 
 
 class GfpError(RuntimeError):
@@ -93,6 +94,11 @@ def load():
     L.gfp_gemm_compressed_vb.restype = st
     L.gfp_amax.argtypes = [i64, i64, vp, i64, vp, vp]
     L.gfp_amax.restype = st
+    L.gfp_winograd_workspace_size.argtypes = [i64, i64, i64, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
+    L.gfp_winograd_workspace_size.restype = st
+    L.gfp_gemm_compressed_winograd.argtypes = [u32, i64, i64, i64, ip, u64, vp, i64, vp, i64, vp, i64, ip, vp,
+                                               ctypes.c_size_t, vp]
+    L.gfp_gemm_compressed_winograd.restype = st
     L.gfp_unpack.argtypes = [u32, i64, i64, vp, i64, ip, u64, ip, ip, vp, i64, vp]
     L.gfp_unpack.restype = st
     L.gfp_gemm_workspace_size.argtypes = [u32, i64, i64, i64, ip, ctypes.POINTER(ctypes.c_size_t)]
@@ -368,6 +374,33 @@ def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: st
     bp, ldb = _mat(CB, wdt, "CB")
     _check(fn(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
               ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
+    return out
+
+
+def gfp_winograd_workspace_size(m: int, k: int, n: int, d: int, levels: int) -> int:
+    L = load()
+    out = ctypes.c_size_t(0)
+    _check(L.gfp_winograd_workspace_size(m, k, n, d, levels, ctypes.byref(out)), "gfp_winograd_workspace_size")
+    return out.value
+
+
+def gfp_gemm_compressed_winograd(p: int, m: int, k: int, n: int, d: int, Q: int, CA: torch.Tensor,
+                                 CB: torch.Tensor, levels: int = 1, out: torch.Tensor | None = None,
+                                 workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Dot form in 64-bit words with `levels` levels of Strassen-Winograd
+    over Z/2^64 on the words: CA (ROWS_REV) x CB (COLS) -> uint8 C (m x n)."""
+    L = load()
+    ap, lda = _mat(CA, torch.int64, "CA")
+    bp, ldb = _mat(CB, torch.int64, "CB")
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.uint8, device=CB.device)
+    cp, ldc = _mat(out, torch.uint8, "C")
+    need = gfp_winograd_workspace_size(m, k, n, d, levels)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=CB.device)
+    _check(L.gfp_gemm_compressed_winograd(p, m, k, n, d, Q, ap, lda, bp, ldb, cp, ldc, levels,
+                                          ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                          _stream(CB, stream)), "gfp_gemm_compressed_winograd")
     return out
 
 

@@ -5,7 +5,8 @@ time (CUDA events, L2 flushed between repetitions) and effective 2mnk/s.
     python -m paper_0803_1975_gb300.run_case --form dot --word u32 --kb 60 --size 1024
 
 Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8 (gfp_gemm); dot, mixed
-(gfp_gemm_compressed, after packing); batched (the 4096-problem adjacency
+(gfp_gemm_compressed, after packing); winograd (the 64-bit dot form with
+--levels of Strassen-Winograd on the words); batched (the 4096-problem adjacency
 workload, one prepared launch); pack_rows_rev, pack_cols, pack_rows,
 unpack_rows (the conversions of A, reported in GB/s of bytes moved).  Useful
 for profiling one kernel.
@@ -33,6 +34,7 @@ def main():
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--algo", default="auto", help="batched: auto, tc_f16, tc_f8 or dot32")
+    ap.add_argument("--levels", type=int, default=1, help="winograd: Strassen-Winograd levels")
     ap.add_argument("--warmup", type=int, default=1)
     a = ap.parse_args()
     m = a.m or a.size
@@ -77,6 +79,15 @@ def main():
         m = k = n = 0
         flops_total = sum(2.0 * it[1].shape[0] ** 3 for it in items)
         fn = lambda: gfp.gfp_batched_launch(ws)
+    elif a.form == "winograd":
+        # the dot form in 64-bit words with Strassen-Winograd levels on the words
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "dot", "u64")
+        CA = gfp.gfp_pack(p, A, d, Q, "rows_rev", "u64")
+        CB = gfp.gfp_pack(p, B, d, Q, "cols", "u64")
+        C = torch.empty((m, n), dtype=torch.uint8, device="cuda")
+        ws = torch.empty(gfp.gfp_winograd_workspace_size(m, k, n, d, a.levels), dtype=torch.uint8, device="cuda")
+        fn = lambda: gfp.gfp_gemm_compressed_winograd(p, m, k, n, d, Q, CA, CB, levels=a.levels, out=C,
+                                                      workspace=ws)
     elif a.form == "mixed":
         d, Q, _ = gfp.gfp_params(p, m, k, n, "mixed", a.word)
         CB = gfp.gfp_pack(p, B, d, Q, "rows", a.word)
@@ -102,7 +113,7 @@ def main():
                           "bytes": pack_bytes, "GB_per_s": round(pack_bytes / ms / 1e6, 1)}))
         return
     flops = flops_total if a.form == "batched" else 2.0 * m * n * k
-    print(json.dumps({"form": a.form, "word": a.word, "algo": a.algo, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
+    print(json.dumps({"form": a.form, "word": a.word, "algo": a.algo, "levels": a.levels, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
                       "T_2mnk_per_s": round(flops / ms / 1e9, 3)}))
 
 
