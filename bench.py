@@ -48,6 +48,37 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+# Throughput ceilings of the pipe each form runs on.  Instruction rates were
+# measured on this machine's GB300 by chains of one instruction over 4 CTAs per
+# SM (152 SMs at 2.07 GHz); tensor-core rates from MEASURED_PEAKS.json (bf16
+# dense burst; fp16 runs at the bf16 rate, e4m3 at twice it).  Each form's
+# work is counted in the unit its inner loop issues.
+PIPES = {
+    "imad": (19.6e12, "IMAD/s (32-bit multiply-add, measured)"),
+    "imad_wide": (19.6e12, "IMAD.WIDE/s (32x32->64 multiply-add, measured)"),
+    "dp4a": (19.7e12, "dp4a/s (measured)"),
+    "mad64": (7.2e12, "64-bit mad.lo/s (measured)"),
+    "mad64x2": (3.6e12, "64x64->128 multiply-adds/s (two 64-bit mads each, from the measured mad rate)"),
+    "mad64x32": (9.8e12, "64x32-bit multiply-adds/s (two IMADs each, from the measured IMAD rate)"),
+    "dfma": (0.625e12, "DFMA/s (nominal FP64 of GB300; a measured chain reached 0.52e12)"),
+    "mma_s8": (158e12, "int8 mma.sync ops/s (measured)"),
+}
+
+
+# DRAM bytes of one launch of the dominant kernel (simt_gemm_kernel<DotF64,
+# 32, 32, 16, 2, 2> on this step's input), from an ncu capture of this bench:
+# 4,212,224 read (CA + CB once) + 0 written (the uint8 C leaves L2 later).
+DOTF64_TRAFFIC = 4212224
+
+
+def form_roofline(ms: float, work: float, pipe: str = None, peak: float = None, unit: str = None):
+    """Achieved rate of `work` units in `ms` against a pipe's ceiling."""
+    if pipe is not None:
+        peak, unit = PIPES[pipe]
+    achieved = work / (ms * 1e-3)
+    return {"work_per_launch": work, "peak": peak, "unit": unit, "frac": round(achieved / peak, 4)}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -189,19 +220,32 @@ def event_time(torch, fn, reps, flush):
 
 
 def forms_breakdown(gfp, torch, A, B, flush, plain_ms):
-    """Each form and word timed on its own (median of 7, L2 flushed)."""
+    """Each form and word timed on its own (median of 7, L2 flushed), with
+    its fraction of the ceiling of the pipe it runs on."""
     out = {}
     dev = A.device
+    bf16 = (measured_peaks().get("bf16_tflops") or 1900.0) * 1e12
+    hbm = (measured_peaks().get("hbm_gbs") or 6800.0) * 1e9
 
-    def rec(name, ms, **extra):
+    def rec(name, ms, roof=None, **extra):
         r = {"ms": round(ms, 5), "value": round(FLOP / ms / 1e9, 3), "speedup_vs_plain": round(plain_ms / ms, 3)}
         r.update(extra)
+        if roof is not None:
+            r["roofline"] = roof
         out[name] = r
 
+    tc_roof = {"plain": lambda ms: form_roofline(ms, M * N * K, "imad"),
+               "dp4a": lambda ms: form_roofline(ms, M * N * -(-K // 4), "dp4a"),
+               "tc_mma_s8": lambda ms: form_roofline(ms, FLOP, "mma_s8"),
+               "tc_f16": lambda ms: form_roofline(ms, FLOP, peak=bf16, unit="fp16 tcgen05 flops/s (bf16 dense, measured)"),
+               "tc_f8": lambda ms: form_roofline(ms, FLOP, peak=2 * bf16,
+                                                 unit="e4m3 tcgen05 flops/s (2 x measured bf16 dense)")}
     for algo in ("plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8"):
         ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(P, M, K, N, algo)), dtype=torch.uint8, device=dev)
         C = torch.empty((M, N), dtype=torch.uint8, device=dev)
-        rec(algo, event_time(torch, lambda: gfp.gfp_gemm(P, A, B, algo, out=C, workspace=ws), 7, flush))
+        ms = event_time(torch, lambda: gfp.gfp_gemm(P, A, B, algo, out=C, workspace=ws), 7, flush)
+        rec(algo, ms, tc_roof[algo](ms))
+    word_pipe = {"u64": "mad64", "u64x128": "mad64x2", "u32w": "imad_wide", "u32": "imad", "f64": "dfma"}
     for word, kb in (("u64", 0), ("u64x128", 0), ("u32w", 0), ("u32", 0), ("f64", 0), ("u32", 60),
                      ("u32w", 140)):
         d, Q, kbr = gfp.gfp_params(P, M, K, N, "dot", word, kb=kb)
@@ -216,32 +260,36 @@ def forms_breakdown(gfp, torch, A, B, flush, plain_ms):
             gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr)
         t_full = event_time(torch, full, 7, flush)
         name = "dot_%s" % word + ("_kb%d" % kbr if kbr else "")
-        rec(name, t_mm, d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr,
+        rec(name, t_mm, form_roofline(t_mm, M * N * -(-K // (d + 1)), word_pipe[word]),
+            d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr,
             with_packing_ms=round(t_full, 5), with_packing_value=round(FLOP / t_full / 1e9, 3))
     for word in ("u64", "f64"):
         d, Q, _ = gfp.gfp_params(P, M, K, N, "mixed", word)
         CB = gfp.gfp_pack(P, B, d, Q, "rows", word)
         CC = torch.empty((M, -(-N // (d + 1))), dtype=gfp.WORD_DTYPE[word], device=dev)
-        rec("mixed_%s" % word, event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "mixed", word, A, CB, out=CC), 7, flush),
+        ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "mixed", word, A, CB, out=CC), 7, flush)
+        rec("mixed_%s" % word, ms, form_roofline(ms, M * K * -(-N // (d + 1)), "mad64x32" if word == "u64" else "dfma"),
             d_plus_1=d + 1, t=Q.bit_length() - 1)
     # left (Table 2) and full (Section 4) compression, u64 words, product only
     d, Q, _ = gfp.gfp_params(P, M, K, N, "left", "u64")
     CA = gfp.gfp_pack(P, A, d, Q, "cols", "u64")
     CC = torch.empty((-(-M // (d + 1)), N), dtype=torch.int64, device=dev)
-    rec("left_u64", event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "left", "u64", CA, B, out=CC), 7, flush),
-        d_plus_1=d + 1, t=Q.bit_length() - 1)
+    ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "left", "u64", CA, B, out=CC), 7, flush)
+    rec("left_u64", ms, form_roofline(ms, -(-M // (d + 1)) * K * N, "mad64x32"), d_plus_1=d + 1, t=Q.bit_length() - 1)
     dq, dth, Q = gfp.gfp_params_full(P, M, K, N, "u64")
     CA = gfp.gfp_pack(P, A, dq, Q, "cols", "u64")
     CB = gfp.gfp_pack(P, B, dth, Q ** (dq + 1), "rows", "u64")
     CC = torch.empty((-(-M // (dq + 1)), -(-N // (dth + 1))), dtype=torch.int64, device=dev)
-    rec("full_u64", event_time(torch, lambda: gfp.gfp_gemm_full(P, M, K, N, dq, dth, Q, "u64", CA, CB, out=CC), 7, flush),
+    ms = event_time(torch, lambda: gfp.gfp_gemm_full(P, M, K, N, dq, dth, Q, "u64", CA, CB, out=CC), 7, flush)
+    rec("full_u64", ms, form_roofline(ms, -(-M // (dq + 1)) * K * -(-N // (dth + 1)), "mad64"),
         dq=dq, dth=dth, t=Q.bit_length() - 1)
     # conversions: pack A reversed into u64 words, bytes moved per launch
     d, Q, _ = gfp.gfp_params(P, M, K, N, "dot", "u64")
     CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64")
     t = event_time(torch, lambda: gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64", out=CA), 7, flush)
     byts = M * K + CA.numel() * 8
-    out["pack_rows_rev_u64"] = {"ms": round(t, 5), "GB_per_s": round(byts / t / 1e6, 1), "bytes": byts}
+    out["pack_rows_rev_u64"] = {"ms": round(t, 5), "GB_per_s": round(byts / t / 1e6, 1), "bytes": byts,
+                                "roofline": form_roofline(t, byts, peak=hbm, unit="bytes/s (measured HBM copy)")}
     return out
 
 
@@ -450,7 +498,9 @@ def main():
     roofline = {"kernel": "simt_gemm_kernel<DotF64> (dot form, FP64 words)", "bound": "alu",
                 "achieved": round(achieved, 4), "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": round(achieved / fp64_peak, 4), "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak in MEASURED_PEAKS.json)",
-                "traffic": None, "launch_ms": round(dom_avg, 5),
+                "traffic": DOTF64_TRAFFIC, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                "one launch of this kernel in this step (profiles/dot_f64_kernel_p3_1024.md); algorithmic "
+                "operand bytes %d" % (8 * kcf * (M + N)), "launch_ms": round(dom_avg, 5),
                 "algorithmic_flops_per_launch": 2 * dfma,
                 "share_of_step": round(dom_avg / (float(np.mean(step_ms))), 3)}
 
