@@ -499,8 +499,7 @@ def main():
                 "achieved": round(achieved, 4), "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": round(achieved / fp64_peak, 4), "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak in MEASURED_PEAKS.json)",
                 "traffic": DOTF64_TRAFFIC, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
-                "one launch of this kernel in this step (profiles/dot_f64_kernel_p3_1024.md); algorithmic "
-                "operand bytes %d" % (8 * kcf * (M + N)), "launch_ms": round(dom_avg, 5),
+                "one launch of this kernel in this step; algorithmic operand bytes %d" % (8 * kcf * (M + N)), "launch_ms": round(dom_avg, 5),
                 "algorithmic_flops_per_launch": 2 * dfma,
                 "share_of_step": round(dom_avg / (float(np.mean(step_ms))), 3)}
 
