@@ -263,6 +263,15 @@ def forms_breakdown(gfp, torch, A, B, flush, plain_ms):
         rec(name, t_mm, form_roofline(t_mm, M * N * -(-K // (d + 1)), word_pipe[word]),
             d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr,
             with_packing_ms=round(t_full, 5), with_packing_value=round(FLOP / t_full / 1e9, 3))
+    # the autotuner's pick of (word, d, Q, k-block) for this shape (untimed search)
+    best, cands = gfp.gfp_dot_autotune(P, M, K, N)
+    word, d, Q, kbr = best["word"], best["d"], best["Q"], best["kb"]
+    CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", word)
+    CB = gfp.gfp_pack(P, B, d, Q, "cols", word)
+    C = torch.empty((M, N), dtype=torch.uint8, device=dev)
+    ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr), 7, flush)
+    rec("dot_autotuned", ms, form_roofline(ms, M * N * -(-K // (d + 1)), word_pipe[word]), word=word,
+        d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr, candidates=len(cands))
     for word in ("u64", "f64"):
         d, Q, _ = gfp.gfp_params(P, M, K, N, "mixed", word)
         CB = gfp.gfp_pack(P, B, d, Q, "rows", word)

@@ -329,6 +329,37 @@ GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int6
                                           void *C, int64_t ldc, int64_t kb,
                                           void *stream);
 
+/* Autotuner of the dot form for one product (no counterpart in the paper,
+ * which fixes the word): a smaller Q -- the bound of eq. (lower) applied to
+ * a k-block kb -- leaves room for more coefficients per word at the price of
+ * an extraction every kb terms, and 32-bit words cost one multiply-add where
+ * 64-bit words cost about three.  The admissible (word in U32, U32W, U64;
+ * d, Q, kb) with no blocking and, for each Q = 2^t, the longest k-block
+ * eq. (lower) allows -- per (word, d) the longest k-block, no
+ * blocking counting as the longest -- are timed with
+ * CUDA events on the proxy shape min(m, 2048) x k x min(n, 2048) with zero
+ * operands in the caller's workspace (gfp_dot_autotune_workspace_size bytes,
+ * 256-byte aligned; its contents are overwritten); *best receives the
+ * fastest, all[0 .. min(*n_all, max_all)) every candidate with its median
+ * time.  Waits for its timings: not capturable in a CUDA graph.  The choice
+ * is valid for (p, m, k, n): pass it to gfp_pack and gfp_gemm_compressed.
+ * Errors: GFP_EINVAL, GFP_EPRIME, GFP_EBOUND (no word admits k),
+ * GFP_EWORKSPACE, GFP_ECUDA. */
+typedef struct gfp_dot_choice {
+    int32_t word;        /* gfp_word */
+    int32_t d;
+    uint64_t Q;
+    int64_t kb;          /* 0: no k-blocking */
+    float ms;            /* median of three timed runs on the proxy shape */
+    int32_t reserved;
+} gfp_dot_choice;
+
+GFP_API gfp_status gfp_dot_autotune_workspace_size(int64_t m, int64_t k, int64_t n, size_t *bytes);
+GFP_API gfp_status gfp_dot_autotune(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                    void *workspace, size_t ws_bytes, void *stream,
+                                    gfp_dot_choice *best, gfp_dot_choice *all, int max_all,
+                                    int *n_all);
+
 /* Strassen-Winograd over the packed words of the dot form (the paper's
  * remark on fast matrix multiplication, Section 5).  With 64-bit words
  * (t(d+1) <= 64) the coefficient of Q^d is exact modulo 2^64, so only the

@@ -37,7 +37,8 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_batched_launch", "gfp_batched_autotune", "gfp_batched_set_table",
            "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
            "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax",
-           "gfp_winograd_workspace_size", "gfp_gemm_compressed_winograd")
+           "gfp_winograd_workspace_size", "gfp_gemm_compressed_winograd", "gfp_dot_autotune_workspace_size",
+           "gfp_dot_autotune")
 
 
 class GfpError(RuntimeError):
@@ -48,6 +49,12 @@ class GfpError(RuntimeError):
         if status == 6 and _lib is not None:
             msg += " (cudaError %d)" % _lib.gfp_last_cuda_error()
         super().__init__(msg)
+
+
+class DotChoice(ctypes.Structure):
+    """struct gfp_dot_choice."""
+    _fields_ = [("word", ctypes.c_int32), ("d", ctypes.c_int32), ("Q", ctypes.c_uint64), ("kb", ctypes.c_int64),
+                ("ms", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -94,6 +101,11 @@ def load():
     L.gfp_gemm_compressed_vb.restype = st
     L.gfp_amax.argtypes = [i64, i64, vp, i64, vp, vp]
     L.gfp_amax.restype = st
+    L.gfp_dot_autotune_workspace_size.argtypes = [i64, i64, i64, ctypes.POINTER(ctypes.c_size_t)]
+    L.gfp_dot_autotune_workspace_size.restype = st
+    L.gfp_dot_autotune.argtypes = [u32, i64, i64, i64, vp, ctypes.c_size_t, vp, ctypes.POINTER(DotChoice),
+                                   ctypes.POINTER(DotChoice), ip, ctypes.POINTER(ip)]
+    L.gfp_dot_autotune.restype = st
     L.gfp_winograd_workspace_size.argtypes = [i64, i64, i64, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
     L.gfp_winograd_workspace_size.restype = st
     L.gfp_gemm_compressed_winograd.argtypes = [u32, i64, i64, i64, ip, u64, vp, i64, vp, i64, vp, i64, ip, vp,
@@ -375,6 +387,26 @@ def gfp_gemm_compressed(p: int, m: int, k: int, n: int, d: int, Q: int, form: st
     _check(fn(p, m, k, n, d, Q, FORMS[form], WORDS[word], ap, lda, bp, ldb, cp,
               ldc, kb, _stream(CB, stream)), "gfp_gemm_compressed")
     return out
+
+
+WORD_NAMES = {v: k for k, v in WORDS.items()}
+
+
+def gfp_dot_autotune(p: int, m: int, k: int, n: int, device=None, stream=None):
+    """Fastest (word, d, Q, kb) of the dot form for (p, m, k, n) on this GPU.
+    Returns (best, all): dicts with word, d, Q, kb, ms."""
+    L = load()
+    need = ctypes.c_size_t(0)
+    _check(L.gfp_dot_autotune_workspace_size(m, k, n, ctypes.byref(need)), "gfp_dot_autotune_workspace_size")
+    dev = torch.device("cuda") if device is None else device
+    ws = torch.empty(max(need.value, 1), dtype=torch.uint8, device=dev)
+    best = DotChoice()
+    arr = (DotChoice * 128)()
+    cnt = ctypes.c_int(0)
+    _check(L.gfp_dot_autotune(p, m, k, n, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(ws, stream),
+                              ctypes.byref(best), arr, 128, ctypes.byref(cnt)), "gfp_dot_autotune")
+    conv = lambda c: {"word": WORD_NAMES[c.word], "d": c.d, "Q": c.Q, "kb": c.kb, "ms": c.ms}
+    return conv(best), [conv(arr[i]) for i in range(min(cnt.value, 128))]
 
 
 def gfp_winograd_workspace_size(m: int, k: int, n: int, d: int, levels: int) -> int:
