@@ -517,7 +517,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             for (int j = 0; j < ti.kblocks; ++j, ++unit) {
                 const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
-                // one lane waits, the warp follows its verdict (tcgen05.ld is warp-collective)
+                // one lane waits, the warp follows its result (tcgen05.ld is warp-collective)
                 int got = 0;
                 if (lane == 0) got = mbar_wait(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI);
                 got = __shfl_sync(0xffffffffu, got, 0);
