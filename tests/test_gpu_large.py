@@ -3,7 +3,8 @@ the benchmark uses: sampled rows against the oracle (which computes them one
 by one) and Freivalds' test on the whole product (a property of any correct
 product, independent of how it was computed).
 
-- tensor-core forms, p in {3, 31, 251}, m = k = n = 8192;
+- tensor-core forms, p in {3, 31, 251}, m = k = n = 8192, and ragged sizes
+  over the 256-column tiles;
 - every form, p = 5, m = k = n = 16384."""
 import numpy as np
 import pytest
@@ -39,6 +40,22 @@ def test_tc_8192(p):
         C = host(gfp.gfp_gemm(p, Ad, Bd, algo))
         check(p, A, B, C, rows)
         del C
+
+
+@pytest.mark.parametrize("p", [7, 31, 251])
+def test_tc_ragged_256_column_tiles(p):
+    """256-column tiles over an odd number (35) of 128-row tiles with ragged
+    m, k and n: the last row tile and the last column tile are partial;
+    p = 251 adds fp16 k-blocks."""
+    m, k, n = 35 * 128 - 37, 1500, 4096 + 5
+    g = inputs.rng(3, 100 + p)
+    A = inputs.residues(g, p, m, k)
+    B = inputs.residues(g, p, k, n)
+    Ad, Bd = dev(A), dev(B)
+    rows = [0, 127, 128, 255, 256, 4095, 4096, m - 2, m - 1]
+    for algo in ("tc_f16",) + (("tc_f8",) if p <= 31 else ()):
+        C = host(gfp.gfp_gemm(p, Ad, Bd, algo))
+        check(p, A, B, C, rows, rounds=3)
 
 
 @pytest.fixture(scope="module")
