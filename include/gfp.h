@@ -329,6 +329,19 @@ GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int6
                                           void *C, int64_t ldc, int64_t kb,
                                           void *stream);
 
+/* Self-test of failure detection (no counterpart in the paper).  Every wait
+ * of the tcgen05 kernels (on a stage's copies, a free stage, an accumulator)
+ * is bounded: when one runs out the kernel records which role gave up in a
+ * status word (1 producer, 2 MMA issuer, 3 epilogue, 4 final drain), the
+ * other roles stop, tensor memory is freed and the kernel returns, leaving
+ * the context usable.  This call runs a 128 x 128 x 128 product whose first
+ * copies are withheld, so a wait runs out after limit_ms (1 .. 10000), and
+ * writes the status word to *status (host).  Workspace: >= 82,176 bytes,
+ * 256-byte aligned, device.  Synchronizes the stream.  Errors: GFP_EINVAL,
+ * GFP_EWORKSPACE, GFP_ECUDA. */
+GFP_API gfp_status gfp_selftest_wait_limit(void *workspace, size_t ws_bytes, uint32_t limit_ms, int *status,
+                                           void *stream);
+
 /* Autotuner of the dot form for one product (no counterpart in the paper,
  * which fixes the word): a smaller Q -- the bound of eq. (lower) applied to
  * a k-block kb -- leaves room for more coefficients per word at the price of

@@ -207,6 +207,12 @@ GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int6
     return launch_mixed(p, m, k, nc, d, t, word, (const uint8_t *)CA_or_A, lda, CB, ldb, C, ldc, s);
 }
 
+GFP_API gfp_status gfp_selftest_wait_limit(void *workspace, size_t ws_bytes, uint32_t limit_ms, int *status,
+                                           void *stream) {
+    if (!status || limit_ms < 1 || limit_ms > 10000) return GFP_EINVAL;
+    return tc_selftest_wait_limit(workspace, ws_bytes, (uint64_t)limit_ms * 1000000ull, status, (cudaStream_t)stream);
+}
+
 GFP_API gfp_status gfp_winograd_workspace_size(int64_t m, int64_t k, int64_t n, int d, int levels,
                                                size_t *bytes) {
     if (!bytes || m < 0 || k < 0 || n < 0 || d < 0 || levels < 0 || levels > 16) return GFP_EINVAL;

@@ -66,7 +66,7 @@ struct TcCfg {
     // 17-22, M >> 4 in bits 24-28.
     static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
-constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;   // 4 s
+constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;   // 4 s: the default bound of every wait
 
 // status codes written to the status word
 constexpr int ST_TIMEOUT_PRODUCER = 1, ST_TIMEOUT_MMA = 2, ST_TIMEOUT_EPI = 3, ST_TIMEOUT_DRAIN = 4;
@@ -101,7 +101,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 // Bounded wait: true when the phase of `parity` completed; false on abort
 // (another role gave up) or on expiry (this role gives up and says so).
 __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag,
-                                       int *status, int code) {
+                                       int *status, int code, uint64_t limit_ns) {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(a, parity)) return true;
@@ -110,7 +110,7 @@ __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int
             const uint64_t now = globaltimer();
             if (t0 == 0) {
                 t0 = now;
-            } else if (now - t0 > WAIT_LIMIT_NS) {
+            } else if (now - t0 > limit_ns) {
                 *abort_flag = 1;
                 if (status) atomicCAS(status, 0, code);
                 return false;
@@ -232,6 +232,8 @@ struct TcArgs {
     int red;           // 1: raw operands and every k-block sum < 2^23 units of 2^-18
     float scale;       // 1, or 2^18 for raw e4m3 operands (values r 2^-9)
     int *status;
+    uint64_t limit_ns; // bound of every wait (WAIT_LIMIT_NS)
+    int stall;         // self-test only: the first stage's copies are never issued
 };
 
 }  // namespace
@@ -416,12 +418,22 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const CUtensorMap *mA = GROUPED ? ti.map : &tmA;
                 const CUtensorMap *mB = GROUPED ? ti.map : &tmB;
                 for (int kt = 0; kt < ti.ktiles; ++kt) {
-                    if (!mbar_wait(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER)) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER, g.limit_ns)) {
                         ok = false;
                         break;
                     }
                     const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
                     mbar_expect_tx(full_bar(stage), STAGE_BYTES);
+                    if (g.stall && kt == 0) {
+                        // self-test: these bytes never come, so the MMA issuer's wait
+                        // on this stage runs out (no copy is in flight for it)
+                        ++stage;
+                        if (stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                        continue;
+                    }
                     tma_load_2d(sa, mA, kt * CFG::BKE, ti.rowA0 + tm * BM, full_bar(stage));
                     tma_load_2d(sb, mB, kt * CFG::BKE, ti.rowB0 + tn * BN, full_bar(stage));
                     issued[stage] = true;
@@ -438,7 +450,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     if (issued[s]) {
                         uint64_t t0 = globaltimer();
                         while (!mbar_try(full_bar(s), issued_parity[s]) &&
-                               globaltimer() - t0 < WAIT_LIMIT_NS) {
+                               globaltimer() - t0 < g.limit_ns) {
                         }
                     }
             }
@@ -455,7 +467,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             while (ok && walk.next(ti)) {
                 for (int j = 0; j < ti.kblocks && ok; ++j, ++unit) {
                     const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
-                    if (!mbar_wait(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA)) {
+                    if (!mbar_wait(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
                         ok = false;
                         break;
                     }
@@ -464,7 +476,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     const int k0 = j * ti.kb_tiles;
                     const int k1 = min(ti.ktiles, k0 + ti.kb_tiles);
                     for (int kt = k0; kt < k1; ++kt) {
-                        if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA)) {
+                        if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
                             ok = false;
                             break;
                         }
@@ -490,7 +502,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             mma_commit(drain_bar);
             uint64_t t0 = globaltimer();
             while (!mbar_try(drain_bar, 0)) {
-                if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                if (globaltimer() - t0 > g.limit_ns) {
                     if (g.status) atomicCAS(g.status, 0, ST_TIMEOUT_DRAIN);
                     break;
                 }
@@ -519,7 +531,7 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
                 // one lane waits, the warp follows its result (tcgen05.ld is warp-collective)
                 int got = 0;
-                if (lane == 0) got = mbar_wait(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI);
+                if (lane == 0) got = mbar_wait(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI, g.limit_ns);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -845,6 +857,8 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     g.red = raw && kb_elems * (int64_t)(p - 1) * (p - 1) < ((int64_t)1 << 23) ? 1 : 0;
     g.scale = raw ? 262144.0f : 1.0f;
     g.status = status;
+    g.limit_ns = WAIT_LIMIT_NS;
+    g.stall = 0;
     const int tiles = g.tiles_m * g.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();
     const bool blk = g.kblocks > 1;
@@ -897,6 +911,7 @@ gfp_status launch_tc_grouped(const void *grp, int grid, int *status, cudaStream_
     TcArgs g;
     std::memset(&g, 0, sizeof(g));
     g.status = status;
+    g.limit_ns = WAIT_LIMIT_NS;
     CUtensorMap unused;
     std::memset(&unused, 0, sizeof(unused));
     launch_cfg<TcGroupCfg, false, true>(unused, unused, g, grid, s, static_cast<const TcGroupHeader *>(grp));
@@ -904,6 +919,49 @@ gfp_status launch_tc_grouped(const void *grp, int grid, int *status, cudaStream_
 }
 
 int tc_grouped_ctas_per_sm() { return TcGroupCfg::MINB; }
+
+// Self-test of the bounded waits: a 128 x 128 x 128 fp16 product of zeros in
+// the caller's workspace whose first stage's copies are withheld, so the MMA
+// issuer's wait on it runs out after limit_ns; the kernel records which role
+// gave up in its status word, stops every role, frees tensor memory and
+// returns.  *status_host receives the status word (0 would mean no wait ran
+// out).  Workspace: [status, 256 B][A 32 KB][B^T 32 KB][C 16 KB].
+gfp_status tc_selftest_wait_limit(void *ws, size_t ws_bytes, uint64_t limit_ns, int *status_host, cudaStream_t s) {
+    constexpr int64_t N = 128, K = 128;
+    const size_t need = 256 + 2 * N * K * 2 + N * N;
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255) || !status_host) return GFP_EWORKSPACE;
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    cudaError_t e = cudaMemsetAsync(base, 0, need, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    uint8_t *Aop = base + 256, *Bop = Aop + N * K * 2, *C = Bop + N * K * 2;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Aop, N, K, BM, false) || !make_map(&mb, Bop, N, K, 128, false)) return GFP_EUNSUPPORTED;
+    TcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.C = C;
+    g.ldc = N;
+    g.m = N;
+    g.n = N;
+    g.tiles_m = 1;
+    g.tiles_n = 1;
+    g.ktiles = (int)(K / 64);
+    g.kb_tiles = g.ktiles;
+    g.kblocks = 1;
+    g.p = 3;
+    g.off = (uint32_t)(((int64_t)1 << 24) + 2) / 3 * 3;
+    g.m32 = (uint32_t)(0xFFFFFFFFull / 3 + 1);
+    g.scale = 1.0f;
+    g.status = reinterpret_cast<int *>(base);
+    g.limit_ns = limit_ns;
+    g.stall = 1;
+    launch_cfg<TcCfg<128, false>, false>(ma, mb, g, 1, s);
+    gfp_status st = check_launch();
+    if (st != GFP_OK) return st;
+    e = cudaMemcpyAsync(status_host, base, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+}
 
 gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
                         const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,

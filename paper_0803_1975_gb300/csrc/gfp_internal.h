@@ -96,6 +96,7 @@ gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8
 bool tc_make_map_u8(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int box_rows);
 gfp_status launch_tc_grouped(const void *grp, int grid, int *status, cudaStream_t s);
 int tc_grouped_ctas_per_sm();
+gfp_status tc_selftest_wait_limit(void *ws, size_t ws_bytes, uint64_t limit_ns, int *status_host, cudaStream_t s);
 int64_t tc_kblock_s32(uint32_t p);      // largest kb with kb ((p-1)/2)^2 + p < 2^30
 int64_t tc_kblock_f32(uint32_t p);      // largest kb (multiple of 128) with kb ((p-1)/2)^2 + p < 2^24
 

@@ -38,7 +38,7 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
            "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax",
            "gfp_winograd_workspace_size", "gfp_gemm_compressed_winograd", "gfp_dot_autotune_workspace_size",
-           "gfp_dot_autotune")
+           "gfp_dot_autotune", "gfp_selftest_wait_limit")
 
 
 class GfpError(RuntimeError):
@@ -106,6 +106,8 @@ def load():
     L.gfp_dot_autotune.argtypes = [u32, i64, i64, i64, vp, ctypes.c_size_t, vp, ctypes.POINTER(DotChoice),
                                    ctypes.POINTER(DotChoice), ip, ctypes.POINTER(ip)]
     L.gfp_dot_autotune.restype = st
+    L.gfp_selftest_wait_limit.argtypes = [vp, ctypes.c_size_t, u32, ctypes.POINTER(ip), vp]
+    L.gfp_selftest_wait_limit.restype = st
     L.gfp_winograd_workspace_size.argtypes = [i64, i64, i64, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
     L.gfp_winograd_workspace_size.restype = st
     L.gfp_gemm_compressed_winograd.argtypes = [u32, i64, i64, i64, ip, u64, vp, i64, vp, i64, vp, i64, ip, vp,
@@ -407,6 +409,17 @@ def gfp_dot_autotune(p: int, m: int, k: int, n: int, device=None, stream=None):
                               ctypes.byref(best), arr, 128, ctypes.byref(cnt)), "gfp_dot_autotune")
     conv = lambda c: {"word": WORD_NAMES[c.word], "d": c.d, "Q": c.Q, "kb": c.kb, "ms": c.ms}
     return conv(best), [conv(arr[i]) for i in range(min(cnt.value, 128))]
+
+
+def gfp_selftest_wait_limit(limit_ms: int = 100, device=None, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the kernel's status word."""
+    L = load()
+    dev = torch.device("cuda") if device is None else device
+    ws = torch.empty(82176, dtype=torch.uint8, device=dev)
+    out = ctypes.c_int(0)
+    _check(L.gfp_selftest_wait_limit(ctypes.c_void_p(ws.data_ptr()), ws.numel(), limit_ms, ctypes.byref(out),
+                                     _stream(ws, stream)), "gfp_selftest_wait_limit")
+    return out.value
 
 
 def gfp_winograd_workspace_size(m: int, k: int, n: int, d: int, levels: int) -> int:
