@@ -503,10 +503,13 @@ GFP_API gfp_status gfp_batched_launch(void *workspace, size_t ws_bytes, void *st
  * (512,2048], above) it times one grouped launch of that bucket's problems
  * with each tile kind (0 = fp16 MMA 64 x 64, 1 = fp16 MMA 32 x 32, 2 = Q-adic
  * 32-bit words with per-problem Q and d, 3 = fp16 MMA 128 x 128, 4 = tcgen05
- * e4m3 128 x 128 for p < 16) and keeps the fastest; the choice
- * is stored in the library (used by GFP_ALGO_AUTO from then on, process
- * wide) and, if `table` is not NULL, written to table[0 .. table_len) (-1 for
- * buckets without problems).  It writes the problems' C matrices and uses
+ * e4m3 128 x 128 for p < 16) and keeps the fastest; then it times the whole
+ * batch with that table, with the default kinds (table -1) and with the
+ * tcgen05 kind in every bucket (where it applies), and keeps the fastest
+ * table -- mixing engines adds a grouped kernel that buckets timed alone do
+ * not see.  The choice is stored in the library (used by GFP_ALGO_AUTO from
+ * then on, process wide) and, if `table` is not NULL, written to
+ * table[0 .. table_len) (-1: the default kind, or no problems).  It writes the problems' C matrices and uses
  * `workspace` (gfp_batched_workspace_size bytes); it synchronizes `stream`. */
 GFP_API gfp_status gfp_batched_autotune(int64_t count, const gfp_problem *probs, void *workspace,
                                         size_t ws_bytes, void *stream, int *table, int table_len);

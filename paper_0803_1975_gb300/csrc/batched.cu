@@ -29,8 +29,8 @@
 //       products accumulate mod 2^32 (t(d+1) <= 32), and the coefficient of
 //       Q^d is extracted every kbw words (eq. (lower) for the k-block) and
 //       summed, then reduced mod p once.  (t, d, kbw) are chosen per problem.
-// The autotuner (gfp_batched_autotune) times the kinds per size bucket and
-// fills the table GFP_ALGO_AUTO uses.
+// The autotuner (gfp_batched_autotune) times the kinds per size bucket, then
+// whole-batch tables, and fills the table GFP_ALGO_AUTO uses.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -1178,16 +1178,60 @@ GFP_API gfp_status gfp_batched_autotune(int64_t count, const gfp_problem *probs,
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (result != GFP_OK) return result;
+    // Buckets timed alone do not see what mixing engines costs the whole
+    // launch (one more grouped kernel, its tail): time the whole batch with
+    // the per-bucket table, with the defaults and with tcgen05 tiles wherever
+    // they apply, and keep the fastest.
+    int cand[3][NBUCKETS];
+    for (int b = 0; b < NBUCKETS; ++b) {
+        cand[0][b] = best[b];
+        cand[1][b] = -1;
+        cand[2][b] = best[b] >= 0 ? KIND_TC8 : -1;
+    }
+    int pick = 0;
+    float pick_ms = 1e30f;
+    int saved[NBUCKETS];
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        for (int b = 0; b < NBUCKETS; ++b)
-            if (best[b] >= 0) g_tuned[b] = best[b];
+        std::memcpy(saved, g_tuned, sizeof(saved));
+    }
+    for (int c = 0; c < 3 && result == GFP_OK && count > 0; ++c) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            std::memcpy(g_tuned, cand[c], sizeof(g_tuned));
+        }
+        gfp_status st = prepare_impl(count, probs, GFP_ALGO_AUTO, nullptr, workspace, ws_bytes, s, nullptr);
+        if (st != GFP_OK && st != GFP_EPRIME && st != GFP_EINVAL && st != GFP_EUNSUPPORTED) {
+            result = st;
+            break;
+        }
+        float ms_sum = 0;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            launch_plan(workspace, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;
+        }
+        if (ms_sum < pick_ms) {
+            pick_ms = ms_sum;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (result != GFP_OK) {
+            std::memcpy(g_tuned, saved, sizeof(g_tuned));
+            return result;
+        }
+        for (int b = 0; b < NBUCKETS; ++b) g_tuned[b] = cand[pick][b] >= 0 ? cand[pick][b] : saved[b];
     }
     if (table)
-        for (int b = 0; b < table_len && b < NBUCKETS; ++b) table[b] = best[b];
+        for (int b = 0; b < table_len && b < NBUCKETS; ++b) table[b] = cand[pick][b];
     return GFP_OK;
 }
 

@@ -43,3 +43,28 @@ def test_autotune_offers_blocked_words_with_more_coefficients():
     u32 = [c for c in cands if c["word"] == "u32"]
     assert any(c["kb"] == 0 and c["d"] == 0 for c in u32)
     assert any(c["kb"] > 0 and c["d"] + 1 >= 3 for c in u32)
+
+
+def test_tuning_cache_round_trip(tmp_path):
+    """The JSON cache with the real tuners: a second process-level cache on
+    the same file reuses both choices, and the installed batched table gives
+    exact products."""
+    from paper_0803_1975_gb300.tuning_cache import TuningCache
+    import torch
+    path = str(tmp_path / "tune.json")
+    c = TuningCache(path)
+    w = c.dot(3, 512, 1024, 512)
+    g = inputs.rng(92, 0)
+    items, host_ops = [], []
+    for p, n in ((3, 40), (5, 200), (7, 300), (251, 90)):
+        A = inputs.adjacency(g, n)
+        items.append((p, dev(A), dev(A), torch.empty((n, n), dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A))
+    arr, cnt = gfp.make_problems(items)
+    table = c.batched(arr, cnt)
+    c2 = TuningCache(path)
+    assert c2.reused and c2.dot(3, 512, 1024, 512) == w and c2.batched(arr, cnt) == table
+    gfp.gfp_gemm_batched(arr, cnt, "auto")
+    for (p, A), it in zip(host_ops, items):
+        assert (host(it[3]) == oracle.gemm(p, A, A)).all()
+    gfp.gfp_batched_set_table([-1] * 7)

@@ -108,7 +108,8 @@ def test_autotune_then_auto():
     items, host_ops = random_batch(14, 60, primes=(3, 5, 7), smax=520)
     arr, cnt = gfp.make_problems(items)
     table = gfp.gfp_batched_autotune(arr, cnt)
-    assert len(table) == 7 and all(v in (-1, 0, 1, 2, 3, 4) for v in table) and any(v >= 0 for v in table)
+    # per bucket a kind, or -1 when the whole-batch comparison kept the defaults
+    assert len(table) == 7 and all(v in (-1, 0, 1, 2, 3, 4) for v in table)
     for it in items:
         it[3].fill_(255)
     gfp.gfp_gemm_batched(arr, cnt, "auto")
