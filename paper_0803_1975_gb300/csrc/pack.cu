@@ -9,9 +9,13 @@
 //   ROWS    : W[i][v] = sum_j X[i][v(d+1)+j] Q^j       (rows, forward)
 // Entries past the edge count as zero.
 //
-// These kernels move bytes: one thread per word, consecutive threads on
-// consecutive words of a row, so both the residue reads and the word writes
-// of a warp are contiguous.
+// These kernels move bytes.  Row layouts stage about 4 KB of a row's
+// residues in shared memory per block: the residues move as aligned 32-bit
+// words (an aligned word that holds a byte of the row lies in the same page,
+// so it cannot fault; the bytes past the row in it are not used), the words
+// as consecutive lanes on consecutive words.  Column layouts give a thread
+// four adjacent columns, read or written as one 32-bit word of residues and
+// stored as one 16-byte store of words.
 #include <cstdint>
 #include <type_traits>
 
@@ -32,59 +36,138 @@ __device__ __forceinline__ uint64_t from_word(W w) {
     else return (uint64_t)w;
 }
 
-// Rows, reversed (REV) or forward: thread per word (i, w).
-template <class W, bool REV>
-__global__ void pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx, int64_t rows,
-                                 int64_t cols, int dp1, int t, W *__restrict__ out, int64_t ldw,
-                                 int64_t wc) {
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= wc) return;
-    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
-        const uint8_t *x = X + i * ldx + w * dp1;
-        const int64_t rem = cols - w * dp1;
-        const int n = rem < dp1 ? (int)rem : dp1;
-        uint64_t acc = 0;
-        for (int j = 0; j < n; ++j) {
-            const int s = REV ? dp1 - 1 - j : j;
-            acc += (uint64_t)x[j] << (t * s);
+constexpr int V = 4;   // words per thread
+
+// Store V consecutive words at p: one vector store when p is 16-byte
+// aligned and all V are inside the row, else one by one.
+template <class W>
+__device__ __forceinline__ void store_words(W *p, const W (&v)[V], int n) {
+    if (n == V && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if constexpr (sizeof(W) == 8) {
+            reinterpret_cast<ulonglong2 *>(p)[0] = make_ulonglong2(*reinterpret_cast<const unsigned long long *>(&v[0]),
+                                                                 *reinterpret_cast<const unsigned long long *>(&v[1]));
+            reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(*reinterpret_cast<const unsigned long long *>(&v[2]),
+                                                                 *reinterpret_cast<const unsigned long long *>(&v[3]));
+        } else {
+            *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
         }
-        out[i * ldw + w] = to_word<W>(acc);
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+        if (e < n) p[e] = v[e];
+}
+
+constexpr int STAGE_BYTES = 4096;          // residues staged per block and row
+
+__device__ __forceinline__ int words_per_block(int dp1) {
+    const int w = STAGE_BYTES / dp1;
+    return w < 1024 ? w : 1024;
+}
+
+// Rows, reversed (REV) or forward: a block packs words w0 .. w0 + wpb - 1 of
+// its rows from the residues staged in shared memory.
+template <class W, bool REV>
+__global__ void __launch_bounds__(256) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx, int64_t rows,
+                                                        int64_t cols, int dp1, int t, W *__restrict__ out,
+                                                        int64_t ldw, int64_t wc) {
+    __shared__ uint32_t sbuf[STAGE_BYTES / 4 + 2];
+    const int wpb = words_per_block(dp1);
+    const int64_t w0 = (int64_t)blockIdx.x * wpb;
+    const int nw = wc - w0 < wpb ? (int)(wc - w0) : wpb;
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+        const uint8_t *row = X + i * ldx;
+        const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(row + b0) & ~(uintptr_t)3;
+        const uintptr_t a1 = (reinterpret_cast<uintptr_t>(row + b1) + 3) & ~(uintptr_t)3;
+        const int nq = (int)((a1 - a0) / 4);
+        for (int q = threadIdx.x; q < nq; q += blockDim.x)
+            sbuf[q] = __ldg(reinterpret_cast<const uint32_t *>(a0) + q);
+        __syncthreads();
+        const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbuf) + (reinterpret_cast<uintptr_t>(row + b0) - a0);
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+            const int64_t rem = cols - (w0 + w) * dp1;
+            const int n = rem < dp1 ? (int)rem : dp1;
+            uint64_t acc = 0;
+            for (int j = 0; j < n; ++j) {
+                const int s = REV ? dp1 - 1 - j : j;
+                acc += (uint64_t)sb[w * dp1 + j] << (t * s);
+            }
+            out[i * ldw + w0 + w] = to_word<W>(acc);
+        }
+        __syncthreads();
     }
 }
 
-// Columns: thread per word (w, j).
+// Columns: thread per V words (w, j0 .. j0+V-1), the residues of four
+// adjacent columns read as one 32-bit word when aligned.
 template <class W>
 __global__ void pack_cols_kernel(const uint8_t *__restrict__ X, int64_t ldx, int64_t rows,
                                  int64_t cols, int dp1, int t, W *__restrict__ out, int64_t ldw,
                                  int64_t wr) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+    const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (j0 >= cols) return;
+    const int nj = cols - j0 < V ? (int)(cols - j0) : V;
     for (int64_t w = blockIdx.y; w < wr; w += gridDim.y) {
         const int64_t rem = rows - w * dp1;
         const int n = rem < dp1 ? (int)rem : dp1;
-        const uint8_t *x = X + (w * dp1) * ldx + j;
-        uint64_t acc = 0;
-        for (int s = 0; s < n; ++s) acc += (uint64_t)x[s * ldx] << (t * s);
-        out[w * ldw + j] = to_word<W>(acc);
+        uint64_t acc[V] = {0, 0, 0, 0};
+        for (int s = 0; s < n; ++s) {
+            const uint8_t *x = X + (w * dp1 + s) * ldx + j0;
+            if (nj == V && (reinterpret_cast<uintptr_t>(x) & 3) == 0) {
+                const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(x));
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] += (uint64_t)((q >> (8 * e)) & 0xffu) << (t * s);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (e < nj) acc[e] += (uint64_t)__ldg(x + e) << (t * s);
+            }
+        }
+        W v[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) v[e] = to_word<W>(acc[e]);
+        store_words<W>(out + w * ldw + j0, v, nj);
     }
 }
 
 template <class W, bool REV>
-__global__ void unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw, int64_t rows,
-                                   int64_t cols, int dp1, int t, uint8_t *__restrict__ X,
-                                   int64_t ldx, int64_t wc) {
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= wc) return;
+__global__ void __launch_bounds__(256) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw, int64_t rows,
+                                                          int64_t cols, int dp1, int t, uint8_t *__restrict__ X,
+                                                          int64_t ldx, int64_t wc) {
+    __shared__ uint32_t sbuf[STAGE_BYTES / 4 + 2];
+    const int wpb = words_per_block(dp1);
+    const int64_t w0 = (int64_t)blockIdx.x * wpb;
+    const int nw = wc - w0 < wpb ? (int)(wc - w0) : wpb;
     const uint64_t mask = (1ull << t) - 1;
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
-        const uint64_t v = from_word<W>(Win[i * ldw + w]);
-        const int64_t rem = cols - w * dp1;
-        const int n = rem < dp1 ? (int)rem : dp1;
-        uint8_t *x = X + i * ldx + w * dp1;
-        for (int j = 0; j < n; ++j) {
-            const int s = REV ? dp1 - 1 - j : j;
-            x[j] = (uint8_t)((v >> (t * s)) & mask);
+        uint8_t *row = X + i * ldx;
+        const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(row + b0), hi = reinterpret_cast<uintptr_t>(row + b1);
+        const uintptr_t a0 = lo & ~(uintptr_t)3;
+        uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf) + (lo - a0);
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+            const uint64_t v = from_word<W>(__ldg(Win + i * ldw + w0 + w));
+            const int64_t rem = cols - (w0 + w) * dp1;
+            const int n = rem < dp1 ? (int)rem : dp1;
+            for (int j = 0; j < n; ++j) {
+                const int s = REV ? dp1 - 1 - j : j;
+                sb[w * dp1 + j] = (uint8_t)((v >> (t * s)) & mask);
+            }
         }
+        __syncthreads();
+        // aligned 32-bit words inside [lo, hi) whole, the two ragged ends by bytes
+        const int nq = (int)((((hi + 3) & ~(uintptr_t)3) - a0) / 4);
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const uintptr_t a = a0 + 4 * (uintptr_t)q;
+            if (a >= lo && a + 4 <= hi) {
+                *reinterpret_cast<uint32_t *>(a) = sbuf[q];
+            } else {
+                for (int e = 0; e < 4; ++e)
+                    if (a + e >= lo && a + e < hi) *reinterpret_cast<uint8_t *>(a + e) = (uint8_t)(sbuf[q] >> (8 * e));
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -92,15 +175,29 @@ template <class W>
 __global__ void unpack_cols_kernel(const W *__restrict__ Win, int64_t ldw, int64_t rows,
                                    int64_t cols, int dp1, int t, uint8_t *__restrict__ X,
                                    int64_t ldx, int64_t wr) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+    const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (j0 >= cols) return;
+    const int nj = cols - j0 < V ? (int)(cols - j0) : V;
     const uint64_t mask = (1ull << t) - 1;
     for (int64_t w = blockIdx.y; w < wr; w += gridDim.y) {
-        const uint64_t v = from_word<W>(Win[w * ldw + j]);
+        uint64_t v[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) v[e] = e < nj ? from_word<W>(__ldg(Win + w * ldw + j0 + e)) : 0;
         const int64_t rem = rows - w * dp1;
         const int n = rem < dp1 ? (int)rem : dp1;
-        uint8_t *x = X + (w * dp1) * ldx + j;
-        for (int s = 0; s < n; ++s) x[s * ldx] = (uint8_t)((v >> (t * s)) & mask);
+        for (int s = 0; s < n; ++s) {
+            uint8_t *x = X + (w * dp1 + s) * ldx + j0;
+            if (nj == V && (reinterpret_cast<uintptr_t>(x) & 3) == 0) {
+                uint32_t q = 0;
+#pragma unroll
+                for (int e = 0; e < V; ++e) q |= (uint32_t)((v[e] >> (t * s)) & mask) << (8 * e);
+                *reinterpret_cast<uint32_t *>(x) = q;
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (e < nj) x[e] = (uint8_t)((v[e] >> (t * s)) & mask);
+            }
+        }
     }
 }
 
@@ -148,9 +245,23 @@ __global__ void unpack_block_kernel(const W *__restrict__ Win, int64_t ldw, int6
 
 constexpr int kThreads = 256;
 
-dim3 grid_for(int64_t inner, int64_t outer) {
-    const int64_t gx = (inner + kThreads - 1) / kThreads;
-    const int64_t gy = outer < 65535 ? outer : 65535;
+// blocks of the staged row kernels: one per STAGE_BYTES of residues of a row
+dim3 rows_grid(int64_t wc, int64_t rows, int dp1) {
+    const int64_t wpb = STAGE_BYTES / dp1 < 1024 ? STAGE_BYTES / dp1 : 1024;
+    const int64_t gx = (wc + wpb - 1) / wpb;
+    // about 16 blocks per SM in all, each looping over rows
+    int64_t gy = ((int64_t)num_sms() * 16 + gx - 1) / gx;
+    if (gy > rows) gy = rows;
+    if (gy > 65535) gy = 65535;
+    return dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1));
+}
+
+dim3 grid_for(int64_t inner, int64_t outer, int per_thread = 1) {
+    const int64_t gx = (inner + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+    // about 16 blocks per SM in all, each looping over the outer index
+    int64_t gy = ((int64_t)num_sms() * 16 + gx - 1) / gx;
+    if (gy > outer) gy = outer;
+    if (gy > 65535) gy = 65535;
     return dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1));
 }
 
@@ -160,16 +271,15 @@ cudaError_t pack_t(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, in
     W *out = static_cast<W *>(Wp);
     if (lay == GFP_LAYOUT_COLS) {
         const int64_t wr = (rows + dp1 - 1) / dp1;
-        pack_cols_kernel<W><<<grid_for(cols, wr), kThreads, 0, s>>>(X, ldx, rows, cols, dp1, t,
+        pack_cols_kernel<W><<<grid_for(cols, wr, V), kThreads, 0, s>>>(X, ldx, rows, cols, dp1, t,
                                                                       out, ldw, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
+        const dim3 g = rows_grid(wc, rows, dp1);
         if (lay == GFP_LAYOUT_ROWS_REV)
-            pack_rows_kernel<W, true><<<grid_for(wc, rows), kThreads, 0, s>>>(X, ldx, rows, cols,
-                                                                               dp1, t, out, ldw, wc);
+            pack_rows_kernel<W, true><<<g, kThreads, 0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc);
         else
-            pack_rows_kernel<W, false><<<grid_for(wc, rows), kThreads, 0, s>>>(
-                X, ldx, rows, cols, dp1, t, out, ldw, wc);
+            pack_rows_kernel<W, false><<<g, kThreads, 0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc);
     }
     return cudaGetLastError();
 }
@@ -180,16 +290,15 @@ cudaError_t unpack_t(int64_t rows, int64_t cols, const void *Wp, int64_t ldw, in
     const W *in = static_cast<const W *>(Wp);
     if (lay == GFP_LAYOUT_COLS) {
         const int64_t wr = (rows + dp1 - 1) / dp1;
-        unpack_cols_kernel<W><<<grid_for(cols, wr), kThreads, 0, s>>>(in, ldw, rows, cols, dp1, t,
+        unpack_cols_kernel<W><<<grid_for(cols, wr, V), kThreads, 0, s>>>(in, ldw, rows, cols, dp1, t,
                                                                         X, ldx, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
+        const dim3 g = rows_grid(wc, rows, dp1);
         if (lay == GFP_LAYOUT_ROWS_REV)
-            unpack_rows_kernel<W, true><<<grid_for(wc, rows), kThreads, 0, s>>>(
-                in, ldw, rows, cols, dp1, t, X, ldx, wc);
+            unpack_rows_kernel<W, true><<<g, kThreads, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc);
         else
-            unpack_rows_kernel<W, false><<<grid_for(wc, rows), kThreads, 0, s>>>(
-                in, ldw, rows, cols, dp1, t, X, ldx, wc);
+            unpack_rows_kernel<W, false><<<g, kThreads, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc);
     }
     return cudaGetLastError();
 }
