@@ -1,6 +1,10 @@
 // CUDA-core forms of C = A B mod p: the classical product, the Q-adic dot
 // form of Section 2 in five machine words, and the right-compressed form of
 // Section 3 with the simultaneous reduction REDQ.
+// Every policy declares the whole interface the kernel template may use
+// (extract, kSlowPipe, ...); an instantiation that does not use a member
+// makes the front end note it, which says nothing here.
+#pragma nv_diag_suppress 177
 #include <cstdint>
 #include <type_traits>
 
