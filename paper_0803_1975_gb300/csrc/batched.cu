@@ -1072,11 +1072,9 @@ gfp_status launch_plan(void *ws, cudaStream_t s) {
     gfp_status st = check_launch();
     if (st != GFP_OK) return st;
     if (simt) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BATCHED);
-            attr = true;
-        }
+        static std::atomic<uint64_t> attr{0};
+        cudaError_t e = smem_attr_once(reinterpret_cast<const void *>(batched_kernel), SMEM_BATCHED, attr);
+        if (e != cudaSuccess) return cuda_fail(e);
         batched_kernel<<<std::max(1, num_sms() * CTAS_PER_SM), NT, SMEM_BATCHED, s>>>(base);
         st = check_launch();
         if (st != GFP_OK) return st;

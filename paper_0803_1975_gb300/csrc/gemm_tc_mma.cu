@@ -271,11 +271,9 @@ gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint
     g.off = (uint32_t)((((int64_t)1 << 30) + p - 1) / p * p);
     g.M = fastmod_magic(p);
     const int smem = STAGES * 2 * TILE_BYTES;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(mma_s8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(mma_s8_kernel), smem, attr);
+    if (ea != cudaSuccess) return cuda_fail(ea);
     dim3 grid((unsigned)(np / BN), (unsigned)(mp / BM));
     mma_s8_kernel<<<grid, NT, smem, s>>>(g);
     return check_launch();

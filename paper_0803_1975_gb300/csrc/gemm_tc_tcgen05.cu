@@ -759,12 +759,9 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp, int 
 template <class CFG, bool BLOCKED, bool GROUPED = false>
 void launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, int grid, cudaStream_t s,
                 const TcGroupHeader *grp = nullptr) {
-    static bool set = false;   // per instantiation
-    if (!set) {
-        cudaFuncSetAttribute(tc_f16_kernel<CFG, BLOCKED, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             CFG::SMEM_BYTES);
-        set = true;
-    }
+    static std::atomic<uint64_t> attr{0};   // per instantiation
+    // a failure here shows up as the launch's error
+    smem_attr_once(reinterpret_cast<const void *>(tc_f16_kernel<CFG, BLOCKED, GROUPED>), CFG::SMEM_BYTES, attr);
     tc_f16_kernel<CFG, BLOCKED, GROUPED><<<grid, NTHREADS, CFG::SMEM_BYTES, s>>>(ma, mb, g, grp);
 }
 

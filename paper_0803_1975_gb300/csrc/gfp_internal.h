@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <atomic>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -18,6 +20,20 @@ inline gfp_status check_launch() {
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
 }
 int num_sms();                         // SM count of the current device (cached per device)
+
+// Raise a kernel's dynamic shared-memory limit on the current device, once
+// per device (the attribute belongs to the device's context); `done` is the
+// kernel's own mask of devices already set.
+inline cudaError_t smem_attr_once(const void *kernel, int bytes, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // ---- parameters (params.cpp) ------------------------------------------------
 bool is_prime_small(uint32_t p);       // p prime and 2 <= p <= 251
