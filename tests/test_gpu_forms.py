@@ -183,7 +183,8 @@ def test_tc_kblock_reduction():
 
 # --------------------------------------------------------------- compressed dot
 DOT_CASES = [(3, 1024, 1024, 1024), (3, 100, 333, 70), (5, 64, 1000, 200), (31, 40, 8, 50),
-             (2, 129, 257, 65), (251, 33, 40, 33)]
+             (2, 129, 257, 65), (251, 33, 40, 33),
+             (7, 1, 1, 1), (3, 1, 500, 1), (5, 300, 1, 2), (3, 2, 3, 1)]
 
 
 @pytest.mark.parametrize("word", ["u64", "u64x128", "u32w", "u32", "f64"])
@@ -251,7 +252,7 @@ def test_dot_blocked(word, p, k, kb):
 
 # ------------------------------------------------------------------------ mixed
 MIXED_CASES = [(3, 1024, 1024, 1024), (3, 77, 300, 101), (5, 64, 200, 64), (251, 20, 30, 41),
-               (2, 65, 129, 67)]
+               (2, 65, 129, 67), (7, 1, 1, 1), (3, 1, 500, 1), (5, 300, 1, 2), (3, 2, 3, 1)]
 
 
 @pytest.mark.parametrize("word", ["u64", "f64"])
@@ -289,7 +290,7 @@ def test_mixed_worst_case(word):
 
 # ------------------------------------------------------ left / full compression
 LEFT_CASES = [(3, 1024, 1024, 1024), (3, 77, 300, 101), (5, 64, 200, 64), (251, 41, 30, 20),
-              (2, 67, 129, 65)]
+              (2, 67, 129, 65), (7, 1, 1, 1), (3, 1, 500, 1), (5, 300, 1, 2), (3, 2, 3, 1)]
 
 
 @pytest.mark.parametrize("word", ["u64", "f64"])
@@ -309,7 +310,7 @@ def test_left_matches_oracle(word, p, m, k, n):
 
 
 FULL_CASES = [(3, 1024, 1024, 1024), (3, 77, 300, 101), (5, 64, 200, 64), (7, 33, 40, 17),
-              (2, 65, 129, 67)]
+              (2, 65, 129, 67), (7, 1, 1, 1), (3, 1, 500, 1), (5, 300, 1, 2), (3, 2, 3, 1)]
 
 
 @pytest.mark.parametrize("word", ["u64", "f64"])
