@@ -457,8 +457,8 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  *  probs       : HOST array of `count` problems; each is validated on the host.
  *  algo        : GFP_ALGO_AUTO   -- per size bucket (the largest of m, k, n),
  *                                   the tile kind gfp_batched_autotune chose;
- *                                   untuned buckets use tcgen05 tiles for
- *                                   p < 16 above m, n = 96, else fp16 MMA tiles;
+ *                                   untuned buckets use the tcgen05 tiles
+ *                                   (GFP_ALGO_TC_F8 below);
  *                GFP_ALGO_TC_F16 -- warp-level fp16 tensor-core MMA tiles
  *                                   (128 x 128 above m, n = 160, 64 x 64,
  *                                   32 x 32 for m, n <= 48) on
@@ -468,9 +468,11 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  *                                   words, residues packed while staged, with
  *                                   (Q, d, k-block) chosen per problem;
  *                GFP_ALGO_TC_F8  -- tcgen05 128 x 128 tiles of a second
- *                                   grouped kernel, for p < 16 (residue bytes
- *                                   read as e4m3 codes of r 2^-9, exact while
- *                                   k (p-1)^2 < 2^24); other problems fall
+ *                                   grouped kernel: for p < 16 residue bytes
+ *                                   read as e4m3 codes of r 2^-9 (exact while
+ *                                   k (p-1)^2 < 2^24), for larger p centred
+ *                                   fp16 (exact while k h^2 + p < 2^24, k <=
+ *                                   32768); problems beyond those bounds fall
  *                                   back to the fp16 MMA tiles.
  *  status      : optional HOST array of `count` per-problem statuses.  A
  *                problem that fails validation is skipped (its C untouched)
@@ -503,7 +505,7 @@ GFP_API gfp_status gfp_batched_launch(void *workspace, size_t ws_bytes, void *st
  * (512,2048], above) it times one grouped launch of that bucket's problems
  * with each tile kind (0 = fp16 MMA 64 x 64, 1 = fp16 MMA 32 x 32, 2 = Q-adic
  * 32-bit words with per-problem Q and d, 3 = fp16 MMA 128 x 128, 4 = tcgen05
- * e4m3 128 x 128 for p < 16) and keeps the fastest; then it times the whole
+ * 128 x 128, e4m3 for p < 16, fp16 above) and keeps the fastest; then it times the whole
  * batch with that table, with the default kinds (table -1) and with the
  * tcgen05 kind in every bucket (where it applies), and keeps the fastest
  * table -- mixing engines adds a grouped kernel that buckets timed alone do

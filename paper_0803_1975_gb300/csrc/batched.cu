@@ -72,7 +72,7 @@ struct Item {                // 8 bytes: problem index, tile row, tile column
     uint16_t tm, tn;
 };
 
-enum ConvMode : int32_t { CONV_F16 = 0, CONV_RAW = 1, CONV_RAW_T = 2 };
+enum ConvMode : int32_t { CONV_F16 = 0, CONV_RAW = 1, CONV_RAW_T = 2, CONV_F16_T = 3 };
 
 struct ConvJob {             // 48 bytes: one operand to convert
     const uint8_t *src;
@@ -172,6 +172,7 @@ __device__ __forceinline__ uint4 staged16(const uint8_t *buf, uint32_t d, int ch
 //             (aligned 16-byte blocks by cp.async, rows keep their
 //             misalignment) and written 4 destination rows x 16 bytes per
 //             thread through 4 x 4 byte transposes.
+// CONV_F16_T: the same transpose, each residue written as centred fp16.
 // Destination rows below drows, columns below dcols; what lies outside the
 // source matrix is written as zero.
 constexpr int CONV_CTAS_PER_SM = 4;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(const ui
         const ConvTask ci = nx;
         if (it + (int)gridDim.x < ntasks) nx = tasks[it + gridDim.x];
         const ConvJob &J = ci.J;
-        if (J.mode == CONV_RAW_T) {
+        if (J.mode == CONV_RAW_T || J.mode == CONV_F16_T) {
             // dst[j][l] = src[l][j]: dst rows j0 .. j0+127, dst columns l0 .. l0+127
             const int j0 = ci.row0, l0 = ci.col0;
             uint8_t *st = stage[tb];
@@ -241,12 +242,34 @@ __global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(const ui
                     D[2][g] = __byte_perm(t2, t3, 0x5410);
                     D[3][g] = __byte_perm(t2, t3, 0x7632);
                 }
+                if (J.mode == CONV_RAW_T) {
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int j = j0 + 4 * wc + b;
-                    if (j < J.drows)
-                        *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)j * J.dld + l0 + 16 * qg) =
-                            make_uint4(D[b][0], D[b][1], D[b][2], D[b][3]);
+                    for (int b = 0; b < 4; ++b) {
+                        const int j = j0 + 4 * wc + b;
+                        if (j < J.drows)
+                            *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)j * J.dld + l0 + 16 * qg) =
+                                make_uint4(D[b][0], D[b][1], D[b][2], D[b][3]);
+                    }
+                } else {
+                    const float hf = J.p == 2 ? 1.f : (float)((J.p - 1) / 2);
+                    const __half2 c1536 = __floats2half2_rn(1536.f, 1536.f);
+                    const __half2 hh = __floats2half2_rn(hf, hf);
+                    const __half2 mp = __floats2half2_rn(-(float)J.p, -(float)J.p);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int j = j0 + 4 * wc + b;
+                        if (j >= J.drows) continue;
+                        uint32_t o[8];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            o[2 * e] = centre2(D[b][e], 0x4140u, c1536, hh, mp);
+                            o[2 * e + 1] = centre2(D[b][e], 0x4342u, c1536, hh, mp);
+                        }
+                        uint4 *dp = reinterpret_cast<uint4 *>(static_cast<__half *>(J.dst) + (int64_t)j * J.dld + l0 +
+                                                              16 * qg);
+                        dp[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                        dp[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                    }
                 }
             }
             continue;
@@ -261,6 +284,8 @@ __global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(const ui
         const __half2 mp = __floats2half2_rn(-(float)J.p, -(float)J.p);
         const int L = min(J.dcols, 512), cpr = L / 16, nb = cpr + 1;   // chunks and blocks per run
         const int G = ci.nrows / 8;                                    // rows of this warp
+        // quotients by nb >= 2 and cpr >= 1 as multiply-high by ceil(2^32 / x)
+        // (exact for the small numerators here); x = 1 has no 32-bit magic
         const uint32_t mnb = 0xFFFFFFFFu / (uint32_t)nb + 1u, mcpr = 0xFFFFFFFFu / (uint32_t)cpr + 1u;
         for (int c0 = 0; c0 < J.dcols; c0 += 512) {
             for (int b = lane; b < G * nb; b += 32) {
@@ -276,7 +301,7 @@ __global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(const ui
             asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
             for (int q = lane; q < G * cpr; q += 32) {
-                const int g = (int)__umulhi((uint32_t)q, mcpr), ch = q - g * cpr;
+                const int g = cpr == 1 ? q : (int)__umulhi((uint32_t)q, mcpr), ch = q - g * cpr;
                 const int r = ci.row0 + warp + 8 * g;
                 const int c = c0 + 16 * ch;
                 if (r >= rend || c >= J.dcols) continue;
@@ -583,13 +608,20 @@ int bucket_of(int64_t m, int64_t k, int64_t n) {
     return 6;
 }
 
+// fp16 mma.sync tile for a problem's size
+int hmma_kind(int64_t m, int64_t n) {
+    const int64_t s = std::max(m, n);
+    return s <= 48 ? KIND_HMMA32 : s <= 160 ? KIND_HMMA64 : KIND_HMMA128;
+}
+
+// Untuned: the tcgen05 tiles (a problem they cannot take falls back to the
+// mma.sync tiles in make_plan).
 int default_kind(int64_t m, int64_t k, int64_t n, uint32_t p) {
+    (void)p;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int b = bucket_of(m, k, n);
     if (g_tuned[b] >= 0) return g_tuned[b];
-    const int64_t s = std::max(m, n);
-    if (p < 16) return KIND_TC8;                 // tcgen05 tiles (falls back when not eligible)
-    return s <= 48 ? KIND_HMMA32 : s <= 160 ? KIND_HMMA64 : KIND_HMMA128;
+    return KIND_TC8;
 }
 
 // (t, d, words per block) of the 32-bit dot form for (p, k): the chooser of
@@ -625,6 +657,7 @@ bool dot32_params(uint32_t p, int64_t k, int *t_out, int *d_out, int *kbw_out) {
 
 struct TcHostProb {                          // a problem of the grouped tcgen05 launch
     int bin;                                 // k-stride bin of its operands
+    int f16;                                 // centred fp16 operands (else raw e4m3)
     int32_t rowA0, rowB0, ktiles, klast;     // rows in the bin's array, k in 128-slices,
                                              // 32-wide MMAs of the last slice
     int64_t m, n, k, ldc;
@@ -669,8 +702,22 @@ int64_t tc8_kmax(uint32_t p) {
     return pr == 0 ? ((int64_t)1 << 30) : (((int64_t)1 << 24) - 1 - p) / pr;
 }
 
+// fp32-exact k-block of the centred fp16 products (|c| <= h = (p-1)/2)
+int64_t tc16_kmax(uint32_t p) {
+    const int64_t h = p == 2 ? 1 : (p - 1) / 2;
+    return (((int64_t)1 << 24) - 1 - p) / (h * h);
+}
+
+// The tcgen05 tiles take a problem whose k fits one fp32-exact k-block and
+// whose K-major rows fit the widest stride bin: raw e4m3 bytes for p < 16,
+// centred fp16 otherwise.
+bool tc_f16_operands(uint32_t p) { return p >= 16; }
+
 bool tc8_eligible(const gfp_problem &q) {
-    return q.p < 16 && q.k > 0 && q.k <= tc8_kmax(q.p) && q.k <= (int64_t)128 << (TC_GROUP_BINS - 1);
+    const int64_t widest = (int64_t)128 << (TC_GROUP_BINS - 1);
+    if (q.k <= 0) return false;
+    if (!tc_f16_operands(q.p)) return q.k <= tc8_kmax(q.p) && q.k <= widest;
+    return q.k <= tc16_kmax(q.p) && 2 * round_to(q.k, 16) <= widest;
 }
 
 // stride bin of k: the smallest 128 2^b >= k
@@ -759,13 +806,18 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
     // not padded: an output entry depends on one row of A and one row of B^T
     // only, so the rows of a neighbour that a 128-row tile also covers reach
     // only outputs outside the product, which are never stored.
-    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, int>, int64_t> tc_seen;
+    std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, int, uint32_t>, int64_t> tc_seen;
     auto tc_job = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld, uint32_t p, int mode,
                       int64_t k) -> int64_t {
-        const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, mode);
+        // raw bytes do not depend on p; centred fp16 values do
+        const bool centred = mode == CONV_F16 || mode == CONV_F16_T;
+        const auto key = std::make_tuple((uintptr_t)src, ld, rows, cols, mode, centred ? p : 0u);
         auto it = tc_seen.find(key);
         if (it != tc_seen.end()) return it->second;
-        const int bin = tc8_bin(k);
+        const bool f16 = mode == CONV_F16 || mode == CONV_F16_T;
+        const int es = f16 ? 2 : 1;
+        const int64_t row_bytes = f16 ? 2 * round_to(k, 16) : round_to(k, 32);
+        const int bin = tc8_bin(row_bytes);
         ConvJob J{};
         J.src = src;
         J.rows = rows;
@@ -773,15 +825,15 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         J.ld = ld;
         J.p = p;
         J.mode = mode;
-        J.dld = (int32_t)(128 << bin);
-        J.dcols = (int32_t)round_to(k, 32);
-        J.drows = mode == CONV_RAW_T ? cols : rows;
+        J.dld = (int32_t)((128 << bin) / es);        // elements
+        J.dcols = (int32_t)(row_bytes / es);
+        J.drows = (mode == CONV_RAW_T || mode == CONV_F16_T) ? cols : rows;
         const int jid = (int)plan.jobs.size();
         plan.jobs.push_back(J);
         const int64_t row0 = plan.bin_rows[bin];
         plan.bin_rows[bin] += J.drows;
         plan.tc_places.push_back(TcJobPlace{jid, bin, row0});
-        if (mode == CONV_RAW_T) {
+        if (mode == CONV_RAW_T || mode == CONV_F16_T) {
             for (int32_t r = 0; r < J.drows; r += 128)
                 for (int32_t c = 0; c < J.dcols; c += 128) plan.citems.push_back(ConvItem{jid, r, c, 128});
         } else {
@@ -798,14 +850,12 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         if (st == GFP_OK) {
             if (forced_kind) kind = *forced_kind;
             else if (algo == GFP_ALGO_AUTO) kind = default_kind(q.m, q.k, q.n, q.p);
-            else if (algo == GFP_ALGO_TC_F16) {
-                const int64_t sz = std::max(q.m, q.n);
-                kind = sz <= 48 ? KIND_HMMA32 : sz <= 160 ? KIND_HMMA64 : KIND_HMMA128;
-            } else if (algo == GFP_ALGO_DOT32) kind = KIND_DOT32;
+            else if (algo == GFP_ALGO_TC_F16) kind = hmma_kind(q.m, q.n);
+            else if (algo == GFP_ALGO_DOT32) kind = KIND_DOT32;
             else if (algo == GFP_ALGO_TC_F8) kind = KIND_TC8;
             else st = GFP_EUNSUPPORTED;
         }
-        if (st == GFP_OK && kind == KIND_TC8 && !tc8_eligible(q)) kind = KIND_HMMA64;
+        if (st == GFP_OK && kind == KIND_TC8 && !tc8_eligible(q)) kind = hmma_kind(q.m, q.n);
         DevProblem P{};
         if (st == GFP_OK && kind == KIND_DOT32) {
             int t = 0, d = 0, kbw = 0;
@@ -823,14 +873,16 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         }
         if (q.m == 0 || q.n == 0) continue;
         if (kind == KIND_TC8) {
-            // raw e4m3 operands: A (m x k) copied, B transposed, both K-major,
-            // padded to 128 rows and 128 columns of k
+            // A (m x k) and B^T, K-major: raw e4m3 bytes (p < 16) or centred fp16
+            const bool f16 = tc_f16_operands(q.p);
+            const int64_t row_bytes = f16 ? 2 * round_to(q.k, 16) : round_to(q.k, 32);
             TcHostProb T{};
-            T.bin = tc8_bin(q.k);
-            T.ktiles = (int32_t)(round_to(q.k, 128) / 128);
-            T.klast = (int32_t)((round_to(q.k, 32) - 128 * (T.ktiles - 1)) / 32);
-            T.rowA0 = (int32_t)tc_job(q.A, q.m, q.k, q.lda, q.p, CONV_RAW, q.k);
-            T.rowB0 = (int32_t)tc_job(q.B, q.k, q.n, q.ldb, q.p, CONV_RAW_T, q.k);
+            T.f16 = f16 ? 1 : 0;
+            T.bin = tc8_bin(row_bytes);
+            T.ktiles = (int32_t)((row_bytes + 127) / 128);
+            T.klast = (int32_t)((row_bytes - 128 * (T.ktiles - 1)) / 32);
+            T.rowA0 = (int32_t)tc_job(q.A, q.m, q.k, q.lda, q.p, f16 ? CONV_F16 : CONV_RAW, q.k);
+            T.rowB0 = (int32_t)tc_job(q.B, q.k, q.n, q.ldb, q.p, f16 ? CONV_F16_T : CONV_RAW_T, q.k);
             T.m = q.m;
             T.n = q.n;
             T.k = q.k;
@@ -938,7 +990,7 @@ size_t bound_bytes(int64_t count, const gfp_problem *probs) {
         items += ((m + 31) / 32) * ((n + 31) / 32);
         tcitems += ((m + 127) / 128) * ((n + 127) / 128);
         const int64_t mm = round_to(m, 128), kk = round_to(k, 128), nn = round_to(n, 128);
-        ops += round_to((mm * kk + kk * nn) * 2, 256) + 2 * 256;
+        ops += round_to((mm * kk + kk * nn) * 4, 256) + 2 * 256;   // fp16 rows in a bin up to twice as wide
         citems += (mm + kk) / 16 + (kk / 64) * (nn / 64);
     }
     ops += TC_GROUP_BINS * 256;
@@ -1011,15 +1063,22 @@ gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
         Q.n = (int32_t)T.n;
         Q.rowA0 = T.rowA0;
         Q.rowB0 = T.rowB0;
-        Q.ktiles = T.ktiles;                 // one k-block: k <= tc8_kmax(p) by eligibility
+        Q.ktiles = T.ktiles;                 // one k-block: k within the kind's bound by eligibility
         Q.klast = T.klast;
-        // sums below 2^23 units: the epilogue reads them from a mantissa
-        Q.red = (int64_t)T.k * (T.p - 1) * (T.p - 1) < ((int64_t)1 << 23) ? 1 : 0;
-        Q.bin = map_of[T.bin];
+        Q.bin = (int16_t)map_of[T.bin];
+        Q.kind = (int16_t)T.f16;
         Q.p = T.p;
-        Q.off = 0;                           // raw residues: every sum is >= 0
-        Q.scale = 262144.0f;                 // raw e4m3: values r 2^-9
         Q.m32 = (uint32_t)(0xFFFFFFFFull / T.p + 1);
+        if (T.f16) {
+            Q.red = 0;                           // centred sums |x| < 2^24: offset, then reduce
+            Q.off = (uint32_t)((((int64_t)1 << 24) + T.p - 1) / T.p * T.p);
+            Q.scale = 1.0f;
+        } else {
+            // sums below 2^23 units: the epilogue reads them from a mantissa
+            Q.red = (int64_t)T.k * (T.p - 1) * (T.p - 1) < ((int64_t)1 << 23) ? 1 : 0;
+            Q.off = 0;                           // raw residues: every sum is >= 0
+            Q.scale = 262144.0f;                 // raw e4m3: values r 2^-9
+        }
     }
     std::vector<uint8_t> host((size_t)L.ops, 0);   // the operand area itself is written by the launch
     std::memcpy(host.data(), &H, sizeof(H));

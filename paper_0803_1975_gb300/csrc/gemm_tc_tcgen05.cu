@@ -472,10 +472,16 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         // the last slice of a grouped product may hold fewer written columns
                         const int nkk = kt == ti.ktiles - 1 ? ti.klast : ROWB / 32;
 #pragma unroll
-                        for (int kk = 0; kk < ROWB / 32; ++kk)   // 32 bytes of k per MMA
-                            if (kk < nkk)
-                                mma_issue<CFG::FP8>(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
-                                                    CFG::IDESC, (kt > k0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < ROWB / 32; ++kk) {  // 32 bytes of k per MMA
+                            if (kk >= nkk) break;
+                            const uint64_t da = smem_desc(sa + kk * 32), db = smem_desc(sb + kk * 32);
+                            const uint32_t acc = (kt > k0 || kk > 0) ? 1u : 0u;
+                            // grouped tiles pick the kind per problem: fp16 operands carry
+                            // scale 1, raw e4m3 ones 2^18 (the instruction descriptor is the
+                            // same: type fields 0 are f16 and e4m3)
+                            if (GROUPED && ti.scale == 1.0f) mma_issue<false>(d, da, db, CFG::IDESC, acc);
+                            else mma_issue<CFG::FP8>(d, da, db, CFG::IDESC, acc);
+                        }
                         mma_commit(empty_bar(stage));
                         if (++stage == STAGES) {
                             stage = 0;

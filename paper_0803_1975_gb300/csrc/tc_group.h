@@ -1,9 +1,10 @@
 // Schedule of the grouped tcgen05 launch (written by batched.cu, read by the
-// kernel in gemm_tc_tcgen05.cu).  The raw e4m3 operands of its problems are
-// stacked, K-major, in a few arrays: one per k-stride bin (128 2^b bytes per
-// row), A rows and B^T rows of a problem in the same array, one tensor map
-// per array.  A problem is then a bin and two row offsets; only its first
-// k (rounded up to 32) columns are written.
+// kernel in gemm_tc_tcgen05.cu).  The operands of its problems -- raw e4m3
+// residues for p < 16, centred fp16 otherwise -- are stacked, K-major, as
+// bytes in a few arrays: one per k-stride bin (128 2^b bytes per row), A rows
+// and B^T rows of a problem in the same array, one byte-typed tensor map per
+// array.  A problem is then a bin, a kind and two row offsets; only its first
+// k elements (rounded up to 32 bytes) of each row are written.
 #pragma once
 
 #include <cstdint>
@@ -17,9 +18,12 @@ struct alignas(64) TcGroupProblem {          // 64 bytes
     int64_t ldc;
     int32_t m, n;
     int32_t rowA0, rowB0;                    // first row of A and of B^T in the bin's array
-    int32_t ktiles, bin;                     // k in 128-element slices; stride bin
+    int32_t ktiles;                          // k in 128-byte slices
+    int16_t bin;                             // stride bin (tensor map index)
+    int16_t kind;                            // 0: raw e4m3 (kind::f8f6f4), 1: centred fp16 (kind::f16);
+                                             // the kernel tells them apart by `scale`
     uint32_t p, off;                         // off: 0 (raw products are non-negative)
-    float scale;
+    float scale;                             // 2^18 (raw e4m3), 1 (fp16)
     uint32_t m32;                            // ceil(2^32 / p)
     int32_t klast;                           // 32-wide MMAs in the last k slice (1-4)
     int32_t red;                             // 1: every sum < 2^23 units (mantissa read)

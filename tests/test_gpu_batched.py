@@ -186,7 +186,8 @@ def test_batched_tcgen05_garbage_workspace():
     items, host_ops = [], []
     shared = inputs.residues(g, 7, 140, 33)
     for p, m, k, n in ((3, 97, 1, 200), (5, 130, 31, 99), (7, 140, 33, 150), (13, 200, 129, 129),
-                       (11, 255, 257, 97), (2, 128, 1000, 300), (3, 300, 96, 101), (5, 101, 160, 400)):
+                       (11, 255, 257, 97), (2, 128, 1000, 300), (3, 300, 96, 101), (5, 101, 160, 400),
+                       (31, 130, 65, 99), (251, 200, 300, 129), (17, 97, 1, 140)):
         A = inputs.residues(g, p, m, k)
         B = inputs.residues(g, p, k, n)
         items.append((p, dev(A), dev(B), torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
@@ -196,6 +197,40 @@ def test_batched_tcgen05_garbage_workspace():
         B = inputs.residues(g, 7, 33, n)
         items.append((7, Sd, dev(B), torch.full((140, n), 255, dtype=torch.uint8, device="cuda")))
         host_ops.append((7, shared, B))
+    arr, cnt = gfp.make_problems(items)
+    ws = torch.full((gfp.gfp_batched_workspace_size(arr, cnt),), 255, dtype=torch.uint8, device="cuda")
+    gfp.gfp_batched_prepare(arr, cnt, "tc_f8", ws)
+    gfp.gfp_batched_launch(ws)
+    torch.cuda.synchronize()
+    assert int(ws[192:196].cpu().numpy().view(np.int32)[0]) == 0
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all(), (p, A.shape, B.shape)
+
+
+def test_batched_tcgen05_fp16_tiles():
+    """p >= 16 on the grouped tcgen05 tiles: centred fp16 operands (kind::f16)
+    in the same launch as raw e4m3 problems; ragged shapes; one matrix shared
+    by products mod 31 and mod 251 (centred differently); the worst case at
+    the fp16 bound (p = 251, k = 1073: every sum k h^2 below 2^24) and one
+    past it (k = 1074, which falls back to the mma.sync tiles)."""
+    g = np.random.Generator(np.random.PCG64(23))
+    items, host_ops = [], []
+    for p, m, k, n in ((17, 129, 200, 127), (31, 300, 513, 260), (101, 97, 64, 400), (251, 1, 700, 130),
+                       (251, 256, 1000, 256), (3, 200, 300, 200), (19, 33, 17, 35)):
+        A = inputs.residues(g, p, m, k)
+        B = inputs.residues(g, p, k, n)
+        items.append((p, dev(A), dev(B), torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A, B))
+    shared = inputs.residues(g, 31, 130, 150)       # one matrix, centred differently for p = 31 and 251
+    for pp in (31, 251):
+        Bs = inputs.residues(g, 31, 150, 90)
+        items.append((pp, dev(shared), dev(Bs), torch.full((130, 90), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((pp, shared, Bs))
+    for k in (1073, 1074):
+        A = np.full((150, k), 125, np.uint8)          # centred +125
+        B = np.full((k, 140), 126, np.uint8)          # centred -125
+        items.append((251, dev(A), dev(B), torch.full((150, 140), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((251, A, B))
     arr, cnt = gfp.make_problems(items)
     ws = torch.full((gfp.gfp_batched_workspace_size(arr, cnt),), 255, dtype=torch.uint8, device="cuda")
     gfp.gfp_batched_prepare(arr, cnt, "tc_f8", ws)
