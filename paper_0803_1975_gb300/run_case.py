@@ -35,6 +35,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--algo", default="auto", help="batched: auto, tc_f16, tc_f8 or dot32")
     ap.add_argument("--levels", type=int, default=1, help="winograd: Strassen-Winograd levels")
+    ap.add_argument("--primes", default="", help="batched: comma-separated primes replacing the workload's "
+                                                 "p in {3, 5, 7} (cycled; 0/1 matrices are residues for any p)")
     ap.add_argument("--warmup", type=int, default=1)
     a = ap.parse_args()
     m = a.m or a.size
@@ -70,7 +72,10 @@ def main():
     elif a.form == "batched":
         # the 4096-problem adjacency workload, one prepared schedule replayed
         items = []
-        for pp, Ah in inputs.batched_problems():
+        primes = [int(x) for x in a.primes.split(",") if x]
+        for i, (pp, Ah) in enumerate(inputs.batched_problems()):
+            if primes:
+                pp = primes[i % len(primes)]
             Ad = torch.from_numpy(Ah).cuda()
             items.append((pp, Ad, Ad, torch.empty(Ah.shape, dtype=torch.uint8, device="cuda")))
         arr, cnt = gfp.make_problems(items)
