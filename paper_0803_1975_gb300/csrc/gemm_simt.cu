@@ -151,9 +151,7 @@ struct DotU64Raw : DotBase<uint64_t, uint64_t, false> {
 // 64-bit words, 128-bit accumulator (largest word < 2^64, t(d+1) <= 128).
 template <bool BLK>
 struct DotU64x128 : DotBase<uint64_t, unsigned __int128, BLK> {
-    __device__ static void mac(unsigned __int128 &acc, uint64_t a, uint64_t b) {
-        acc += (unsigned __int128)a * b;
-    }
+    __device__ static void mac(unsigned __int128 &acc, uint64_t a, uint64_t b) { mad_u64_u128(acc, a, b); }
     __device__ static uint64_t digit(unsigned __int128 acc, const DotParams &prm) {
         return (uint64_t)(acc >> prm.td) & prm.mask;
     }
@@ -404,44 +402,89 @@ struct FullT {
     }
 };
 
-// Tile shapes, 256 threads each: L = 128 x 128 (8 x 8 per thread), S = 64 x 64
-// (4 x 4), XS = 32 x 32 (2 x 2).  Larger register tiles issue fewer shared-
-// memory loads per multiply-add; smaller tiles balance better over the SMs.
+// Tile shapes, 256 threads each: L = 128 x 128 (8 x 8 per thread), M = 128 x
+// 64 (8 x 4), S = 64 x 64 (4 x 4), XS = 32 x 32 (2 x 2).  Larger register
+// tiles issue fewer shared-memory loads per multiply-add; smaller tiles
+// balance better over the SMs and leave registers for more resident warps.
 // The choice minimises (tiles on the busiest SM) x (tile area) / (issue
-// efficiency of the tile), with the efficiency taken as 1 for every shape when
-// the policy is bound by a slow pipe (kSlowPipe, e.g. FP64).
-enum class Tile { L, S, XS };
+// efficiency of the tile), with the efficiencies measured on GB300 (products
+// of 4096 and 16384 on a side) per class of policy:
+//   byte operands, 32-bit accumulator (classical): L 1, M 0.95, S 0.86, XS 0.46
+//   32-bit words, 32-bit accumulator:              L 0.9, M 1, S 0.83, XS 0.5
+//   32-bit words, 64-bit accumulator:              L 0.95, M 1, S 0.97, XS 0.83
+//   64-bit words:                                  L 0.85, M 0.9, S 1, XS 0.95
+//   128-bit accumulator:                           M 0.88, S 0.93, XS 1
+//   a slow pipe (FP64 words, kSlowPipe):           1 for every shape
+// L and M hold 32 to 64 accumulators per thread: not for 128-bit
+// accumulators, nor for 64-bit ones beside the 32-bit block sums of a blocked
+// product (they would spill).
+enum class Tile { L, M, S, XS };
 
 template <class P>
-Tile choose_tile(int64_t M, int64_t N, bool allow_large) {
+constexpr bool large_tiles_fit() {
+    return sizeof(typename P::Acc) <= 8 && !(P::kBlocked && sizeof(typename P::Acc) > 4);
+}
+
+struct TileEff {
+    double L, M, S, XS;
+};
+
+template <class P>
+constexpr TileEff tile_eff() {
+    if constexpr (P::kSlowPipe) return {1.0, 1.0, 1.0, 1.0};
+    else if constexpr (sizeof(typename P::Acc) > 8) return {0.5, 0.88, 0.93, 1.0};
+    else if constexpr (sizeof(typename P::SA) == 8 || sizeof(typename P::SB) == 8) return {0.85, 0.9, 1.0, 0.95};
+    else if constexpr (sizeof(typename P::GA) == 1 && sizeof(typename P::GB) == 1) return {1.0, 0.95, 0.86, 0.46};
+    else if constexpr (sizeof(typename P::Acc) == 8) return {0.95, 1.0, 0.97, 0.83};
+    else return {0.9, 1.0, 0.83, 0.5};
+}
+
+template <class P>
+Tile choose_tile(int64_t M, int64_t N) {
     const int64_t sms = num_sms();
-    const double effL = 1.0, effS = P::kSlowPipe ? 1.0 : 0.7, effXS = P::kSlowPipe ? 1.0 : 0.4;
-    auto cost = [&](int bm, int bn, double eff) {
-        const int64_t t = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
-        return (double)((t + sms - 1) / sms) * bm * bn / eff;
+    constexpr TileEff eff = tile_eff<P>();
+    auto tiles = [&](int bm, int bn) { return ((M + bm - 1) / bm) * ((N + bn - 1) / bn); };
+    auto cost = [&](int bm, int bn, double e) {
+        return (double)((tiles(bm, bn) + sms - 1) / sms) * bm * bn / e;
     };
+    // a large tile runs one CTA (8 warps) per SM; in a grid of less than two
+    // waves of them the cold operand reads are not hidden (measured: at 1024
+    // on a side the 64 x 64 tiles, two CTAs per SM, are 15-20% faster)
+    auto min_tiles = [&](Tile t) { return t == Tile::L || t == Tile::M ? 2 * sms : 0; };
     Tile best = Tile::S;
-    double c = cost(64, 64, effS);
-    if (allow_large && cost(128, 128, effL) < c) {
-        best = Tile::L;
-        c = cost(128, 128, effL);
+    double c = cost(64, 64, eff.S);
+    auto consider = [&](Tile t, int bm, int bn, double e) {
+        const double ct = cost(bm, bn, e);
+        if (ct < c && tiles(bm, bn) >= min_tiles(t)) {
+            best = t;
+            c = ct;
+        }
+    };
+    if constexpr (large_tiles_fit<P>()) {
+        consider(Tile::L, 128, 128, eff.L);
+        consider(Tile::M, 128, 64, eff.M);
     }
-    if (cost(32, 32, effXS) < c) best = Tile::XS;
+    consider(Tile::XS, 32, 32, eff.XS);
     return best;
 }
 
 template <class P>
 cudaError_t run_simt(const typename P::GA *A, int64_t lda, const typename P::GB *B, int64_t ldb,
                      typename P::GC *C, int64_t ldc, int64_t M, int64_t N, int64_t K,
-                     const typename P::Params &prm, cudaStream_t s, bool allow_large = true,
-                     int splits = 1) {
+                     const typename P::Params &prm, cudaStream_t s, int splits = 1) {
     // k-slice depth: as deep as the 48 KB of static shared memory allows, so
     // the register prefetch of the next slice covers the global-load latency
     constexpr bool narrow = sizeof(typename P::SA) <= 4 && sizeof(typename P::SB) <= 4;
-    switch (choose_tile<P>(M, N, allow_large)) {
-        case Tile::L:
+    const Tile tile = choose_tile<P>(M, N);
+    if constexpr (large_tiles_fit<P>()) {
+        if (tile == Tile::L)
             return simt_gemm_launch<P, 128, 128, narrow ? 16 : 8, 8, 8>(A, lda, B, ldb, C, ldc, M, N, K,
                                                                        prm, s, splits);
+        if (tile == Tile::M)
+            return simt_gemm_launch<P, 128, 64, narrow ? 16 : 8, 8, 4>(A, lda, B, ldb, C, ldc, M, N, K,
+                                                                      prm, s, splits);
+    }
+    switch (tile) {
         case Tile::XS:
             return simt_gemm_launch<P, 32, 32, 16, 2, 2>(A, lda, B, ldb, C, ldc, M, N, K, prm, s, splits);
         default:
@@ -512,14 +555,8 @@ cudaError_t run_dot(const void *CA, int64_t lda, const void *CB, int64_t ldb, ui
     using W = typename P<false>::GA;
     const W *a = static_cast<const W *>(CA);
     const W *b = static_cast<const W *>(CB);
-    if (blocked) {
-        // 64-bit accumulators plus the 32-bit block sums need the small tile
-        constexpr bool wide = sizeof(typename P<true>::Acc) > 4;
-        return run_simt<P<true>>(a, lda, b, ldb, C, ldc, m, n, kc, prm, s, !wide);
-    }
-    // 128-bit accumulators do not fit the 8 x 8 register tile
-    constexpr bool huge = sizeof(typename P<false>::Acc) > 8;
-    return run_simt<P<false>>(a, lda, b, ldb, C, ldc, m, n, kc, prm, s, !huge);
+    if (blocked) return run_simt<P<true>>(a, lda, b, ldb, C, ldc, m, n, kc, prm, s);
+    return run_simt<P<false>>(a, lda, b, ldb, C, ldc, m, n, kc, prm, s);
 }
 
 }  // namespace

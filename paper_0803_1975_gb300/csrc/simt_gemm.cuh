@@ -223,4 +223,33 @@ __device__ __forceinline__ uint32_t fastmod_u32(uint32_t a, uint64_t M, uint32_t
     return (uint32_t)__umul64hi(M * (uint64_t)a, (uint64_t)p);
 }
 
+// acc += a b for 64-bit a, b and a 128-bit accumulator held as four 32-bit
+// limbs c0..c3: the four limb products a_i b_j, each added at limb i + j with
+// its carries (low halves by mad.lo, high halves by madc.hi, carries rippled
+// up).  Ten 32-bit multiply-adds and adds, slightly fewer issue slots than
+// the 64 x 64 -> 128-bit multiply followed by a 128-bit add.
+__device__ __forceinline__ void mad_u64_u128(unsigned __int128 &acc, uint64_t a, uint64_t b) {
+    uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
+    asm("{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, c2, c3;\n\t"
+        "mov.b64 {a0, a1}, %2;\n\t"
+        "mov.b64 {b0, b1}, %3;\n\t"
+        "mov.b64 {c0, c1}, %0;\n\t"
+        "mov.b64 {c2, c3}, %1;\n\t"
+        "mad.lo.cc.u32 c0, a0, b0, c0;\n\t"
+        "madc.hi.cc.u32 c1, a0, b0, c1;\n\t"
+        "madc.lo.cc.u32 c2, a1, b1, c2;\n\t"
+        "madc.hi.u32 c3, a1, b1, c3;\n\t"
+        "mad.lo.cc.u32 c1, a0, b1, c1;\n\t"
+        "madc.hi.cc.u32 c2, a0, b1, c2;\n\t"
+        "addc.u32 c3, c3, 0;\n\t"
+        "mad.lo.cc.u32 c1, a1, b0, c1;\n\t"
+        "madc.hi.cc.u32 c2, a1, b0, c2;\n\t"
+        "addc.u32 c3, c3, 0;\n\t"
+        "mov.b64 %0, {c0, c1};\n\t"
+        "mov.b64 %1, {c2, c3};\n\t}"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+    acc = ((unsigned __int128)hi << 64) | lo;
+}
+
 }  // namespace gfp
