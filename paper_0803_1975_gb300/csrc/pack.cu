@@ -9,13 +9,12 @@
 //   ROWS    : W[i][v] = sum_j X[i][v(d+1)+j] Q^j       (rows, forward)
 // Entries past the edge count as zero.
 //
-// These kernels move bytes.  Row layouts stage about 4 KB of a row's
-// residues in shared memory per block: the residues move as aligned 32-bit
-// words (an aligned word that holds a byte of the row lies in the same page,
-// so it cannot fault; the bytes past the row in it are not used), the words
-// as consecutive lanes on consecutive words.  Column layouts give a thread
-// four adjacent columns, read or written as one 32-bit word of residues and
-// stored as one 16-byte store of words.
+// These kernels move bytes.  Row layouts stage a chunk of up to 8 KB of a
+// row's residues in shared memory per block, moved as aligned 16-byte blocks,
+// and give a thread four consecutive words (vector loads and stores of words).
+// Column layouts give a thread four adjacent columns, read or written as one
+// 32-bit word of residues and stored as one 16-byte store of words.
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 
@@ -58,42 +57,113 @@ __device__ __forceinline__ void store_words(W *p, const W (&v)[V], int n) {
         if (e < n) p[e] = v[e];
 }
 
-constexpr int STAGE_BYTES = 4096;          // residues staged per block and row
-
-__device__ __forceinline__ int words_per_block(int dp1) {
-    const int w = STAGE_BYTES / dp1;
-    return w < 1024 ? w : 1024;
+// Load V consecutive words at p: one vector load when p is 16-byte aligned
+// and all V are inside the row, else one by one (zero past the row).
+template <class W>
+__device__ __forceinline__ void load_words(const W *p, W (&v)[V], int n) {
+    if (n == V && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if constexpr (sizeof(W) == 8) {
+            const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+            const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2 *>(p) + 1);
+            const unsigned long long u[V] = {x.x, x.y, y.x, y.y};
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] = __builtin_bit_cast(W, u[e]);
+        } else {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+            const uint32_t u[V] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] = __builtin_bit_cast(W, u[e]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = e < n ? __ldg(p + e) : W(0);
 }
 
-// Rows, reversed (REV) or forward: a block packs words w0 .. w0 + wpb - 1 of
+// Row layouts.  A block handles a chunk of up to ROW_WORDS consecutive words
+// of a row (at most ROW_STAGE residues, staged in shared memory), V words per
+// thread, and loops over rows; packing fetches the next row's residues while
+// it builds the current row's words (the same for unpacking was measured
+// slower: its sixteen words per thread stay in registers across the writes).  The residues move as aligned 16-byte blocks
+// (an aligned block that holds a byte of the row lies in the same page, so
+// reading it cannot fault; on the write side only the blocks that lie inside
+// the chunk are written whole, the two ragged ends byte by byte); up to
+// ROW_LPT such loads per thread are issued back to back so that about 8 KB per
+// block is in flight.
+constexpr int ROW_THREADS = 256;
+constexpr int ROW_STAGE = 8192;                                  // residues per chunk
+constexpr int ROW_WORDS = 4096;                                  // words per chunk
+constexpr int ROW_GROUPS = ROW_WORDS / (V * ROW_THREADS);        // V-word groups per thread
+constexpr int ROW_LPT = (ROW_STAGE / 16 + 2 + ROW_THREADS - 1) / ROW_THREADS;
+
+// Words per chunk: the row's wc words in as few chunks as the stage allows,
+// of equal length (a multiple of V) so that no block gets a sliver.
+inline int row_chunk_words(int64_t wc, int dp1) {
+    int64_t most = ROW_STAGE / dp1;
+    most = most < ROW_WORDS ? most : ROW_WORDS;
+    most &= ~(int64_t)(V - 1);
+    if (most < V) most = V;
+    const int64_t chunks = (wc + most - 1) / most;
+    int64_t w = chunks > 0 ? (wc + chunks - 1) / chunks : V;
+    w = (w + V - 1) & ~(int64_t)(V - 1);
+    return (int)(w < most ? w : most);
+}
+
+// Rows, reversed (REV) or forward: a block packs words w0 .. w0 + nw - 1 of
 // its rows from the residues staged in shared memory.
 template <class W, bool REV>
-__global__ void __launch_bounds__(256) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx, int64_t rows,
-                                                        int64_t cols, int dp1, int t, W *__restrict__ out,
-                                                        int64_t ldw, int64_t wc) {
-    __shared__ uint32_t sbuf[STAGE_BYTES / 4 + 2];
-    const int wpb = words_per_block(dp1);
-    const int64_t w0 = (int64_t)blockIdx.x * wpb;
-    const int nw = wc - w0 < wpb ? (int)(wc - w0) : wpb;
+__global__ void __launch_bounds__(ROW_THREADS, 4) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx,
+                                                                int64_t rows, int64_t cols, int dp1, int t,
+                                                                W *__restrict__ out, int64_t ldw, int64_t wc,
+                                                                int cw) {
+    __shared__ uint4 sbuf[ROW_STAGE / 16 + 2];
+    const int64_t w0 = (int64_t)blockIdx.x * cw;
+    const int nw = wc - w0 < cw ? (int)(wc - w0) : cw;
+    const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
+    // the aligned 16-byte blocks covering row i's chunk, into registers
+    uint4 r[ROW_LPT];
+    auto fetch = [&](int64_t i) {
+        const uint8_t *row = X + i * ldx;
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(row + b0) & ~(uintptr_t)15;
+        const int nq = (int)((reinterpret_cast<uintptr_t>(row + b1) + 15 - a0) / 16);
+#pragma unroll
+        for (int e = 0; e < ROW_LPT; ++e) {
+            const int q = threadIdx.x + e * ROW_THREADS;
+            if (q < nq) r[e] = __ldg(reinterpret_cast<const uint4 *>(a0) + q);
+        }
+    };
+    if (blockIdx.y < rows) fetch(blockIdx.y);
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
         const uint8_t *row = X + i * ldx;
-        const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
-        const uintptr_t a0 = reinterpret_cast<uintptr_t>(row + b0) & ~(uintptr_t)3;
-        const uintptr_t a1 = (reinterpret_cast<uintptr_t>(row + b1) + 3) & ~(uintptr_t)3;
-        const int nq = (int)((a1 - a0) / 4);
-        for (int q = threadIdx.x; q < nq; q += blockDim.x)
-            sbuf[q] = __ldg(reinterpret_cast<const uint32_t *>(a0) + q);
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(row + b0), a0 = lo & ~(uintptr_t)15;
+        const int nq = (int)((reinterpret_cast<uintptr_t>(row + b1) + 15 - a0) / 16);
+#pragma unroll
+        for (int e = 0; e < ROW_LPT; ++e) {
+            const int q = threadIdx.x + e * ROW_THREADS;
+            if (q < nq) sbuf[q] = r[e];
+        }
         __syncthreads();
-        const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbuf) + (reinterpret_cast<uintptr_t>(row + b0) - a0);
-        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-            const int64_t rem = cols - (w0 + w) * dp1;
-            const int n = rem < dp1 ? (int)rem : dp1;
-            uint64_t acc = 0;
-            for (int j = 0; j < n; ++j) {
-                const int s = REV ? dp1 - 1 - j : j;
-                acc += (uint64_t)sb[w * dp1 + j] << (t * s);
+        // the next row's blocks are in flight while this row's words are built
+        if (i + gridDim.y < rows) fetch(i + gridDim.y);
+        const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbuf) + (lo - a0);
+#pragma unroll
+        for (int g = 0; g < ROW_GROUPS; ++g) {
+            const int w = (threadIdx.x + g * ROW_THREADS) * V;
+            if (w >= nw) break;
+            W v[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                // residues of word w0 + w + e inside the row (none past the last word)
+                const int64_t rem = cols - (w0 + w + e) * dp1;
+                const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
+                uint64_t acc = 0;
+                for (int j = 0; j < n; ++j) {
+                    const int sh = REV ? dp1 - 1 - j : j;
+                    acc += (uint64_t)sb[(w + e) * dp1 + j] << (t * sh);
+                }
+                v[e] = to_word<W>(acc);
             }
-            out[i * ldw + w0 + w] = to_word<W>(acc);
+            store_words<W>(out + i * ldw + w0 + w, v, nw - w < V ? nw - w : V);
         }
         __syncthreads();
     }
@@ -132,39 +202,56 @@ __global__ void pack_cols_kernel(const uint8_t *__restrict__ X, int64_t ldx, int
 }
 
 template <class W, bool REV>
-__global__ void __launch_bounds__(256) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw, int64_t rows,
-                                                          int64_t cols, int dp1, int t, uint8_t *__restrict__ X,
-                                                          int64_t ldx, int64_t wc) {
-    __shared__ uint32_t sbuf[STAGE_BYTES / 4 + 2];
-    const int wpb = words_per_block(dp1);
-    const int64_t w0 = (int64_t)blockIdx.x * wpb;
-    const int nw = wc - w0 < wpb ? (int)(wc - w0) : wpb;
+__global__ void __launch_bounds__(ROW_THREADS, 3) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw,
+                                                                  int64_t rows, int64_t cols, int dp1, int t,
+                                                                  uint8_t *__restrict__ X, int64_t ldx, int64_t wc,
+                                                                  int cw) {
+    __shared__ uint4 sbuf[ROW_STAGE / 16 + 2];
+    const int64_t w0 = (int64_t)blockIdx.x * cw;
+    const int nw = wc - w0 < cw ? (int)(wc - w0) : cw;
+    const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
     const uint64_t mask = (1ull << t) - 1;
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
         uint8_t *row = X + i * ldx;
-        const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
         const uintptr_t lo = reinterpret_cast<uintptr_t>(row + b0), hi = reinterpret_cast<uintptr_t>(row + b1);
-        const uintptr_t a0 = lo & ~(uintptr_t)3;
+        const uintptr_t a0 = lo & ~(uintptr_t)15;
         uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf) + (lo - a0);
-        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-            const uint64_t v = from_word<W>(__ldg(Win + i * ldw + w0 + w));
-            const int64_t rem = cols - (w0 + w) * dp1;
-            const int n = rem < dp1 ? (int)rem : dp1;
-            for (int j = 0; j < n; ++j) {
-                const int s = REV ? dp1 - 1 - j : j;
-                sb[w * dp1 + j] = (uint8_t)((v >> (t * s)) & mask);
+        // all of this thread's words first (their loads in flight together)
+        W v[ROW_GROUPS][V];
+#pragma unroll
+        for (int g = 0; g < ROW_GROUPS; ++g) {
+            const int w = (threadIdx.x + g * ROW_THREADS) * V;
+            if (w < nw) load_words<W>(Win + i * ldw + w0 + w, v[g], nw - w < V ? nw - w : V);
+        }
+#pragma unroll
+        for (int g = 0; g < ROW_GROUPS; ++g) {
+            const int w = (threadIdx.x + g * ROW_THREADS) * V;
+            if (w >= nw) break;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int64_t rem = cols - (w0 + w + e) * dp1;
+                const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
+                const uint64_t x = from_word<W>(v[g][e]);
+                for (int j = 0; j < n; ++j) {
+                    const int sh = REV ? dp1 - 1 - j : j;
+                    sb[(w + e) * dp1 + j] = (uint8_t)((x >> (t * sh)) & mask);
+                }
             }
         }
         __syncthreads();
-        // aligned 32-bit words inside [lo, hi) whole, the two ragged ends by bytes
-        const int nq = (int)((((hi + 3) & ~(uintptr_t)3) - a0) / 4);
-        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-            const uintptr_t a = a0 + 4 * (uintptr_t)q;
-            if (a >= lo && a + 4 <= hi) {
-                *reinterpret_cast<uint32_t *>(a) = sbuf[q];
+        // aligned 16-byte blocks inside [lo, hi) whole, the two ragged ends by bytes
+        const int nq = (int)((((hi + 15) & ~(uintptr_t)15) - a0) / 16);
+#pragma unroll
+        for (int e = 0; e < ROW_LPT; ++e) {
+            const int q = threadIdx.x + e * ROW_THREADS;
+            if (q >= nq) break;
+            const uintptr_t a = a0 + 16 * (uintptr_t)q;
+            if (a >= lo && a + 16 <= hi) {
+                *reinterpret_cast<uint4 *>(a) = sbuf[q];
             } else {
-                for (int e = 0; e < 4; ++e)
-                    if (a + e >= lo && a + e < hi) *reinterpret_cast<uint8_t *>(a + e) = (uint8_t)(sbuf[q] >> (8 * e));
+                const uint8_t *src = reinterpret_cast<const uint8_t *>(&sbuf[q]);
+                for (int c = 0; c < 16; ++c)
+                    if (a + c >= lo && a + c < hi) *reinterpret_cast<uint8_t *>(a + c) = src[c];
             }
         }
         __syncthreads();
@@ -245,15 +332,38 @@ __global__ void unpack_block_kernel(const W *__restrict__ Win, int64_t ldw, int6
 
 constexpr int kThreads = 256;
 
-// blocks of the staged row kernels: one per STAGE_BYTES of residues of a row
-dim3 rows_grid(int64_t wc, int64_t rows, int dp1) {
-    const int64_t wpb = STAGE_BYTES / dp1 < 1024 ? STAGE_BYTES / dp1 : 1024;
-    const int64_t gx = (wc + wpb - 1) / wpb;
-    // about 16 blocks per SM in all, each looping over rows
-    int64_t gy = ((int64_t)num_sms() * 16 + gx - 1) / gx;
+// Blocks of a staged row kernel: one per chunk of a row (row_chunk_words
+// words) times as many row slices as the SMs hold resident blocks (the
+// occupancy of the kernel, asked once) -- a single wave -- each block looping
+// over rows.
+template <class K>
+dim3 rows_grid(K kernel, std::atomic<int> &per_sm, int64_t wc, int64_t rows, int dp1) {
+    int r = per_sm.load(std::memory_order_relaxed);
+    if (r < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, ROW_THREADS, 0) != cudaSuccess || r < 1) {
+            (void)cudaGetLastError();
+            r = 1;
+        }
+        per_sm.store(r, std::memory_order_relaxed);
+    }
+    const int64_t cw = row_chunk_words(wc, dp1);
+    const int64_t gx = (wc + cw - 1) / cw;
+    int64_t gy = (int64_t)num_sms() * r / gx;   // one wave: every block resident
     if (gy > rows) gy = rows;
     if (gy > 65535) gy = 65535;
     return dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1));
+}
+
+template <class W, bool REV>
+dim3 pack_rows_grid(int64_t wc, int64_t rows, int dp1) {
+    static std::atomic<int> per_sm{0};
+    return rows_grid(pack_rows_kernel<W, REV>, per_sm, wc, rows, dp1);
+}
+
+template <class W, bool REV>
+dim3 unpack_rows_grid(int64_t wc, int64_t rows, int dp1) {
+    static std::atomic<int> per_sm{0};
+    return rows_grid(unpack_rows_kernel<W, REV>, per_sm, wc, rows, dp1);
 }
 
 dim3 grid_for(int64_t inner, int64_t outer, int per_thread = 1) {
@@ -275,11 +385,12 @@ cudaError_t pack_t(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, in
                                                                       out, ldw, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        const dim3 g = rows_grid(wc, rows, dp1);
         if (lay == GFP_LAYOUT_ROWS_REV)
-            pack_rows_kernel<W, true><<<g, kThreads, 0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc);
+            pack_rows_kernel<W, true><<<pack_rows_grid<W, true>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
+                X, ldx, rows, cols, dp1, t, out, ldw, wc, row_chunk_words(wc, dp1));
         else
-            pack_rows_kernel<W, false><<<g, kThreads, 0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc);
+            pack_rows_kernel<W, false><<<pack_rows_grid<W, false>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
+                X, ldx, rows, cols, dp1, t, out, ldw, wc, row_chunk_words(wc, dp1));
     }
     return cudaGetLastError();
 }
@@ -294,11 +405,12 @@ cudaError_t unpack_t(int64_t rows, int64_t cols, const void *Wp, int64_t ldw, in
                                                                         X, ldx, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        const dim3 g = rows_grid(wc, rows, dp1);
         if (lay == GFP_LAYOUT_ROWS_REV)
-            unpack_rows_kernel<W, true><<<g, kThreads, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc);
+            unpack_rows_kernel<W, true><<<unpack_rows_grid<W, true>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
+                in, ldw, rows, cols, dp1, t, X, ldx, wc, row_chunk_words(wc, dp1));
         else
-            unpack_rows_kernel<W, false><<<g, kThreads, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc);
+            unpack_rows_kernel<W, false><<<unpack_rows_grid<W, false>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
+                in, ldw, rows, cols, dp1, t, X, ldx, wc, row_chunk_words(wc, dp1));
     }
     return cudaGetLastError();
 }

@@ -21,7 +21,9 @@ def _built():
 
 # --------------------------------------------------------------------------- pack
 PACK_CASES = [(3, 1024, 1024, 3, 13), (3, 37, 129, 3, 13), (5, 130, 67, 2, 19), (251, 9, 300, 1, 30),
-              (2, 64, 64, 7, 8), (7, 1, 1, 0, 6)]
+              (2, 64, 64, 7, 8), (7, 1, 1, 0, 6),
+              # rows of several staged chunks (a chunk holds up to 8192 residues)
+              (3, 5, 20001, 3, 13), (251, 3, 9001, 0, 30)]
 
 
 @pytest.mark.parametrize("word", ["u64", "u32w", "f64"])
@@ -61,6 +63,34 @@ def test_pack_strided_views():
     ref = oracle.pack_rows_rev(np.ascontiguousarray(X[:, 3:90]), 3, 2 ** 13)
     got = words_np(W, "u64")
     assert (got[:, :22] == ref).all() and (got[:, 22:] == 0).all()
+
+
+@pytest.mark.parametrize("word", ["u64", "u32w", "f64"])
+@pytest.mark.parametrize("layout", ["rows_rev", "rows"])
+def test_pack_unpack_long_unaligned_rows(word, layout):
+    """Rows of several chunks starting at odd byte addresses (a view with an
+    odd leading dimension and column offset), unpacked into a strided view of a
+    sentinel-filled buffer: only the view's bytes change."""
+    p, t = 3, 13
+    d = 2 if word == "u32w" else 3      # the largest 32-bit word holds three digits of 2^13
+    Q = 2 ** t
+    g = inputs.rng(82, len(word) + len(layout))
+    big = inputs.residues(g, p, 7, 30011)
+    X = np.ascontiguousarray(big[:, 5:29999])
+    Xd = dev(big)[:, 5:29999]
+    W = gfp.gfp_pack(p, Xd, d, Q, layout, word)
+    ref = {"rows_rev": oracle.pack_rows_rev, "rows": oracle.pack_rows}[layout](X, d, Q, dtype=np.uint64)
+    got = words_np(W, word)
+    dt = np_words_dtype(word)
+    assert (got.astype(np.uint64) == ref).all() if dt is not np.float64 else (got == ref.astype(np.float64)).all()
+    sentinel = torch.full((9, 30017), 0xA5, dtype=torch.uint8, device="cuda")
+    view = sentinel[1:8, 3:3 + X.shape[1]]
+    gfp.gfp_unpack(p, W, X.shape[0], X.shape[1], d, Q, layout, word, out=view)
+    out = host(sentinel)
+    assert (out[1:8, 3:3 + X.shape[1]] == X).all()
+    mask = np.ones(out.shape, bool)
+    mask[1:8, 3:3 + X.shape[1]] = False
+    assert (out[mask] == 0xA5).all()
 
 
 # ------------------------------------------------------------------ plain / TC
