@@ -37,47 +37,50 @@ __device__ __forceinline__ uint64_t from_word(W w) {
 
 constexpr int V = 4;   // words per thread
 
-// Store V consecutive words at p: one vector store when p is 16-byte
-// aligned and all V are inside the row, else one by one.
-template <class W>
-__device__ __forceinline__ void store_words(W *p, const W (&v)[V], int n) {
-    if (n == V && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-        if constexpr (sizeof(W) == 8) {
-            reinterpret_cast<ulonglong2 *>(p)[0] = make_ulonglong2(*reinterpret_cast<const unsigned long long *>(&v[0]),
-                                                                 *reinterpret_cast<const unsigned long long *>(&v[1]));
-            reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(*reinterpret_cast<const unsigned long long *>(&v[2]),
-                                                                 *reinterpret_cast<const unsigned long long *>(&v[3]));
-        } else {
-            *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+// Store N consecutive words at p: one vector store when N = 4, p is 16-byte
+// aligned and all N are inside the row, else one by one.
+template <class W, int N = V>
+__device__ __forceinline__ void store_words(W *p, const W (&v)[N], int n) {
+    if constexpr (N == 4) {
+        if (n == N && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            if constexpr (sizeof(W) == 8) {
+                const unsigned long long *u = reinterpret_cast<const unsigned long long *>(v);
+                reinterpret_cast<ulonglong2 *>(p)[0] = make_ulonglong2(u[0], u[1]);
+                reinterpret_cast<ulonglong2 *>(p)[1] = make_ulonglong2(u[2], u[3]);
+            } else {
+                *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+            }
+            return;
         }
-        return;
     }
 #pragma unroll
-    for (int e = 0; e < V; ++e)
+    for (int e = 0; e < N; ++e)
         if (e < n) p[e] = v[e];
 }
 
-// Load V consecutive words at p: one vector load when p is 16-byte aligned
-// and all V are inside the row, else one by one (zero past the row).
-template <class W>
-__device__ __forceinline__ void load_words(const W *p, W (&v)[V], int n) {
-    if (n == V && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-        if constexpr (sizeof(W) == 8) {
-            const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(p));
-            const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2 *>(p) + 1);
-            const unsigned long long u[V] = {x.x, x.y, y.x, y.y};
+// Load N consecutive words at p: one vector load when N = 4, p is 16-byte
+// aligned and all N are inside the row, else one by one (zero past the row).
+template <class W, int N = V>
+__device__ __forceinline__ void load_words(const W *p, W (&v)[N], int n) {
+    if constexpr (N == 4) {
+        if (n == N && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+            if constexpr (sizeof(W) == 8) {
+                const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+                const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2 *>(p) + 1);
+                const unsigned long long u[4] = {x.x, x.y, y.x, y.y};
 #pragma unroll
-            for (int e = 0; e < V; ++e) v[e] = __builtin_bit_cast(W, u[e]);
-        } else {
-            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
-            const uint32_t u[V] = {x.x, x.y, x.z, x.w};
+                for (int e = 0; e < 4; ++e) v[e] = __builtin_bit_cast(W, u[e]);
+            } else {
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+                const uint32_t u[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-            for (int e = 0; e < V; ++e) v[e] = __builtin_bit_cast(W, u[e]);
+                for (int e = 0; e < 4; ++e) v[e] = __builtin_bit_cast(W, u[e]);
+            }
+            return;
         }
-        return;
     }
 #pragma unroll
-    for (int e = 0; e < V; ++e) v[e] = e < n ? __ldg(p + e) : W(0);
+    for (int e = 0; e < N; ++e) v[e] = e < n ? __ldg(p + e) : W(0);
 }
 
 // Row layouts.  A block handles a chunk of up to ROW_WORDS consecutive words
@@ -93,26 +96,37 @@ __device__ __forceinline__ void load_words(const W *p, W (&v)[V], int n) {
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_STAGE = 8192;                                  // residues per chunk
 constexpr int ROW_WORDS = 4096;                                  // words per chunk
-constexpr int ROW_GROUPS = ROW_WORDS / (V * ROW_THREADS);        // V-word groups per thread
 constexpr int ROW_LPT = (ROW_STAGE / 16 + 2 + ROW_THREADS - 1) / ROW_THREADS;
 
+// words per chunk with vw words per thread: short rows (one word per thread)
+// need at most one word in each of V passes over the block
+__host__ __device__ constexpr int row_words(int vw) { return vw == 1 ? V * ROW_THREADS : ROW_WORDS; }
+// resident blocks the register budget aims at: all the rows of a small
+// matrix in flight at once (one word per thread), one wave of long rows
+__host__ __device__ constexpr int row_min_blocks(int vw, bool pack) { return vw == 1 ? 8 : pack ? 4 : 3; }
+
 // Words per chunk: the row's wc words in as few chunks as the stage allows,
-// of equal length (a multiple of V) so that no block gets a sliver.
-inline int row_chunk_words(int64_t wc, int dp1) {
+// of equal length (a multiple of vw) so that no block gets a sliver.
+inline int row_chunk_words(int64_t wc, int dp1, int vw) {
     int64_t most = ROW_STAGE / dp1;
-    most = most < ROW_WORDS ? most : ROW_WORDS;
-    most &= ~(int64_t)(V - 1);
-    if (most < V) most = V;
+    most = most < row_words(vw) ? most : row_words(vw);
+    most -= most % vw;
+    if (most < vw) most = vw;
     const int64_t chunks = (wc + most - 1) / most;
-    int64_t w = chunks > 0 ? (wc + chunks - 1) / chunks : V;
-    w = (w + V - 1) & ~(int64_t)(V - 1);
+    int64_t w = chunks > 0 ? (wc + chunks - 1) / chunks : vw;
+    w = (w + vw - 1) / vw * vw;
     return (int)(w < most ? w : most);
 }
 
+// Words per thread: V (vector loads and stores of words) for rows of at least
+// V * ROW_THREADS words, one for shorter rows, whose chunk would otherwise
+// leave most of the block idle.
+inline int row_words_per_thread(int64_t wc) { return wc >= (int64_t)V * ROW_THREADS ? V : 1; }
+
 // Rows, reversed (REV) or forward: a block packs words w0 .. w0 + nw - 1 of
 // its rows from the residues staged in shared memory.
-template <class W, bool REV>
-__global__ void __launch_bounds__(ROW_THREADS, 4) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx,
+template <class W, bool REV, int VW>
+__global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, true)) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx,
                                                                 int64_t rows, int64_t cols, int dp1, int t,
                                                                 W *__restrict__ out, int64_t ldw, int64_t wc,
                                                                 int cw) {
@@ -132,27 +146,30 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) pack_rows_kernel(const uint8_t
             if (q < nq) r[e] = __ldg(reinterpret_cast<const uint4 *>(a0) + q);
         }
     };
-    if (blockIdx.y < rows) fetch(blockIdx.y);
+    // long rows (VW > 1): the next row's blocks are in flight while this row's
+    // words are built; short rows have a block each and fetch as they go
+    constexpr bool ahead = VW > 1;
+    if (ahead && blockIdx.y < rows) fetch(blockIdx.y);
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
         const uint8_t *row = X + i * ldx;
         const uintptr_t lo = reinterpret_cast<uintptr_t>(row + b0), a0 = lo & ~(uintptr_t)15;
         const int nq = (int)((reinterpret_cast<uintptr_t>(row + b1) + 15 - a0) / 16);
+        if (!ahead) fetch(i);
 #pragma unroll
         for (int e = 0; e < ROW_LPT; ++e) {
             const int q = threadIdx.x + e * ROW_THREADS;
             if (q < nq) sbuf[q] = r[e];
         }
         __syncthreads();
-        // the next row's blocks are in flight while this row's words are built
-        if (i + gridDim.y < rows) fetch(i + gridDim.y);
+        if (ahead && i + gridDim.y < rows) fetch(i + gridDim.y);
         const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbuf) + (lo - a0);
 #pragma unroll
-        for (int g = 0; g < ROW_GROUPS; ++g) {
-            const int w = (threadIdx.x + g * ROW_THREADS) * V;
+        for (int g = 0; g < row_words(VW) / (VW * ROW_THREADS); ++g) {
+            const int w = (threadIdx.x + g * ROW_THREADS) * VW;
             if (w >= nw) break;
-            W v[V];
+            W v[VW];
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
+            for (int e = 0; e < VW; ++e) {
                 // residues of word w0 + w + e inside the row (none past the last word)
                 const int64_t rem = cols - (w0 + w + e) * dp1;
                 const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) pack_rows_kernel(const uint8_t
                 }
                 v[e] = to_word<W>(acc);
             }
-            store_words<W>(out + i * ldw + w0 + w, v, nw - w < V ? nw - w : V);
+            store_words<W, VW>(out + i * ldw + w0 + w, v, nw - w < VW ? nw - w : VW);
         }
         __syncthreads();
     }
@@ -201,8 +218,8 @@ __global__ void pack_cols_kernel(const uint8_t *__restrict__ X, int64_t ldx, int
     }
 }
 
-template <class W, bool REV>
-__global__ void __launch_bounds__(ROW_THREADS, 3) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw,
+template <class W, bool REV, int VW>
+__global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, false)) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw,
                                                                   int64_t rows, int64_t cols, int dp1, int t,
                                                                   uint8_t *__restrict__ X, int64_t ldx, int64_t wc,
                                                                   int cw) {
@@ -217,18 +234,19 @@ __global__ void __launch_bounds__(ROW_THREADS, 3) unpack_rows_kernel(const W *__
         const uintptr_t a0 = lo & ~(uintptr_t)15;
         uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf) + (lo - a0);
         // all of this thread's words first (their loads in flight together)
-        W v[ROW_GROUPS][V];
+        constexpr int G = row_words(VW) / (VW * ROW_THREADS);
+        W v[G][VW];
 #pragma unroll
-        for (int g = 0; g < ROW_GROUPS; ++g) {
-            const int w = (threadIdx.x + g * ROW_THREADS) * V;
-            if (w < nw) load_words<W>(Win + i * ldw + w0 + w, v[g], nw - w < V ? nw - w : V);
+        for (int g = 0; g < G; ++g) {
+            const int w = (threadIdx.x + g * ROW_THREADS) * VW;
+            if (w < nw) load_words<W, VW>(Win + i * ldw + w0 + w, v[g], nw - w < VW ? nw - w : VW);
         }
 #pragma unroll
-        for (int g = 0; g < ROW_GROUPS; ++g) {
-            const int w = (threadIdx.x + g * ROW_THREADS) * V;
+        for (int g = 0; g < G; ++g) {
+            const int w = (threadIdx.x + g * ROW_THREADS) * VW;
             if (w >= nw) break;
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
+            for (int e = 0; e < VW; ++e) {
                 const int64_t rem = cols - (w0 + w + e) * dp1;
                 const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
                 const uint64_t x = from_word<W>(v[g][e]);
@@ -337,7 +355,7 @@ constexpr int kThreads = 256;
 // occupancy of the kernel, asked once) -- a single wave -- each block looping
 // over rows.
 template <class K>
-dim3 rows_grid(K kernel, std::atomic<int> &per_sm, int64_t wc, int64_t rows, int dp1) {
+dim3 rows_grid(K kernel, std::atomic<int> &per_sm, int64_t wc, int64_t rows, int cw) {
     int r = per_sm.load(std::memory_order_relaxed);
     if (r < 1) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, ROW_THREADS, 0) != cudaSuccess || r < 1) {
@@ -346,7 +364,6 @@ dim3 rows_grid(K kernel, std::atomic<int> &per_sm, int64_t wc, int64_t rows, int
         }
         per_sm.store(r, std::memory_order_relaxed);
     }
-    const int64_t cw = row_chunk_words(wc, dp1);
     const int64_t gx = (wc + cw - 1) / cw;
     int64_t gy = (int64_t)num_sms() * r / gx;   // one wave: every block resident
     if (gy > rows) gy = rows;
@@ -354,16 +371,24 @@ dim3 rows_grid(K kernel, std::atomic<int> &per_sm, int64_t wc, int64_t rows, int
     return dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1));
 }
 
-template <class W, bool REV>
-dim3 pack_rows_grid(int64_t wc, int64_t rows, int dp1) {
+template <class W, bool REV, int VW>
+cudaError_t launch_pack_rows(const uint8_t *X, int64_t ldx, int64_t rows, int64_t cols, int dp1, int t, W *out,
+                             int64_t ldw, int64_t wc, cudaStream_t s) {
     static std::atomic<int> per_sm{0};
-    return rows_grid(pack_rows_kernel<W, REV>, per_sm, wc, rows, dp1);
+    const int cw = row_chunk_words(wc, dp1, VW);
+    pack_rows_kernel<W, REV, VW><<<rows_grid(pack_rows_kernel<W, REV, VW>, per_sm, wc, rows, cw), ROW_THREADS,
+                                   0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc, cw);
+    return cudaGetLastError();
 }
 
-template <class W, bool REV>
-dim3 unpack_rows_grid(int64_t wc, int64_t rows, int dp1) {
+template <class W, bool REV, int VW>
+cudaError_t launch_unpack_rows(const W *in, int64_t ldw, int64_t rows, int64_t cols, int dp1, int t, uint8_t *X,
+                               int64_t ldx, int64_t wc, cudaStream_t s) {
     static std::atomic<int> per_sm{0};
-    return rows_grid(unpack_rows_kernel<W, REV>, per_sm, wc, rows, dp1);
+    const int cw = row_chunk_words(wc, dp1, VW);
+    unpack_rows_kernel<W, REV, VW><<<rows_grid(unpack_rows_kernel<W, REV, VW>, per_sm, wc, rows, cw),
+                                     ROW_THREADS, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc, cw);
+    return cudaGetLastError();
 }
 
 dim3 grid_for(int64_t inner, int64_t outer, int per_thread = 1) {
@@ -385,12 +410,11 @@ cudaError_t pack_t(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, in
                                                                       out, ldw, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        if (lay == GFP_LAYOUT_ROWS_REV)
-            pack_rows_kernel<W, true><<<pack_rows_grid<W, true>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
-                X, ldx, rows, cols, dp1, t, out, ldw, wc, row_chunk_words(wc, dp1));
-        else
-            pack_rows_kernel<W, false><<<pack_rows_grid<W, false>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
-                X, ldx, rows, cols, dp1, t, out, ldw, wc, row_chunk_words(wc, dp1));
+        const bool rev = lay == GFP_LAYOUT_ROWS_REV, vec = row_words_per_thread(wc) == V;
+        if (rev) return vec ? launch_pack_rows<W, true, V>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s)
+                            : launch_pack_rows<W, true, 1>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        return vec ? launch_pack_rows<W, false, V>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s)
+                   : launch_pack_rows<W, false, 1>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
     }
     return cudaGetLastError();
 }
@@ -405,12 +429,11 @@ cudaError_t unpack_t(int64_t rows, int64_t cols, const void *Wp, int64_t ldw, in
                                                                         X, ldx, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        if (lay == GFP_LAYOUT_ROWS_REV)
-            unpack_rows_kernel<W, true><<<unpack_rows_grid<W, true>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
-                in, ldw, rows, cols, dp1, t, X, ldx, wc, row_chunk_words(wc, dp1));
-        else
-            unpack_rows_kernel<W, false><<<unpack_rows_grid<W, false>(wc, rows, dp1), ROW_THREADS, 0, s>>>(
-                in, ldw, rows, cols, dp1, t, X, ldx, wc, row_chunk_words(wc, dp1));
+        const bool rev = lay == GFP_LAYOUT_ROWS_REV, vec = row_words_per_thread(wc) == V;
+        if (rev) return vec ? launch_unpack_rows<W, true, V>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s)
+                            : launch_unpack_rows<W, true, 1>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        return vec ? launch_unpack_rows<W, false, V>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s)
+                   : launch_unpack_rows<W, false, 1>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
     }
     return cudaGetLastError();
 }
