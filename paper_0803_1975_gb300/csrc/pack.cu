@@ -105,17 +105,28 @@ __host__ __device__ constexpr int row_words(int vw) { return vw == 1 ? V * ROW_T
 // matrix in flight at once (one word per thread), one wave of long rows
 __host__ __device__ constexpr int row_min_blocks(int vw, bool pack) { return vw == 1 ? 8 : pack ? 4 : 3; }
 
-// Words per chunk: the row's wc words in as few chunks as the stage allows,
-// of equal length (a multiple of vw) so that no block gets a sliver.
+// Words per chunk: the row's wc words in equal chunks (a multiple of vw
+// words each, at most what the stage and row_words allow), the count chosen
+// to minimise chunks x passes of the block over a chunk -- a block waits at
+// its barrier for its busiest thread, so a chunk of 1.3 passes costs two.
 inline int row_chunk_words(int64_t wc, int dp1, int vw) {
     int64_t most = ROW_STAGE / dp1;
     most = most < row_words(vw) ? most : row_words(vw);
     most -= most % vw;
     if (most < vw) most = vw;
-    const int64_t chunks = (wc + most - 1) / most;
-    int64_t w = chunks > 0 ? (wc + chunks - 1) / chunks : vw;
-    w = (w + vw - 1) / vw * vw;
-    return (int)(w < most ? w : most);
+    const int64_t c0 = (wc + most - 1) / most, per_pass = (int64_t)vw * ROW_THREADS;
+    int64_t best_w = most, best_cost = -1;
+    for (int64_t c = c0 > 0 ? c0 : 1; c <= c0 + 8; ++c) {
+        int64_t w = (wc + c - 1) / c;
+        w = (w + vw - 1) / vw * vw;
+        if (w > most) continue;
+        const int64_t cost = c * ((w + per_pass - 1) / per_pass);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_w = w;
+        }
+    }
+    return (int)best_w;
 }
 
 // Words per thread: V (vector loads and stores of words) for rows of at least
@@ -173,10 +184,16 @@ __global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, true)) pack_ro
                 // residues of word w0 + w + e inside the row (none past the last word)
                 const int64_t rem = cols - (w0 + w + e) * dp1;
                 const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
+                // Horner in base Q = 2^t, highest power first (each residue < Q)
+                const uint8_t *src = sb + (w + e) * dp1;
                 uint64_t acc = 0;
-                for (int j = 0; j < n; ++j) {
-                    const int sh = REV ? dp1 - 1 - j : j;
-                    acc += (uint64_t)sb[(w + e) * dp1 + j] << (t * sh);
+                if (REV) {
+#pragma unroll 1
+                    for (int j = 0; j < n; ++j) acc = (acc << t) | src[j];
+                    if (n < dp1 && n > 0) acc <<= t * (dp1 - n);   // the missing residues are the low powers
+                } else {
+#pragma unroll 1
+                    for (int j = n - 1; j >= 0; --j) acc = (acc << t) | src[j];
                 }
                 v[e] = to_word<W>(acc);
             }
@@ -249,10 +266,16 @@ __global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, false)) unpack
             for (int e = 0; e < VW; ++e) {
                 const int64_t rem = cols - (w0 + w + e) * dp1;
                 const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
-                const uint64_t x = from_word<W>(v[g][e]);
-                for (int j = 0; j < n; ++j) {
-                    const int sh = REV ? dp1 - 1 - j : j;
-                    sb[(w + e) * dp1 + j] = (uint8_t)((x >> (t * sh)) & mask);
+                // digits peeled off the low end, lowest power first
+                uint64_t x = from_word<W>(v[g][e]);
+                uint8_t *dst = sb + (w + e) * dp1;
+                if (REV) {
+                    if (n < dp1 && n > 0) x >>= t * (dp1 - n);      // the missing residues' powers
+#pragma unroll 1
+                    for (int j = n - 1; j >= 0; --j, x >>= t) dst[j] = (uint8_t)(x & mask);
+                } else {
+#pragma unroll 1
+                    for (int j = 0; j < n; ++j, x >>= t) dst[j] = (uint8_t)(x & mask);
                 }
             }
         }
