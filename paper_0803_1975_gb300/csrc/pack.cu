@@ -212,20 +212,38 @@ __global__ void pack_cols_kernel(const uint8_t *__restrict__ X, int64_t ldx, int
     const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
     if (j0 >= cols) return;
     const int nj = cols - j0 < V ? (int)(cols - j0) : V;
+    // all four columns of every residue row in one aligned 32-bit load
+    const bool vec = nj == V && ((reinterpret_cast<uintptr_t>(X + j0) | (uintptr_t)ldx) & 3) == 0;
+    constexpr int MAXR = 8;   // residue rows per word held in registers (loads in flight together)
     for (int64_t w = blockIdx.y; w < wr; w += gridDim.y) {
         const int64_t rem = rows - w * dp1;
         const int n = rem < dp1 ? (int)rem : dp1;
+        const uint8_t *x0 = X + w * dp1 * ldx + j0;
+        // Horner in base Q = 2^t over the residue rows, highest power (row n-1) first
         uint64_t acc[V] = {0, 0, 0, 0};
-        for (int s = 0; s < n; ++s) {
-            const uint8_t *x = X + (w * dp1 + s) * ldx + j0;
-            if (nj == V && (reinterpret_cast<uintptr_t>(x) & 3) == 0) {
-                const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(x));
+        if (vec && n <= MAXR) {
+            uint32_t q[MAXR];
 #pragma unroll
-                for (int e = 0; e < V; ++e) acc[e] += (uint64_t)((q >> (8 * e)) & 0xffu) << (t * s);
-            } else {
+            for (int r = 0; r < MAXR; ++r)
+                if (r < n) q[r] = __ldg(reinterpret_cast<const uint32_t *>(x0 + r * ldx));
 #pragma unroll
-                for (int e = 0; e < V; ++e)
-                    if (e < nj) acc[e] += (uint64_t)__ldg(x + e) << (t * s);
+            for (int r = MAXR - 1; r >= 0; --r)
+                if (r < n) {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) acc[e] = (acc[e] << t) | ((q[r] >> (8 * e)) & 0xffu);
+                }
+        } else {
+            for (int r = n - 1; r >= 0; --r) {
+                const uint8_t *x = x0 + r * ldx;
+                if (vec) {
+                    const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(x));
+#pragma unroll
+                    for (int e = 0; e < V; ++e) acc[e] = (acc[e] << t) | ((q >> (8 * e)) & 0xffu);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (e < nj) acc[e] = (acc[e] << t) | __ldg(x + e);
+                }
             }
         }
         W v[V];
@@ -313,18 +331,21 @@ __global__ void unpack_cols_kernel(const W *__restrict__ Win, int64_t ldw, int64
         for (int e = 0; e < V; ++e) v[e] = e < nj ? from_word<W>(__ldg(Win + w * ldw + j0 + e)) : 0;
         const int64_t rem = rows - w * dp1;
         const int n = rem < dp1 ? (int)rem : dp1;
+        // digits peeled off the low end: residue row s holds the coefficient of Q^s
         for (int s = 0; s < n; ++s) {
             uint8_t *x = X + (w * dp1 + s) * ldx + j0;
             if (nj == V && (reinterpret_cast<uintptr_t>(x) & 3) == 0) {
                 uint32_t q = 0;
 #pragma unroll
-                for (int e = 0; e < V; ++e) q |= (uint32_t)((v[e] >> (t * s)) & mask) << (8 * e);
+                for (int e = 0; e < V; ++e) q |= (uint32_t)(v[e] & mask) << (8 * e);
                 *reinterpret_cast<uint32_t *>(x) = q;
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    if (e < nj) x[e] = (uint8_t)((v[e] >> (t * s)) & mask);
+                    if (e < nj) x[e] = (uint8_t)(v[e] & mask);
             }
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] >>= t;
         }
     }
 }

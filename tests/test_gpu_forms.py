@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_0803_1975_gb300 import gfp, inputs
 
-from helpers import (dev, ensure_built, freivalds, host, np_words_dtype, operands, oracle_product,
+from helpers import (THREADS, dev, ensure_built, freivalds, host, np_words_dtype, operands, oracle_product,
                      to_word_tensor, words_np)
 
 pytestmark = pytest.mark.gpu
@@ -91,6 +91,35 @@ def test_pack_unpack_long_unaligned_rows(word, layout):
     mask = np.ones(out.shape, bool)
     mask[1:8, 3:3 + X.shape[1]] = False
     assert (out[mask] == 0xA5).all()
+
+
+# Results spanning at least two waves of the 128 x 128 and 128 x 64 register tiles
+# of the CUDA-core kernels (the only shapes that use them), ragged in both
+# dimensions: at 4001 x 3999 the classical and dp4a products run on 128 x 128
+# tiles, the 32-bit word products (whole and k-blocked) on 128 x 64.
+@pytest.fixture(scope="module")
+def wide_case():
+    p, m, k, n = 3, 4001, 200, 3999
+    A, B = operands(9, 1, p, m, k, n)
+    return p, A, B, oracle.gemm(p, A, B, threads=THREADS)
+
+
+@pytest.mark.parametrize("form", ["plain", "dp4a", "dot_u32", "dot_u32_kb60", "dot_u32w", "dot_u64"])
+def test_large_register_tiles_ragged(wide_case, form):
+    p, A, B, ref = wide_case
+    m, k = A.shape
+    n = B.shape[1]
+    Ad, Bd = dev(A), dev(B)
+    if form in ("plain", "dp4a"):
+        C = gfp.gfp_gemm(p, Ad, Bd, form)
+    else:
+        word = form.split("_")[1]
+        kb = 60 if form.endswith("kb60") else 0
+        d, Q, kb = gfp.gfp_params(p, m, k, n, "dot", word, kb=kb)
+        CA = gfp.gfp_pack(p, Ad, d, Q, "rows_rev", word)
+        CB = gfp.gfp_pack(p, Bd, d, Q, "cols", word)
+        C = gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", word, CA, CB, kb=kb)
+    assert (host(C) == ref).all()
 
 
 # ------------------------------------------------------------------ plain / TC
