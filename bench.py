@@ -170,8 +170,11 @@ class Step:
         self.ws8 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_mma_s8"))
         self.dom = None   # (start, end) events around the dominant kernel
 
-    def run(self, dom_events=None):
+    def run(self, dom_events=None, done=None):
+        """One step.  `done(name)`, if given, is called as soon as the launch
+        that completes output `name` has been issued (to start its copy)."""
         g = self.gfp
+        done = done or (lambda name: None)
         # parameters (host)
         d64, Q64, _ = g.gfp_params(P, M, K, N, "dot", "u64")
         df, Qf, _ = g.gfp_params(P, M, K, N, "dot", "f64")
@@ -180,6 +183,7 @@ class Step:
         g.gfp_pack(P, self.A, d64, Q64, "rows_rev", "u64", out=self.CA64)
         g.gfp_pack(P, self.B, d64, Q64, "cols", "u64", out=self.CB64)
         g.gfp_gemm_compressed(P, M, K, N, d64, Q64, "dot", "u64", self.CA64, self.CB64, out=self.outs["dot_u64"])
+        done("dot_u64")
         # dot form, FP64 words: 3 launches (the product is the step's dominant kernel)
         g.gfp_pack(P, self.A, df, Qf, "rows_rev", "f64", out=self.CAf)
         g.gfp_pack(P, self.B, df, Qf, "cols", "f64", out=self.CBf)
@@ -188,17 +192,23 @@ class Step:
         g.gfp_gemm_compressed(P, M, K, N, df, Qf, "dot", "f64", self.CAf, self.CBf, out=self.outs["dot_f64"])
         if dom_events is not None:
             dom_events[1].record()
+        done("dot_f64")
         # right-compressed form with REDQ: 3 launches
         g.gfp_pack(P, self.B, dm, Qm, "rows", "u64", out=self.CBr)
         g.gfp_gemm_compressed(P, M, K, N, dm, Qm, "mixed", "u64", self.A, self.CBr, out=self.CC)
         g.gfp_unpack(P, self.CC, M, N, dm, Qm, "rows", "u64", out=self.outs["mixed_u64"])
+        done("mixed_u64")
         # classical product: 1 launch
         g.gfp_gemm(P, self.A, self.B, "plain", out=self.outs["plain"])
+        done("plain")
         # tensor-core forms: 3 + 2 + 3 launches (operand conversion, product; the
         # fp8 form converts only B for p < 16)
         g.gfp_gemm(P, self.A, self.B, "tc_f16", out=self.outs["tc_f16"], workspace=self.ws16)
+        done("tc_f16")
         g.gfp_gemm(P, self.A, self.B, "tc_f8", out=self.outs["tc_f8"], workspace=self.wsf8)
+        done("tc_f8")
         g.gfp_gemm(P, self.A, self.B, "tc_mma_s8", out=self.outs["tc_mma_s8"], workspace=self.ws8)
+        done("tc_mma_s8")
 
     @property
     def products(self):
@@ -473,10 +483,21 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * step.products * FLOP / ms_per_step / 1e9
 
-    # end to end: pinned host inputs -> device -> all forms -> results to pinned host memory
+    # end to end: pinned host inputs -> device -> all forms -> results to pinned host memory;
+    # each result is copied on a second stream as soon as its product is done
+    # (ordered by an event), overlapping the copies with the later products
     A_pin = torch.from_numpy(A_h).pin_memory()
     B_pin = torch.from_numpy(B_h).pin_memory()
     outs_pin = {k: torch.empty((M, N), dtype=torch.uint8).pin_memory() for k in step.outs}
+    copy_stream = torch.cuda.Stream()
+
+    def copy_out(name):
+        ev = torch.cuda.Event()
+        ev.record()
+        copy_stream.wait_event(ev)
+        with torch.cuda.stream(copy_stream):
+            outs_pin[name].copy_(step.outs[name], non_blocking=True)
+
     barrier()
     e2e_ms = []
     for _ in range(args.steps):
@@ -486,9 +507,8 @@ def main():
         e0.record()
         A.copy_(A_pin, non_blocking=True)
         B.copy_(B_pin, non_blocking=True)
-        step.run()
-        for k_, C in step.outs.items():
-            outs_pin[k_].copy_(C, non_blocking=True)
+        step.run(done=copy_out)
+        torch.cuda.current_stream().wait_stream(copy_stream)
         e1.record()
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
