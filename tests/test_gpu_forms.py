@@ -23,7 +23,9 @@ def _built():
 PACK_CASES = [(3, 1024, 1024, 3, 13), (3, 37, 129, 3, 13), (5, 130, 67, 2, 19), (251, 9, 300, 1, 30),
               (2, 64, 64, 7, 8), (7, 1, 1, 0, 6),
               # rows of several staged chunks (a chunk holds up to 8192 residues)
-              (3, 5, 20001, 3, 13), (251, 3, 9001, 0, 30), (5, 3, 10001, 1, 19), (3, 4, 12002, 2, 13)]
+              (3, 5, 20001, 3, 13), (251, 3, 9001, 0, 30), (5, 3, 10001, 1, 19), (3, 4, 12002, 2, 13),
+              # long rows of more than four residues per word (the run-time digit count)
+              (2, 3, 9000, 7, 8), (3, 2, 10007, 5, 10)]
 
 
 @pytest.mark.parametrize("word", ["u64", "u32w", "f64"])
