@@ -59,6 +59,11 @@ struct Dp4aP : PlainP {
         uint32_t v = 0;
         if (i < M) {
             const int64_t k0 = 4 * g;
+            // a whole group of a row on a 4-byte boundary: the row's bytes are
+            // the group's residues in order, one 32-bit load
+            const GA *group = A + i * lda + k0;
+            if (k0 + 4 <= prm.k && (reinterpret_cast<uintptr_t>(group) & 3) == 0)
+                return __ldg(reinterpret_cast<const uint32_t *>(group));
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (k0 + q < prm.k) v |= (uint32_t)A[i * lda + k0 + q] << (8 * q);
