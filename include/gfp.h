@@ -114,7 +114,10 @@ typedef enum gfp_layout {
  *                        per term, 32-bit sums, one reduction per entry.
  *                        Needs k (p-1)^2 < 2^32.
  *  GFP_ALGO_DP4A       : classical product on the 4-way byte dot-product
- *                        instruction (same bound).
+ *                        instruction (same bound); B is first transposed into
+ *                        the workspace (roundup(n, 64) x roundup(k, 64) bytes
+ *                        after 256) so that both operands are read as one
+ *                        32-bit word per 4 residues.
  *  GFP_ALGO_TC_MMA_S8  : centred residues c in [-(p-1)/2, (p-1)/2] as int8 on
  *                        the warp-level int8 tensor-core MMA with int32
  *                        accumulation; reduced mod p after every k-block kb

@@ -118,6 +118,7 @@ GFP_API gfp_status gfp_gemm_workspace_size(uint32_t p, int64_t m, int64_t k, int
     gfp_status st = resolve_algo(p, m, k, n, algo, &a);
     if (st != GFP_OK) return st;
     *bytes = 0;
+    if (a == GFP_ALGO_DP4A) *bytes = dp4a_workspace_bytes(k, n);
     if (a == GFP_ALGO_TC_MMA_S8) *bytes = tc_mma_workspace(m, k, n);
     if (a == GFP_ALGO_TC_F16) *bytes = tc_f16_workspace(m, k, n);
     if (a == GFP_ALGO_TC_F8) *bytes = tc_f8_workspace(m, k, n);
@@ -144,7 +145,10 @@ GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n, const u
     if (a == GFP_ALGO_PLAIN || a == GFP_ALGO_DP4A) {
         const unsigned __int128 tot = (unsigned __int128)k * (p - 1) * (p - 1);
         if (tot >= ((unsigned __int128)1 << 32)) return GFP_EBOUND;
-        return launch_plain(p, m, k, n, A, lda, B, ldb, C, ldc, a == GFP_ALGO_DP4A, s);
+        if (a == GFP_ALGO_DP4A &&
+            (!workspace || ws_bytes < dp4a_workspace_bytes(k, n) || ((uintptr_t)workspace & 255)))
+            return GFP_EWORKSPACE;
+        return launch_plain(p, m, k, n, A, lda, B, ldb, C, ldc, a == GFP_ALGO_DP4A, workspace, ws_bytes, s);
     }
     const size_t need = a == GFP_ALGO_TC_MMA_S8 ? tc_mma_workspace(m, k, n)
                         : a == GFP_ALGO_TC_F8   ? tc_f8_workspace(m, k, n)

@@ -27,6 +27,7 @@ struct PlainP {
     using GC = uint8_t;
     static constexpr bool kBlocked = false;
     static constexpr bool kAtomic = false;
+    static constexpr bool kBKMajor = false;
     static constexpr bool kSlowPipe = false;
     struct Params {
         uint64_t M;
@@ -50,8 +51,12 @@ struct PlainP {
 };
 
 // Classical product on the byte dot-product instruction: each shared-memory
-// element holds 4 consecutive k-entries of a row of A or a column of B.
+// element holds 4 consecutive k-entries of a row of A or a column of B.  B
+// comes transposed (row j of the stored matrix is column j of B, zero past k,
+// rows 4-byte aligned), so that both operands are read as one 32-bit word per
+// group of 4 residues.
 struct Dp4aP : PlainP {
+    static constexpr bool kBKMajor = true;
     // The loop runs over groups g < ceil(k/4); prm.k (the true k) guards
     // the entries of the last group.
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t g, int64_t M, int64_t,
@@ -70,16 +75,11 @@ struct Dp4aP : PlainP {
         }
         return v;
     }
-    __device__ static SB ldB(const GB *B, int64_t ldb, int64_t g, int64_t j, int64_t, int64_t N,
-                             const Params &prm) {
-        uint32_t v = 0;
-        if (j < N) {
-            const int64_t k0 = 4 * g;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (k0 + q < prm.k) v |= (uint32_t)B[(k0 + q) * ldb + j] << (8 * q);
-        }
-        return v;
+    // Bt: n rows of ldb bytes (ldb a multiple of 4, zero from k on); groups
+    // g < K = ceil(k/4) lie inside the row
+    __device__ static SB ldB(const GB *Bt, int64_t ldb, int64_t g, int64_t j, int64_t K, int64_t N,
+                             const Params &) {
+        return (g < K && j < N) ? __ldg(reinterpret_cast<const uint32_t *>(Bt + j * ldb + 4 * g)) : 0u;
     }
     __device__ static void mac(Acc &acc, SA a, SB b) { acc = __dp4a(a, b, acc); }
 };
@@ -117,6 +117,7 @@ struct DotBase {
     using Params = DotParams;
     static constexpr bool kBlocked = BLK;
     static constexpr bool kAtomic = false;
+    static constexpr bool kBKMajor = false;
     static constexpr bool kSlowPipe = std::is_floating_point<W>::value;   // FP64 words: DFMA-bound
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                                     const Params &) {
@@ -284,6 +285,7 @@ struct MixedU64T {
     using Params = MixedParams;
     static constexpr bool kBlocked = false;
     static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kBKMajor = false;
     static constexpr bool kSlowPipe = std::is_floating_point<GB>::value;
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                                     const Params &) {
@@ -318,6 +320,7 @@ struct MixedF64T {
     using Params = MixedParams;
     static constexpr bool kBlocked = false;
     static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kBKMajor = false;
     static constexpr bool kSlowPipe = std::is_floating_point<GB>::value;
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                                     const Params &) {
@@ -374,6 +377,7 @@ struct LeftT {
     using Params = MixedParams;
     static constexpr bool kBlocked = false;
     static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kBKMajor = false;
     static constexpr bool kSlowPipe = FP;
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                              const Params &) {
@@ -411,6 +415,7 @@ struct FullT {
     using Params = MixedParams;
     static constexpr bool kBlocked = false;
     static constexpr bool kAtomic = PARTIAL;
+    static constexpr bool kBKMajor = false;
     static constexpr bool kSlowPipe = FP;
     __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t k, int64_t M, int64_t K,
                              const Params &) {
@@ -592,13 +597,23 @@ cudaError_t run_dot(const void *CA, int64_t lda, const void *CB, int64_t ldb, ui
 
 }  // namespace
 
+size_t dp4a_workspace_bytes(int64_t k, int64_t n) {
+    return 256 + (size_t)((n + 63) / 64 * 64) * (size_t)((k + 63) / 64 * 64);
+}
+
 gfp_status launch_plain(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
-                        const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, bool dp4a,
-                        cudaStream_t s) {
+                        const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, bool dp4a, void *ws,
+                        size_t ws_bytes, cudaStream_t s) {
     PlainP::Params prm{fastmod_magic(p), p, 0, k};
     cudaError_t e;
     if (dp4a) {
-        e = run_simt<Dp4aP>(A, lda, B, ldb, C, ldc, m, n, (k + 3) / 4, prm, s);
+        // B transposed into the workspace (k-major rows of kp bytes, zero past k)
+        const int64_t kp = (k + 63) / 64 * 64, np = (n + 63) / 64 * 64;
+        if (!ws || ws_bytes < dp4a_workspace_bytes(k, n)) return GFP_EWORKSPACE;
+        uint8_t *Bt = static_cast<uint8_t *>(ws) + 256;
+        const gfp_status st = launch_transpose_bytes(B, ldb, k, n, Bt, kp, np, s);
+        if (st != GFP_OK) return st;
+        e = run_simt<Dp4aP>(A, lda, Bt, kp, C, ldc, m, n, (k + 3) / 4, prm, s);
     } else {
         e = run_simt<PlainP>(A, lda, B, ldb, C, ldc, m, n, k, prm, s);
     }

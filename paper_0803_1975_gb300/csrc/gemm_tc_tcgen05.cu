@@ -864,6 +864,18 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
 
 }  // namespace
 
+// out[j][l] = B[l][j] for l < k, j < n, zero elsewhere in np x kp (kp, np
+// multiples of 64; out 16-byte aligned): the raw byte transpose of the fp8
+// operands, also the k-major B of the dp4a classical product.
+gfp_status launch_transpose_bytes(const uint8_t *B, int64_t ldb, int64_t k, int64_t n, uint8_t *out, int64_t kp,
+                                  int64_t np, cudaStream_t s) {
+    if (kp % 64 || np % 64 || kp / 64 > 2147483647 || np / 64 > 65535) return GFP_EINVAL;
+    if (kp == 0 || np == 0) return GFP_OK;
+    to_op_transpose_kernel<true, true><<<dim3((unsigned)(kp / 64), (unsigned)(np / 64)), 256, 0, s>>>(
+        B, ldb, k, n, out, kp, np, 0u, 0u);
+    return check_launch();
+}
+
 // largest multiple of 128 with kb h^2 + p < 2^24 (one fp32-exact k-block)
 int64_t tc_kblock_f32(uint32_t p) {
     const int64_t h = p == 2 ? 1 : (p - 1) / 2;

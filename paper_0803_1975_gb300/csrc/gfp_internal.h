@@ -74,9 +74,13 @@ gfp_status launch_pack(uint32_t p, int64_t rows, int64_t cols, const uint8_t *X,
 gfp_status launch_unpack(int64_t rows, int64_t cols, const void *W, int64_t ldw, int d, int t,
                          gfp_layout lay, gfp_word word, uint8_t *X, int64_t ldx, cudaStream_t s);
 
+// dp4a needs the workspace dp4a_workspace_bytes(k, n) for B transposed
 gfp_status launch_plain(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
                         int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
-                        bool dp4a, cudaStream_t s);
+                        bool dp4a, void *ws, size_t ws_bytes, cudaStream_t s);
+size_t dp4a_workspace_bytes(int64_t k, int64_t n);
+gfp_status launch_transpose_bytes(const uint8_t *B, int64_t ldb, int64_t k, int64_t n, uint8_t *out, int64_t kp,
+                                  int64_t np, cudaStream_t s);
 gfp_status launch_dot(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t, gfp_word word,
                       const void *CA, int64_t lda, const void *CB, int64_t ldb, uint8_t *C,
                       int64_t ldc, int64_t kbw, cudaStream_t s);

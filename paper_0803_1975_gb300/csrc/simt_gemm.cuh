@@ -20,6 +20,9 @@
 //            accumulator restarts from zero after each block.
 //   kAtomic  when true the result is added atomically to C (split-k slices
 //            of a linear accumulator; the caller zeroes C and finishes it).
+//   kBKMajor when true B is stored k-contiguous (element (k, j) of the
+//            product's B lies in row j of the stored matrix): its tile is
+//            read along k like A's, consecutive threads on consecutive k.
 #pragma once
 
 #include <cstdint>
@@ -78,7 +81,8 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
     using SA = typename P::SA;
     using SB = typename P::SB;
     using Acc = typename P::Acc;
-    constexpr int PADA = 16 / sizeof(SA), PADB = 0;   // keeps rows 16-byte aligned
+    // pads keep rows 16-byte aligned and spread the transposing stores over banks
+    constexpr int PADA = 16 / sizeof(SA), PADB = P::kBKMajor ? 16 / sizeof(SB) : 0;
     __shared__ __align__(16) SA As[2][BK][BM + PADA];
     __shared__ __align__(16) SB Bs[2][BK][BN + PADB];
 
@@ -106,7 +110,7 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
 #pragma unroll
         for (int e = 0; e < LB; ++e) {
             const int idx = tid + e * NT;
-            const int r = idx / BN, c = idx % BN;
+            const int r = P::kBKMajor ? idx % BK : idx / BN, c = P::kBKMajor ? idx / BK : idx % BN;
             const int64_t gk = k0 + r, gj = n0 + c;
             rb[e] = P::ldB(B, ldb, gk, gj, kz1, N, prm);
         }
@@ -120,7 +124,8 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
 #pragma unroll
         for (int e = 0; e < LB; ++e) {
             const int idx = tid + e * NT;
-            Bs[buf][idx / BN][idx % BN] = rb[e];
+            if constexpr (P::kBKMajor) Bs[buf][idx % BK][idx / BK] = rb[e];
+            else Bs[buf][idx / BN][idx % BN] = rb[e];
         }
     };
 
