@@ -4,8 +4,8 @@ time (CUDA events, L2 flushed between repetitions) and effective 2mnk/s.
     python -m paper_0803_1975_gb300.run_case --form tc_f16 --p 3 --size 8192 --reps 3
     python -m paper_0803_1975_gb300.run_case --form dot --word u32 --kb 60 --size 1024
 
-Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8 (gfp_gemm); dot, mixed
-(gfp_gemm_compressed, after packing); winograd (the 64-bit dot form with
+Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8 (gfp_gemm); dot, mixed, left
+(gfp_gemm_compressed, after packing); full (gfp_gemm_full, 64-bit words); winograd (the 64-bit dot form with
 --levels of Strassen-Winograd on the words); batched (the 4096-problem adjacency
 workload, one prepared launch); pack_rows_rev, pack_cols, pack_rows,
 unpack_rows (the conversions of A, reported in GB/s of bytes moved).  Useful
@@ -98,6 +98,19 @@ def main():
         CB = gfp.gfp_pack(p, B, d, Q, "rows", a.word)
         C = torch.empty((m, -(-n // (d + 1))), dtype=gfp.WORD_DTYPE[a.word], device="cuda")
         fn = lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "mixed", a.word, A, CB, out=C)
+    elif a.form == "left":
+        # left compression (Table 2): A packed along m (column words) times uncompressed B
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "left", "u64")
+        CA = gfp.gfp_pack(p, A, d, Q, "cols", "u64")
+        C = torch.empty((-(-m // (d + 1)), n), dtype=torch.int64, device="cuda")
+        fn = lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "left", "u64", CA, B, out=C)
+    elif a.form == "full":
+        # full compression (Section 4): A along m in base Q, B along n in base Q^(dq+1)
+        dq, dth, Q = gfp.gfp_params_full(p, m, k, n, "u64")
+        CA = gfp.gfp_pack(p, A, dq, Q, "cols", "u64")
+        CB = gfp.gfp_pack(p, B, dth, Q ** (dq + 1), "rows", "u64")
+        C = torch.empty((-(-m // (dq + 1)), -(-n // (dth + 1))), dtype=torch.int64, device="cuda")
+        fn = lambda: gfp.gfp_gemm_full(p, m, k, n, dq, dth, Q, "u64", CA, CB, out=C)
     else:
         raise SystemExit("unknown form %s" % a.form)
     for _ in range(a.warmup):
