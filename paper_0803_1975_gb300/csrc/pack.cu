@@ -87,12 +87,12 @@ __device__ __forceinline__ void load_words(const W *p, W (&v)[N], int n) {
 // of a row (at most ROW_STAGE residues, staged in shared memory), V words per
 // thread, and loops over rows; packing fetches the next row's residues while
 // it builds the current row's words (the same for unpacking was measured
-// slower: its sixteen words per thread stay in registers across the writes).  The residues move as aligned 16-byte blocks
-// (an aligned block that holds a byte of the row lies in the same page, so
-// reading it cannot fault; on the write side only the blocks that lie inside
-// the chunk are written whole, the two ragged ends byte by byte); up to
-// ROW_LPT such loads per thread are issued back to back so that about 8 KB per
-// block is in flight.
+// slower: its sixteen words per thread stay in registers across the writes).
+// The residues move as aligned 16-byte blocks (an aligned block that holds a
+// byte of the row lies in the same page, so reading it cannot fault; on the
+// write side only the blocks that lie inside the chunk are written whole, the
+// two ragged ends byte by byte); up to ROW_LPT such loads per thread are
+// issued back to back so that about 8 KB per block is in flight.
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_STAGE = 8192;                                  // residues per chunk
 constexpr int ROW_WORDS = 4096;                                  // words per chunk
@@ -137,10 +137,9 @@ inline int row_words_per_thread(int64_t wc) { return wc >= (int64_t)V * ROW_THRE
 // Rows, reversed (REV) or forward: a block packs words w0 .. w0 + nw - 1 of
 // its rows from the residues staged in shared memory.
 template <class W, bool REV, int VW, int DP1>
-__global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, true)) pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx,
-                                                                int64_t rows, int64_t cols, int dp1_arg, int t,
-                                                                W *__restrict__ out, int64_t ldw, int64_t wc,
-                                                                int cw) {
+__global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, true))
+pack_rows_kernel(const uint8_t *__restrict__ X, int64_t ldx, int64_t rows, int64_t cols, int dp1_arg, int t,
+                 W *__restrict__ out, int64_t ldw, int64_t wc, int cw) {
     __shared__ uint4 sbuf[ROW_STAGE / 16 + 2];
     const int dp1 = DP1 > 0 ? DP1 : dp1_arg;      // residues per word (a constant when DP1 > 0)
     const int64_t whole = cols / dp1;            // words of dp1 residues; word `whole` holds the tail
@@ -260,10 +259,9 @@ __global__ void pack_cols_kernel(const uint8_t *__restrict__ X, int64_t ldx, int
 }
 
 template <class W, bool REV, int VW, int DP1>
-__global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, false)) unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw,
-                                                                  int64_t rows, int64_t cols, int dp1_arg, int t,
-                                                                  uint8_t *__restrict__ X, int64_t ldx, int64_t wc,
-                                                                  int cw) {
+__global__ void __launch_bounds__(ROW_THREADS, row_min_blocks(VW, false))
+unpack_rows_kernel(const W *__restrict__ Win, int64_t ldw, int64_t rows, int64_t cols, int dp1_arg, int t,
+                   uint8_t *__restrict__ X, int64_t ldx, int64_t wc, int cw) {
     __shared__ uint4 sbuf[ROW_STAGE / 16 + 2];
     const int dp1 = DP1 > 0 ? DP1 : dp1_arg;
     const int64_t whole = cols / dp1;
@@ -444,7 +442,8 @@ cudaError_t launch_pack_rows(const uint8_t *X, int64_t ldx, int64_t rows, int64_
 template <class W, bool REV>
 cudaError_t pack_rows_dispatch(const uint8_t *X, int64_t ldx, int64_t rows, int64_t cols, int dp1, int t, W *out,
                                int64_t ldw, int64_t wc, cudaStream_t s) {
-    if (row_words_per_thread(wc) != V) return launch_pack_rows<W, REV, 1, 0>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+    if (row_words_per_thread(wc) != V)
+        return launch_pack_rows<W, REV, 1, 0>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
     switch (dp1) {
         case 1: return launch_pack_rows<W, REV, V, 1>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
         case 2: return launch_pack_rows<W, REV, V, 2>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
@@ -467,7 +466,8 @@ cudaError_t launch_unpack_rows(const W *in, int64_t ldw, int64_t rows, int64_t c
 template <class W, bool REV>
 cudaError_t unpack_rows_dispatch(const W *in, int64_t ldw, int64_t rows, int64_t cols, int dp1, int t, uint8_t *X,
                                  int64_t ldx, int64_t wc, cudaStream_t s) {
-    if (row_words_per_thread(wc) != V) return launch_unpack_rows<W, REV, 1, 0>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+    if (row_words_per_thread(wc) != V)
+        return launch_unpack_rows<W, REV, 1, 0>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
     switch (dp1) {
         case 1: return launch_unpack_rows<W, REV, V, 1>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
         case 2: return launch_unpack_rows<W, REV, V, 2>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
@@ -496,7 +496,8 @@ cudaError_t pack_t(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, in
                                                                       out, ldw, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        if (lay == GFP_LAYOUT_ROWS_REV) return pack_rows_dispatch<W, true>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
+        if (lay == GFP_LAYOUT_ROWS_REV)
+            return pack_rows_dispatch<W, true>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
         return pack_rows_dispatch<W, false>(X, ldx, rows, cols, dp1, t, out, ldw, wc, s);
     }
     return cudaGetLastError();
@@ -512,7 +513,8 @@ cudaError_t unpack_t(int64_t rows, int64_t cols, const void *Wp, int64_t ldw, in
                                                                         X, ldx, wr);
     } else {
         const int64_t wc = (cols + dp1 - 1) / dp1;
-        if (lay == GFP_LAYOUT_ROWS_REV) return unpack_rows_dispatch<W, true>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
+        if (lay == GFP_LAYOUT_ROWS_REV)
+            return unpack_rows_dispatch<W, true>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
         return unpack_rows_dispatch<W, false>(in, ldw, rows, cols, dp1, t, X, ldx, wc, s);
     }
     return cudaGetLastError();
