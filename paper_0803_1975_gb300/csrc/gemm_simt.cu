@@ -54,26 +54,29 @@ struct PlainP {
 // element holds 4 consecutive k-entries of a row of A or a column of B.  B
 // comes transposed (row j of the stored matrix is column j of B, zero past k,
 // rows 4-byte aligned), so that both operands are read as one 32-bit word per
-// group of 4 residues.
-struct Dp4aP : PlainP {
+// group of 4 residues.  ALIGNED_A: A and its leading dimension are 4-byte
+// aligned, so every group of A is one aligned word (the bytes of a last
+// partial group past k meet B's zeros; an aligned word holding a byte of the
+// row lies in the same page, so reading it cannot fault).
+template <bool ALIGNED_A>
+struct Dp4aT : PlainP {
     static constexpr bool kBKMajor = true;
     // The loop runs over groups g < ceil(k/4); prm.k (the true k) guards
     // the entries of the last group.
-    __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t g, int64_t M, int64_t,
+    __device__ static SA ldA(const GA *A, int64_t lda, int64_t i, int64_t g, int64_t M, int64_t K,
                              const Params &prm) {
-        uint32_t v = 0;
-        if (i < M) {
-            const int64_t k0 = 4 * g;
-            // a whole group of a row on a 4-byte boundary: the row's bytes are
-            // the group's residues in order, one 32-bit load
-            const GA *group = A + i * lda + k0;
-            if (k0 + 4 <= prm.k && (reinterpret_cast<uintptr_t>(group) & 3) == 0)
-                return __ldg(reinterpret_cast<const uint32_t *>(group));
+        if constexpr (ALIGNED_A) {
+            return (i < M && g < K) ? __ldg(reinterpret_cast<const uint32_t *>(A + i * lda + 4 * g)) : 0u;
+        } else {
+            uint32_t v = 0;
+            if (i < M) {
+                const int64_t k0 = 4 * g;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (k0 + q < prm.k) v |= (uint32_t)A[i * lda + k0 + q] << (8 * q);
+                for (int q = 0; q < 4; ++q)
+                    if (k0 + q < prm.k) v |= (uint32_t)A[i * lda + k0 + q] << (8 * q);
+            }
+            return v;
         }
-        return v;
     }
     // Bt: n rows of ldb bytes (ldb a multiple of 4, zero from k on); groups
     // g < K = ceil(k/4) lie inside the row
@@ -445,6 +448,7 @@ struct FullT {
 // efficiency of the tile), with the efficiencies measured on GB300 (products
 // of 4096 and 16384 on a side) per class of policy:
 //   byte operands, 32-bit accumulator (classical): L 1, M 0.95, S 0.86, XS 0.46
+//   byte groups on dp4a, B k-major:                L 0.97, M 1, S 0.66, XS 0.46
 //   32-bit words, 32-bit accumulator:              L 0.9, M 1, S 0.83, XS 0.5
 //   32-bit words, 64-bit accumulator:              L 0.95, M 1, S 0.97, XS 0.83
 //   64-bit words:                                  L 0.85, M 0.9, S 1, XS 0.9
@@ -470,6 +474,7 @@ constexpr TileEff tile_eff() {
     if constexpr (P::kSlowPipe) return {1.0, 1.0, 1.0, 1.0};
     else if constexpr (std::is_same<typename P::Acc, unsigned __int128>::value) return {0.5, 0.88, 0.93, 1.0};
     else if constexpr (sizeof(typename P::SA) == 8 || sizeof(typename P::SB) == 8) return {0.85, 0.9, 1.0, 0.9};
+    else if constexpr (P::kBKMajor) return {0.97, 1.0, 0.66, 0.46};
     else if constexpr (sizeof(typename P::GA) == 1 && sizeof(typename P::GB) == 1) return {1.0, 0.95, 0.86, 0.46};
     else if constexpr (sizeof(typename P::Acc) == 8) return {0.95, 1.0, 0.97, 0.83};
     else return {0.9, 1.0, 0.83, 0.5};
@@ -613,7 +618,10 @@ gfp_status launch_plain(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8
         uint8_t *Bt = static_cast<uint8_t *>(ws) + 256;
         const gfp_status st = launch_transpose_bytes(B, ldb, k, n, Bt, kp, np, s);
         if (st != GFP_OK) return st;
-        e = run_simt<Dp4aP>(A, lda, Bt, kp, C, ldc, m, n, (k + 3) / 4, prm, s);
+        if (((reinterpret_cast<uintptr_t>(A) | (uintptr_t)lda) & 3) == 0)
+            e = run_simt<Dp4aT<true>>(A, lda, Bt, kp, C, ldc, m, n, (k + 3) / 4, prm, s);
+        else
+            e = run_simt<Dp4aT<false>>(A, lda, Bt, kp, C, ldc, m, n, (k + 3) / 4, prm, s);
     } else {
         e = run_simt<PlainP>(A, lda, B, ldb, C, ldc, m, n, k, prm, s);
     }

@@ -95,6 +95,18 @@ def test_pack_unpack_long_unaligned_rows(word, layout):
     assert (out[mask] == 0xA5).all()
 
 
+def test_dp4a_aligned_rows_with_a_partial_last_group():
+    """dp4a reads A four residues at a time when its rows are 4-byte aligned: with
+    k = 1025 inside rows of 1028 bytes, the last group holds three bytes past k
+    (real residues of the wider matrix), which must not reach C."""
+    p, m, k, n = 7, 300, 1025, 260
+    g = inputs.rng(83, 0)
+    wide = inputs.residues(g, p, m, 1028)
+    B = inputs.residues(g, p, k, n)
+    C = gfp.gfp_gemm(p, dev(wide)[:, :k], dev(B), "dp4a")
+    assert (host(C) == oracle.gemm(p, np.ascontiguousarray(wide[:, :k]), B, threads=THREADS)).all()
+
+
 # Results spanning at least two waves of the 128 x 128 and 128 x 64 register tiles
 # of the CUDA-core kernels (the only shapes that use them), ragged in both
 # dimensions: at 4001 x 3999 the classical and dp4a products run on 128 x 128
