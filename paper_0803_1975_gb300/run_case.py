@@ -38,6 +38,9 @@ def main():
     ap.add_argument("--primes", default="", help="batched: comma-separated primes replacing the workload's "
                                                  "p in {3, 5, 7} (cycled; 0/1 matrices are residues for any p)")
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--graph", type=int, default=0,
+                    help="capture this many calls in one CUDA graph and report the time per call of its "
+                         "replay (launch overhead removed; the operands stay in L2 between the calls)")
     a = ap.parse_args()
     m = a.m or a.size
     k = a.k or a.size
@@ -115,6 +118,16 @@ def main():
         raise SystemExit("unknown form %s" % a.form)
     for _ in range(a.warmup):
         fn()
+    calls = 1
+    if a.graph > 0:
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(a.graph):
+                fn()
+        calls = a.graph
+        fn = graph.replay
+        fn()
     ts = []
     for _ in range(a.reps):
         flush.zero_()
@@ -125,14 +138,14 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
-    ms = float(np.median(ts))
+    ms = float(np.median(ts)) / calls
     if a.form.startswith(("pack", "unpack")):
         print(json.dumps({"form": a.form, "word": a.word, "p": p, "rows": m, "cols": k, "ms": round(ms, 5),
                           "bytes": pack_bytes, "GB_per_s": round(pack_bytes / ms / 1e6, 1)}))
         return
     flops = flops_total if a.form == "batched" else 2.0 * m * n * k
     print(json.dumps({"form": a.form, "word": a.word, "algo": a.algo, "levels": a.levels, "p": p, "m": m, "k": k, "n": n, "ms": round(ms, 5),
-                      "T_2mnk_per_s": round(flops / ms / 1e9, 3)}))
+                      "T_2mnk_per_s": round(flops / ms / 1e9, 3), "graph_calls": a.graph}))
 
 
 if __name__ == "__main__":
