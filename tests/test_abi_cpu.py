@@ -140,6 +140,17 @@ def test_workspace_sizes(L):
     assert gfp.gfp_gemm_workspace_size(3, 256, 256, 256, "plain") == 0
     ws = gfp.gfp_gemm_workspace_size(3, 100, 70, 200, "tc_mma_s8")
     assert ws >= (128 + 256) * 128
+    # dp4a: B transposed into k-major rows, both dimensions padded to 64, after 256 bytes
+    assert gfp.gfp_gemm_workspace_size(3, 100, 70, 200, "dp4a") == 256 + 256 * 128
+    assert gfp.gfp_gemm_workspace_size(3, 5, 64, 64, "dp4a") == 256 + 64 * 64
+
+
+def test_dp4a_requires_its_workspace(L):
+    # rejected on the host before any launch (the pointers are never read)
+    A = ctypes.c_void_p(256)
+    need = gfp.gfp_gemm_workspace_size(3, 8, 8, 8, "dp4a")
+    assert L.gfp_gemm(3, 8, 8, 8, A, 8, A, 8, A, 8, gfp.ALGOS["dp4a"], None, 0, None) == 7   # GFP_EWORKSPACE
+    assert L.gfp_gemm(3, 8, 8, 8, A, 8, A, 8, A, 8, gfp.ALGOS["dp4a"], A, need - 1, None) == 7
 
 
 def test_left_chooser_matches_oracle(L):
