@@ -63,16 +63,21 @@ __global__ void centre_transpose_kernel(const uint8_t *__restrict__ B, int64_t l
                                         int64_t n, int8_t *__restrict__ Bt, int64_t kp, int64_t np,
                                         uint32_t p, uint32_t h) {
     __shared__ int8_t tile[64][64 + 4];
-    const int64_t l0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
+    const int64_t l0 = (int64_t)blockIdx.x * 64;
     const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;   // 256 threads: 64 x 4
-    for (int r = ty; r < 64; r += 4) {
-        const int64_t l = l0 + r, j = j0 + tx;
-        tile[r][tx] = (l < k && j < n) ? centre(B[l * ldb + j], p, h) : (int8_t)0;
-    }
-    __syncthreads();
-    for (int r = ty; r < 64; r += 4) {
-        const int64_t j = j0 + r, l = l0 + tx;
-        if (j < np && l < kp) Bt[j * kp + l] = tile[tx][r];
+    // column tiles of 64 in a grid-stride loop (np / 64 may exceed the grid's y limit)
+    for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
+        const int64_t j0 = jt * 64;
+        for (int r = ty; r < 64; r += 4) {
+            const int64_t l = l0 + r, j = j0 + tx;
+            tile[r][tx] = (l < k && j < n) ? centre(B[l * ldb + j], p, h) : (int8_t)0;
+        }
+        __syncthreads();
+        for (int r = ty; r < 64; r += 4) {
+            const int64_t j = j0 + r, l = l0 + tx;
+            if (j < np && l < kp) Bt[j * kp + l] = tile[tx][r];
+        }
+        __syncthreads();
     }
 }
 
@@ -254,7 +259,7 @@ gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint
     {
         dim3 grid((unsigned)((kp / 4 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
         centre_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, Ac, kp, mp, p, h);
-        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64));
+        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
         centre_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, Bt, kp, np, p, h);
     }
     MmaArgs g;

@@ -701,29 +701,34 @@ __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ld
                                        uint32_t p, uint32_t h) {
     constexpr int ES = FP8 ? 1 : 2;
     __shared__ int8_t tile[64][64 + 4];
-    const int64_t l0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 64;
+    const int64_t l0 = (int64_t)blockIdx.x * 64;
     const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
-    {
-        const int64_t l = l0 + r;
-        uint32_t v[16];
-        load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
+    // column tiles of 64 in a grid-stride loop (np / 64 may exceed the grid's y limit)
+    for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
+        const int64_t j0 = jt * 64;
+        {
+            const int64_t l = l0 + r;
+            uint32_t v[16];
+            load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) tile[r][q + e] = (int8_t)(RAW ? (int)v[e] : centre_i(v[e], p, h));
-    }
-    __syncthreads();
-    const int64_t j = j0 + r;
-    if (j < np) {
-        if constexpr (RAW) {
-            uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int e = 0; e < 16; ++e) w[e >> 2] |= (uint32_t)(uint8_t)tile[q + e][r] << (8 * (e & 3));
-            *reinterpret_cast<uint4 *>(out + j * kp + l0 + q) = make_uint4(w[0], w[1], w[2], w[3]);
-        } else {
-            int c[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) c[e] = tile[q + e][r];
-            put16<FP8>(out + (j * kp + l0 + q) * ES, c);
+            for (int e = 0; e < 16; ++e) tile[r][q + e] = (int8_t)(RAW ? (int)v[e] : centre_i(v[e], p, h));
         }
+        __syncthreads();
+        const int64_t j = j0 + r;
+        if (j < np) {
+            if constexpr (RAW) {
+                uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int e = 0; e < 16; ++e) w[e >> 2] |= (uint32_t)(uint8_t)tile[q + e][r] << (8 * (e & 3));
+                *reinterpret_cast<uint4 *>(out + j * kp + l0 + q) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                int c[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) c[e] = tile[q + e][r];
+                put16<FP8>(out + (j * kp + l0 + q) * ES, c);
+            }
+        }
+        __syncthreads();   // the tile is refilled by the next iteration
     }
 }
 
@@ -812,7 +817,7 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     if (e != cudaSuccess) return cuda_fail(e);
     {
         dim3 grid((unsigned)((kp / 16 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
-        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64));
+        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
         if (raw) {
             to_op_transpose_kernel<true, true><<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
         } else if (fp8) {
@@ -869,9 +874,10 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
 // operands, also the k-major B of the dp4a classical product.
 gfp_status launch_transpose_bytes(const uint8_t *B, int64_t ldb, int64_t k, int64_t n, uint8_t *out, int64_t kp,
                                   int64_t np, cudaStream_t s) {
-    if (kp % 64 || np % 64 || kp / 64 > 2147483647 || np / 64 > 65535) return GFP_EINVAL;
+    if (kp % 64 || np % 64 || kp / 64 > 2147483647) return GFP_EINVAL;
     if (kp == 0 || np == 0) return GFP_OK;
-    to_op_transpose_kernel<true, true><<<dim3((unsigned)(kp / 64), (unsigned)(np / 64)), 256, 0, s>>>(
+    to_op_transpose_kernel<true, true><<<dim3((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535)),
+                                         256, 0, s>>>(
         B, ldb, k, n, out, kp, np, 0u, 0u);
     return check_launch();
 }

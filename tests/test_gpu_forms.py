@@ -107,6 +107,16 @@ def test_dp4a_aligned_rows_with_a_partial_last_group():
     assert (host(C) == oracle.gemm(p, np.ascontiguousarray(wide[:, :k]), B, threads=THREADS)).all()
 
 
+@pytest.mark.parametrize("algo", ["dp4a", "tc_mma_s8", "tc_f16", "tc_f8"])
+def test_wider_than_the_grid_limit(algo):
+    """n = 4,300,000 columns: more 64-column tiles of B^T (67,188) than a grid's y
+    dimension holds (65,535); the operand transposes loop over them."""
+    p, m, k, n = 5, 3, 5, 4_300_000
+    A, B = operands(10, 1, p, m, k, n)
+    C = gfp.gfp_gemm(p, dev(A), dev(B), algo)
+    assert (host(C) == oracle.gemm(p, A, B, threads=THREADS)).all()
+
+
 # Results spanning at least two waves of the 128 x 128 and 128 x 64 register tiles
 # of the CUDA-core kernels (the only shapes that use them), ragged in both
 # dimensions: at 4001 x 3999 the classical and dp4a products run on 128 x 128
