@@ -1,25 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the exact GF(p) product, one JSON line on stdout.
 
-Workload: p = 3, m = k = n = 1024, residues i.i.d. uniform in [0, p) (seeded,
-synthetic: the paper has no dataset).  One step runs every stage of the hot
-path once on that input:
+Workload (the headline): every form of C = A B mod p at p = 5,
+m = k = n = 16384, residues i.i.d. uniform in [0, p) (seeded, synthetic: the
+paper has no dataset).  One step runs each form once on that input:
 
-  parameters (host)            gfp_params for every form
+  classical product            gfp_gemm(plain): one 32-bit multiply-add per term
+  classical product on dp4a    gfp_gemm(dp4a): four byte products per instruction
   Q-adic dot form, u64 words   gfp_pack(A, rows reversed), gfp_pack(B, columns),
                                gfp_gemm_compressed(dot, u64)
-  Q-adic dot form, FP64 words  the same with binary64 words (round-toward-zero)
+  Q-adic dot form, tuned       the same with the word, d, Q and k-block the
+                               dot-form autotuner picks for this shape
   right-compressed form, u64   gfp_pack(B, rows), gfp_gemm_compressed(mixed)
                                with REDQ, gfp_unpack(CC)
-  classical product            gfp_gemm(plain)
-  exact tensor-core forms      gfp_gemm(tc_f16), gfp_gemm(tc_f8), gfp_gemm(tc_mma_s8)
+  exact tensor-core forms      gfp_gemm(tc_mma_s8), gfp_gemm(tc_f16),
+                               gfp_gemm(tc_f8), gfp_gemm(tc_e2m1)
 
 value = (products per step x 2mnk) / step time (every product is the full
-C = A B mod p).  Each step is timed alone with CUDA events; a 256 MiB buffer
-is written between steps so that no step starts with its inputs in L2.
-`forms` gives each form (and each machine word) timed on its own, `batched`
-the grouped launch over 4096 adjacency squares, `roofline` the dominant
-kernel of the step against its pipe's peak.
+C = A B mod p, checked bit for bit before timing).  Each step is timed with
+CUDA events on the launching stream; the operands (256 MiB each) are larger
+than L2 and a 256 MiB buffer is also written between steps.  `forms` gives
+each form's time inside the step, its rate, its speedup over both classical
+products and its kernel's fraction of the pipe it runs on; `roofline` is the
+step's dominant kernel.  Extra keys carry the other workloads:
+`compressed_1024` (p = 3, 1024^3, every machine word including FP64),
+`tensor_core_8192` (p in {3, 31, 251}, 8192^3) and `batched` (4096 adjacency
+squares in one graph replay).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfp|reference]
 """
@@ -37,46 +43,41 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-P, M, K, N = 3, 1024, 1024, 1024
+P, M, K, N = 5, 16384, 16384, 16384
 FLOP = 2.0 * M * N * K
 METRIC = "GF(p) GEMM effective 2mnk/s (bit-exact) per form vs plain GPU; % of roofline"
 UNIT = "T(2mnk)/s"
-WORKLOAD = "Q-adic compressed GEMM and all forms, p=3, m=k=n=1024, uniform residues"
+WORKLOAD = "all forms, p=5, m=k=n=16384, residues i.i.d. uniform in [0,p)"
+SEED = (5, 0)                 # inputs.rng(workload 5, trial 0)
+ORACLE_ROWS = 16              # rows of the product the reference arm's oracle computes per step
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-# Throughput ceilings of the pipe each form runs on.  Instruction rates were
-# measured on this machine's GB300 by chains of one instruction over 4 CTAs per
-# SM (152 SMs at 2.07 GHz); tensor-core rates from MEASURED_PEAKS.json (bf16
-# dense burst; fp16 runs at the bf16 rate, e4m3 at twice it).  Each form's
-# work is counted in the unit its inner loop issues.
+def config_dict():
+    """The workload description shared by both arms of the benchmark."""
+    return {"workload": WORKLOAD, "p": P, "m": M, "k": K, "n": N,
+            "l2": "operands of 256 MiB each (larger than L2) and a 256 MiB buffer written between steps"}
+
+
+# Throughput ceilings of the pipes the CUDA-core forms run on.  GB300: 152
+# SMs at up to 2.07 GHz.  The per-SM instruction rates were measured on this
+# pool's GB300 with chains of one instruction over 4 CTAs per SM: 64 32-bit
+# multiply-adds (IMAD, IMAD.WIDE) or dp4a per SM per clock, and 7.2e12/s for
+# the 64-bit multiply-add as the compiler lowers it.  Each form's work is
+# counted in the unit its inner loop issues.
+SMS, CLOCK = 152, 2.07e9
 PIPES = {
-    "imad": (19.6e12, "IMAD/s (32-bit multiply-add, measured)"),
-    "imad_wide": (19.6e12, "IMAD.WIDE/s (32x32->64 multiply-add, measured)"),
-    "dp4a": (19.7e12, "dp4a/s (measured)"),
-    "mad64": (7.2e12, "64-bit mad.lo/s (measured)"),
-    "mad64x2": (3.6e12, "64x64->128 multiply-adds/s (two 64-bit mads each, from the measured mad rate)"),
-    "mad64x32": (9.8e12, "64x32-bit multiply-adds/s (two IMADs each, from the measured IMAD rate)"),
-    "dfma": (0.625e12, "DFMA/s (nominal FP64 of GB300; a measured chain reached 0.52e12)"),
+    "imad": (SMS * 64 * CLOCK, "IMAD/s (152 SMs x 64 lanes x 2.07 GHz)"),
+    "imad_wide": (SMS * 64 * CLOCK, "IMAD.WIDE/s (152 SMs x 64 lanes x 2.07 GHz)"),
+    "dp4a": (SMS * 64 * CLOCK, "dp4a/s (152 SMs x 64 lanes x 2.07 GHz)"),
+    "mad64": (7.2e12, "64-bit mad.lo/s (measured chain rate)"),
+    "mad64x2": (3.6e12, "64x64->128 multiply-adds/s (two 64-bit mads each)"),
+    "mad64x32": (SMS * 64 * CLOCK / 2, "64x32-bit multiply-adds/s (two IMADs each)"),
     "mma_s8": (158e12, "int8 mma.sync ops/s (measured)"),
 }
-
-
-# DRAM bytes of one launch of the dominant kernel (simt_gemm_kernel<DotF64,
-# 32, 32, 16, 2, 2> on this step's input), from an ncu capture of this bench:
-# 4,212,224 read (CA + CB once) + 0 written (the uint8 C leaves L2 later).
-DOTF64_TRAFFIC = 4212224
-
-
-def form_roofline(ms: float, work: float, pipe: str = None, peak: float = None, unit: str = None):
-    """Achieved rate of `work` units in `ms` against a pipe's ceiling."""
-    if pipe is not None:
-        peak, unit = PIPES[pipe]
-    achieved = work / (ms * 1e-3)
-    return {"work_per_launch": work, "peak": peak, "unit": unit, "frac": round(achieved / peak, 4)}
 
 
 def measured_peaks():
@@ -85,6 +86,44 @@ def measured_peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def tensor_peaks():
+    """Dense tensor-core peaks (flops/s) from the measured bf16 rate: fp16 runs
+    at the bf16 rate, e4m3 at twice it and e2m1 (block-scaled fp4) at six
+    times it (GB300's nominal dense rates 2.25 : 4.5 : 13.5 PFLOP/s; a
+    cuBLASLt e4m3 product measured 1.96x bf16 on this GPU)."""
+    pk = measured_peaks()
+    bf16 = (pk.get("bf16_tflops") or 1900.0) * 1e12
+    src = "MEASURED_PEAKS.json bf16_tflops (burst)" if pk.get("bf16_tflops") else "fallback 1.9 PFLOP/s"
+    return {"tc_f16": (bf16, "fp16 tcgen05 flops/s (bf16 dense, %s)" % src),
+            "tc_f8": (2 * bf16, "e4m3 tcgen05 flops/s (2 x bf16 dense, %s)" % src),
+            "tc_e2m1": (6 * bf16, "e2m1 block-scaled tcgen05 flops/s (6 x bf16 dense, %s)" % src),
+            "tc_mma_s8": PIPES["mma_s8"]}
+
+
+def form_roofline(ms: float, work: float, pipe: str = None, peak: float = None, unit: str = None):
+    """Achieved rate of `work` units in `ms` against a pipe's ceiling."""
+    if pipe is not None:
+        peak, unit = PIPES[pipe]
+    achieved = work / (ms * 1e-3)
+    return {"work_per_launch": work, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": round(achieved / peak, 4)}
+
+
+def event_time(torch, fn, reps, flush):
+    """Median CUDA-event time (ms) of fn over reps calls, L2 flushed before each."""
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
 
 
 # ---------------------------------------------------------------------------
@@ -138,183 +177,229 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+
+
 # ---------------------------------------------------------------------------
 # the GPU step
 # ---------------------------------------------------------------------------
 class Step:
-    """Every stage of the hot path on one (A, B); buffers allocated once."""
+    """Every form on one (A, B); buffers allocated once.  Each form is a list
+    of preparation launches, one product launch, and finishing launches, so
+    that events can bracket the form and its product kernel separately."""
 
-    LAUNCHES = 17   # kernels of this library per step (counted below)
-
-    def __init__(self, gfp, torch, A, B):
+    def __init__(self, gfp, torch, A, B, tuned):
         self.gfp, self.torch = gfp, torch
         self.A, self.B = A, B
         dev = A.device
         e = lambda *s, dt=torch.uint8: torch.empty(*s, dtype=dt, device=dev)
-        self.d64, self.Q64, _ = gfp.gfp_params(P, M, K, N, "dot", "u64")
-        self.df, self.Qf, _ = gfp.gfp_params(P, M, K, N, "dot", "f64")
-        self.dm, self.Qm, _ = gfp.gfp_params(P, M, K, N, "mixed", "u64")
-        kc64 = -(-K // (self.d64 + 1))
-        kcf = -(-K // (self.df + 1))
-        self.CA64 = e((M, kc64), dt=torch.int64)
-        self.CB64 = e((kc64, N), dt=torch.int64)
-        self.CAf = e((M, kcf), dt=torch.float64)
-        self.CBf = e((kcf, N), dt=torch.float64)
-        ncm = -(-N // (self.dm + 1))
-        self.CBr = e((K, ncm), dt=torch.int64)
-        self.CC = e((M, ncm), dt=torch.int64)
-        self.outs = {name: e((M, N)) for name in ("dot_u64", "dot_f64", "mixed_u64", "plain", "tc_f16",
-                                                  "tc_f8", "tc_mma_s8")}
-        self.ws16 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_f16"))
-        self.wsf8 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_f8"))
-        self.ws8 = e(gfp.gfp_gemm_workspace_size(P, M, K, N, "tc_mma_s8"))
-        self.dom = None   # (start, end) events around the dominant kernel
+        g = gfp
+        self.forms = {}          # name -> (prep, product, finish, product work, pipe, launches)
+        self.outs = {}
 
-    def run(self, dom_events=None, done=None):
-        """One step.  `done(name)`, if given, is called as soon as the launch
-        that completes output `name` has been issued (to start its copy)."""
-        g = self.gfp
-        done = done or (lambda name: None)
-        # parameters (host)
-        d64, Q64, _ = g.gfp_params(P, M, K, N, "dot", "u64")
-        df, Qf, _ = g.gfp_params(P, M, K, N, "dot", "f64")
+        def out(name):
+            self.outs[name] = e((M, N))
+            return self.outs[name]
+
+        ws = lambda algo: e(max(1, g.gfp_gemm_workspace_size(P, M, K, N, algo)))
+        # classical products
+        C = out("plain")
+        self.forms["plain"] = ([], lambda C=C: g.gfp_gemm(P, A, B, "plain", out=C), [],
+                               M * N * K, "imad", 1)
+        C, w = out("dp4a"), ws("dp4a")
+        self.forms["dp4a"] = ([], lambda C=C, w=w: g.gfp_gemm(P, A, B, "dp4a", out=C, workspace=w), [],
+                              M * N * -(-K // 4), "dp4a", 2)
+        # Q-adic dot forms: 64-bit words, and the autotuner's choice
+        self.dot = {}
+        for name, (word, d, Q, kb) in (("dot_u64", ("u64",) + g.gfp_params(P, M, K, N, "dot", "u64")),
+                                       ("dot_tuned", tuned)):
+            kc = -(-K // (d + 1))
+            CA = e((M, kc), dt=g.WORD_DTYPE[word])
+            CB = e((kc, N), dt=g.WORD_DTYPE[word])
+            C = out(name)
+            prep = [lambda CA=CA, word=word, d=d, Q=Q: g.gfp_pack(P, A, d, Q, "rows_rev", word, out=CA),
+                    lambda CB=CB, word=word, d=d, Q=Q: g.gfp_pack(P, B, d, Q, "cols", word, out=CB)]
+            prod = (lambda CA=CA, CB=CB, C=C, word=word, d=d, Q=Q, kb=kb:
+                    g.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kb))
+            pipe = {"u64": "mad64", "u64x128": "mad64x2", "u32w": "imad_wide", "u32": "imad"}[word]
+            self.forms[name] = (prep, prod, [], M * N * kc, pipe, 3)
+            self.dot[name] = {"word": word, "d_plus_1": d + 1, "t": Q.bit_length() - 1, "kb": kb}
+        # right-compressed form with REDQ, then the words unpacked
         dm, Qm, _ = g.gfp_params(P, M, K, N, "mixed", "u64")
-        # dot form, u64 words: 3 launches
-        g.gfp_pack(P, self.A, d64, Q64, "rows_rev", "u64", out=self.CA64)
-        g.gfp_pack(P, self.B, d64, Q64, "cols", "u64", out=self.CB64)
-        g.gfp_gemm_compressed(P, M, K, N, d64, Q64, "dot", "u64", self.CA64, self.CB64, out=self.outs["dot_u64"])
-        done("dot_u64")
-        # dot form, FP64 words: 3 launches (the product is the step's dominant kernel)
-        g.gfp_pack(P, self.A, df, Qf, "rows_rev", "f64", out=self.CAf)
-        g.gfp_pack(P, self.B, df, Qf, "cols", "f64", out=self.CBf)
-        if dom_events is not None:
-            dom_events[0].record()
-        g.gfp_gemm_compressed(P, M, K, N, df, Qf, "dot", "f64", self.CAf, self.CBf, out=self.outs["dot_f64"])
-        if dom_events is not None:
-            dom_events[1].record()
-        done("dot_f64")
-        # right-compressed form with REDQ: 3 launches
-        g.gfp_pack(P, self.B, dm, Qm, "rows", "u64", out=self.CBr)
-        g.gfp_gemm_compressed(P, M, K, N, dm, Qm, "mixed", "u64", self.A, self.CBr, out=self.CC)
-        g.gfp_unpack(P, self.CC, M, N, dm, Qm, "rows", "u64", out=self.outs["mixed_u64"])
-        done("mixed_u64")
-        # classical product: 1 launch
-        g.gfp_gemm(P, self.A, self.B, "plain", out=self.outs["plain"])
-        done("plain")
-        # tensor-core forms: 3 + 2 + 3 launches (operand conversion, product; the
-        # fp8 form converts only B for p < 16)
-        g.gfp_gemm(P, self.A, self.B, "tc_f16", out=self.outs["tc_f16"], workspace=self.ws16)
-        done("tc_f16")
-        g.gfp_gemm(P, self.A, self.B, "tc_f8", out=self.outs["tc_f8"], workspace=self.wsf8)
-        done("tc_f8")
-        g.gfp_gemm(P, self.A, self.B, "tc_mma_s8", out=self.outs["tc_mma_s8"], workspace=self.ws8)
-        done("tc_mma_s8")
+        ncm = -(-N // (dm + 1))
+        CBr = e((K, ncm), dt=torch.int64)
+        CC = e((M, ncm), dt=torch.int64)
+        C = out("mixed_u64")
+        self.forms["mixed_u64"] = (
+            [lambda: g.gfp_pack(P, B, dm, Qm, "rows", "u64", out=CBr)],
+            lambda: g.gfp_gemm_compressed(P, M, K, N, dm, Qm, "mixed", "u64", A, CBr, out=CC),
+            [lambda C=C: g.gfp_unpack(P, CC, M, N, dm, Qm, "rows", "u64", out=C)],
+            M * K * ncm, "mad64x32", 3)
+        self.dot["mixed_u64"] = {"word": "u64", "d_plus_1": dm + 1, "t": Qm.bit_length() - 1}
+        # exact tensor-core forms (operand conversions inside the call)
+        tpk = tensor_peaks()
+        launches = {"tc_mma_s8": 3, "tc_f16": 3, "tc_f8": 2, "tc_e2m1": 3}
+        for algo in ("tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1"):
+            if algo not in g.ALGOS:
+                continue
+            C, w = out(algo), ws(algo)
+            self.forms[algo] = ([], lambda C=C, w=w, algo=algo: g.gfp_gemm(P, A, B, algo, out=C, workspace=w),
+                                [], FLOP, tpk[algo], launches[algo])
 
     @property
     def products(self):
-        return len(self.outs)
+        return len(self.forms)
+
+    @property
+    def launches(self):
+        return sum(f[5] for f in self.forms.values())
+
+    def run(self, ev=None, done=None):
+        """One step.  ev: name -> four events (form start, product start,
+        product end, form end), recorded on the current stream.  done(name),
+        if given, is called once the launches completing output `name` are
+        issued (to start its copy to the host)."""
+        for name, (prep, prod, finish, _, _, _) in self.forms.items():
+            e4 = ev[name] if ev is not None else None
+            if e4:
+                e4[0].record()
+            for f in prep:
+                f()
+            if e4:
+                e4[1].record()
+            prod()
+            if e4:
+                e4[2].record()
+            for f in finish:
+                f()
+            if e4:
+                e4[3].record()
+            if done is not None:
+                done(name)
 
 
-def event_time(torch, fn, reps, flush):
-    ts = []
-    for _ in range(reps):
-        flush.zero_()
+# ---------------------------------------------------------------------------
+# the other workloads (extra keys)
+# ---------------------------------------------------------------------------
+def fp64_peak(torch):
+    """FP64 denominator measured here: cuBLAS DGEMM (torch.matmul in float64)
+    at 4096^3, best of 5 (CUDA events).  flops/s."""
+    a = torch.rand(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.rand(4096, 4096, dtype=torch.float64, device="cuda")
+    c = torch.empty_like(a)
+    for _ in range(2):
+        torch.matmul(a, b, out=c)
+    best = None
+    for _ in range(5):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        fn()
+        torch.matmul(a, b, out=c)
         e1.record()
         torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    return float(np.median(ts))
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return 2.0 * 4096 ** 3 / (best * 1e-3)
 
 
-def forms_breakdown(gfp, torch, A, B, flush, plain_ms):
-    """Each form and word timed on its own (median of 7, L2 flushed), with
-    its fraction of the ceiling of the pipe it runs on."""
-    out = {}
+def compressed_1024(gfp, torch, inputs, flush, f64_peak):
+    """p = 3, m = k = n = 1024: every machine word of the dot form (FP64
+    included), the mixed, left and full forms, both classical products and
+    the tensor-core forms, each timed alone (median of 7, L2 flushed)."""
+    p, m, k, n = 3, 1024, 1024, 1024
+    flop = 2.0 * m * n * k
+    g = inputs.rng(2, 0)
+    A = torch.from_numpy(inputs.residues(g, p, m, k)).cuda()
+    B = torch.from_numpy(inputs.residues(g, p, k, n)).cuda()
     dev = A.device
-    bf16 = (measured_peaks().get("bf16_tflops") or 1900.0) * 1e12
-    hbm = (measured_peaks().get("hbm_gbs") or 6800.0) * 1e9
+    out = {"workload": "Q-adic compressed GEMM and all forms, p=3, m=k=n=1024, uniform residues"}
+    tpk = tensor_peaks()
+    pipes = dict(PIPES, dfma=(f64_peak / 2, "DFMA/s (half the measured cuBLAS DGEMM flops/s)"))
+    base = {}
 
-    def rec(name, ms, roof=None, **extra):
-        r = {"ms": round(ms, 5), "value": round(FLOP / ms / 1e9, 3), "speedup_vs_plain": round(plain_ms / ms, 3)}
+    def rec(name, ms, work=None, pipe=None, **extra):
+        r = {"ms": round(ms, 5), "value": round(flop / ms / 1e9, 3)}
+        for b in ("plain", "dp4a"):
+            if b in base:
+                r["speedup_vs_" + b] = round(base[b] / ms, 3)
         r.update(extra)
-        if roof is not None:
-            r["roofline"] = roof
+        if work is not None:
+            peak, unit = pipes[pipe] if isinstance(pipe, str) else pipe
+            r["roofline"] = form_roofline(ms, work, peak=peak, unit=unit)
         out[name] = r
 
-    tc_roof = {"plain": lambda ms: form_roofline(ms, M * N * K, "imad"),
-               "dp4a": lambda ms: form_roofline(ms, M * N * -(-K // 4), "dp4a"),
-               "tc_mma_s8": lambda ms: form_roofline(ms, FLOP, "mma_s8"),
-               "tc_f16": lambda ms: form_roofline(ms, FLOP, peak=bf16, unit="fp16 tcgen05 flops/s (bf16 dense, measured)"),
-               "tc_f8": lambda ms: form_roofline(ms, FLOP, peak=2 * bf16,
-                                                 unit="e4m3 tcgen05 flops/s (2 x measured bf16 dense)")}
-    for algo in ("plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8"):
-        ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(P, M, K, N, algo)), dtype=torch.uint8, device=dev)
-        C = torch.empty((M, N), dtype=torch.uint8, device=dev)
-        ms = event_time(torch, lambda: gfp.gfp_gemm(P, A, B, algo, out=C, workspace=ws), 7, flush)
-        rec(algo, ms, tc_roof[algo](ms))
+    for algo in ("plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1"):
+        if algo not in gfp.ALGOS:
+            continue
+        ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(p, m, k, n, algo)), dtype=torch.uint8, device=dev)
+        C = torch.empty((m, n), dtype=torch.uint8, device=dev)
+        ms = event_time(torch, lambda: gfp.gfp_gemm(p, A, B, algo, out=C, workspace=ws), 7, flush)
+        work = {"plain": (m * n * k, "imad"), "dp4a": (m * n * -(-k // 4), "dp4a")}.get(algo, (flop, tpk.get(algo)))
+        if algo in ("plain", "dp4a"):
+            base[algo] = ms
+        rec(algo, ms, *work)
     word_pipe = {"u64": "mad64", "u64x128": "mad64x2", "u32w": "imad_wide", "u32": "imad", "f64": "dfma"}
     for word, kb in (("u64", 0), ("u64x128", 0), ("u32w", 0), ("u32", 0), ("f64", 0), ("u32", 60),
                      ("u32w", 140)):
-        d, Q, kbr = gfp.gfp_params(P, M, K, N, "dot", word, kb=kb)
-        CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", word)
-        CB = gfp.gfp_pack(P, B, d, Q, "cols", word)
-        C = torch.empty((M, N), dtype=torch.uint8, device=dev)
-        t_mm = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr), 7, flush)
-
-        def full():
-            gfp.gfp_pack(P, A, d, Q, "rows_rev", word, out=CA)
-            gfp.gfp_pack(P, B, d, Q, "cols", word, out=CB)
-            gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr)
-        t_full = event_time(torch, full, 7, flush)
+        d, Q, kbr = gfp.gfp_params(p, m, k, n, "dot", word, kb=kb)
+        CA = gfp.gfp_pack(p, A, d, Q, "rows_rev", word)
+        CB = gfp.gfp_pack(p, B, d, Q, "cols", word)
+        C = torch.empty((m, n), dtype=torch.uint8, device=dev)
+        t_mm = event_time(torch, lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", word, CA, CB, out=C,
+                                                                 kb=kbr), 7, flush)
         name = "dot_%s" % word + ("_kb%d" % kbr if kbr else "")
-        rec(name, t_mm, form_roofline(t_mm, M * N * -(-K // (d + 1)), word_pipe[word]),
-            d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr,
-            with_packing_ms=round(t_full, 5), with_packing_value=round(FLOP / t_full / 1e9, 3))
-    # the autotuner's pick of (word, d, Q, k-block) for this shape (untimed search)
-    best, cands = gfp.gfp_dot_autotune(P, M, K, N)
-    word, d, Q, kbr = best["word"], best["d"], best["Q"], best["kb"]
-    CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", word)
-    CB = gfp.gfp_pack(P, B, d, Q, "cols", word)
-    C = torch.empty((M, N), dtype=torch.uint8, device=dev)
-    ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "dot", word, CA, CB, out=C, kb=kbr), 7, flush)
-    rec("dot_autotuned", ms, form_roofline(ms, M * N * -(-K // (d + 1)), word_pipe[word]), word=word,
-        d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr, candidates=len(cands))
+        rec(name, t_mm, m * n * -(-k // (d + 1)), word_pipe[word], d_plus_1=d + 1, t=Q.bit_length() - 1, kb=kbr)
     for word in ("u64", "f64"):
-        d, Q, _ = gfp.gfp_params(P, M, K, N, "mixed", word)
-        CB = gfp.gfp_pack(P, B, d, Q, "rows", word)
-        CC = torch.empty((M, -(-N // (d + 1))), dtype=gfp.WORD_DTYPE[word], device=dev)
-        ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "mixed", word, A, CB, out=CC), 7, flush)
-        rec("mixed_%s" % word, ms, form_roofline(ms, M * K * -(-N // (d + 1)), "mad64x32" if word == "u64" else "dfma"),
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "mixed", word)
+        CB = gfp.gfp_pack(p, B, d, Q, "rows", word)
+        CC = torch.empty((m, -(-n // (d + 1))), dtype=gfp.WORD_DTYPE[word], device=dev)
+        ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "mixed", word, A, CB, out=CC),
+                        7, flush)
+        rec("mixed_%s" % word, ms, m * k * -(-n // (d + 1)), "mad64x32" if word == "u64" else "dfma",
             d_plus_1=d + 1, t=Q.bit_length() - 1)
-    # left (Table 2) and full (Section 4) compression, u64 words, product only
-    d, Q, _ = gfp.gfp_params(P, M, K, N, "left", "u64")
-    CA = gfp.gfp_pack(P, A, d, Q, "cols", "u64")
-    CC = torch.empty((-(-M // (d + 1)), N), dtype=torch.int64, device=dev)
-    ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(P, M, K, N, d, Q, "left", "u64", CA, B, out=CC), 7, flush)
-    rec("left_u64", ms, form_roofline(ms, -(-M // (d + 1)) * K * N, "mad64x32"), d_plus_1=d + 1, t=Q.bit_length() - 1)
-    dq, dth, Q = gfp.gfp_params_full(P, M, K, N, "u64")
-    CA = gfp.gfp_pack(P, A, dq, Q, "cols", "u64")
-    CB = gfp.gfp_pack(P, B, dth, Q ** (dq + 1), "rows", "u64")
-    CC = torch.empty((-(-M // (dq + 1)), -(-N // (dth + 1))), dtype=torch.int64, device=dev)
-    ms = event_time(torch, lambda: gfp.gfp_gemm_full(P, M, K, N, dq, dth, Q, "u64", CA, CB, out=CC), 7, flush)
-    rec("full_u64", ms, form_roofline(ms, -(-M // (dq + 1)) * K * -(-N // (dth + 1)), "mad64"),
-        dq=dq, dth=dth, t=Q.bit_length() - 1)
-    # conversions: pack A reversed into u64 words, bytes moved per launch
-    d, Q, _ = gfp.gfp_params(P, M, K, N, "dot", "u64")
-    CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64")
-    t = event_time(torch, lambda: gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64", out=CA), 7, flush)
-    byts = M * K + CA.numel() * 8
-    out["pack_rows_rev_u64"] = {"ms": round(t, 5), "GB_per_s": round(byts / t / 1e6, 1), "bytes": byts,
-                                "roofline": form_roofline(t, byts, peak=hbm, unit="bytes/s (measured HBM copy)")}
+    d, Q, _ = gfp.gfp_params(p, m, k, n, "left", "u64")
+    CA = gfp.gfp_pack(p, A, d, Q, "cols", "u64")
+    CC = torch.empty((-(-m // (d + 1)), n), dtype=torch.int64, device=dev)
+    ms = event_time(torch, lambda: gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "left", "u64", CA, B, out=CC), 7, flush)
+    rec("left_u64", ms, -(-m // (d + 1)) * k * n, "mad64x32", d_plus_1=d + 1, t=Q.bit_length() - 1)
+    dq, dth, Q = gfp.gfp_params_full(p, m, k, n, "u64")
+    CA = gfp.gfp_pack(p, A, dq, Q, "cols", "u64")
+    CB = gfp.gfp_pack(p, B, dth, Q ** (dq + 1), "rows", "u64")
+    CC = torch.empty((-(-m // (dq + 1)), -(-n // (dth + 1))), dtype=torch.int64, device=dev)
+    ms = event_time(torch, lambda: gfp.gfp_gemm_full(p, m, k, n, dq, dth, Q, "u64", CA, CB, out=CC), 7, flush)
+    rec("full_u64", ms, -(-m // (dq + 1)) * k * -(-n // (dth + 1)), "mad64", dq=dq, dth=dth, t=Q.bit_length() - 1)
     return out
 
 
-def batched_measure(gfp, torch, flush):
+def tensor_core_8192(gfp, torch, inputs, flush):
+    """p in {3, 31, 251}, m = k = n = 8192: every tensor-core algorithm the
+    prime allows, median of 5 calls (operand conversion included), with its
+    fraction of the dense peak of the pipe it runs on."""
+    n = 8192
+    flop = 2.0 * n ** 3
+    tpk = tensor_peaks()
+    out = {"workload": "exact tensor-core GEMM, p in {3,31,251}, m=k=n=8192, uniform residues"}
+    for p in (3, 31, 251):
+        g = inputs.rng(3, p)
+        A = torch.from_numpy(inputs.residues(g, p, n, n)).cuda()
+        B = torch.from_numpy(inputs.residues(g, p, n, n)).cuda()
+        row = {}
+        for algo in ("tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1"):
+            if algo not in gfp.ALGOS or not algo_admits(algo, p):
+                continue
+            ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(p, n, n, n, algo)), dtype=torch.uint8,
+                             device="cuda")
+            C = torch.empty((n, n), dtype=torch.uint8, device="cuda")
+            ms = event_time(torch, lambda: gfp.gfp_gemm(p, A, B, algo, out=C, workspace=ws), 5, flush)
+            peak, unit = tpk[algo]
+            row[algo] = {"ms": round(ms, 4), "value": round(flop / ms / 1e9, 2),
+                         "roofline": form_roofline(ms, flop, peak=peak, unit=unit)}
+        out["p%d" % p] = row
+        del A, B
+    return out
+
+
+def batched_measure(gfp, torch, inputs, flush):
     """4096 squares of adjacency matrices in one grouped launch (CUDA graph)."""
-    from paper_0803_1975_gb300 import inputs
     probs = inputs.batched_problems()
     dev = torch.device("cuda")
     items = []
@@ -340,78 +425,118 @@ def batched_measure(gfp, torch, flush):
     with torch.cuda.graph(graph):
         gfp.gfp_batched_launch(ws)
     ms = event_time(torch, graph.replay, 7, flush)
-    # kinds in use: the tuned kind of every size bucket that holds a problem
-    kinds = set()
-    for p, A in probs:
-        n = A.shape[0]
-        b = 0 if n <= 32 else 1 if n <= 64 else 2 if n <= 128 else 3 if n <= 256 else 4 if n <= 512 else 5
-        k = table[b]
-        kinds.add(k if k >= 0 else (4 if p < 16 else 0))
-    kernels = 1 + (1 if kinds & {0, 1, 2, 3} else 0) + (1 if 4 in kinds else 0)
-    return {"problems": cnt, "sum_2n3": flops, "ms": round(ms, 4), "value": round(flops / ms / 1e9, 3),
-            "unit": UNIT, "kernels_per_replay": kernels,
-            "autotuned_kinds": [gfp.BATCHED_KINDS.get(v, None) for v in table],
-            "note": "one graph replay = operand conversion kernel, then one persistent grouped kernel per "
-                    "engine in use: tcgen05 e4m3 tiles (p < 16) and/or mma.sync / Q-adic SIMT tiles"}
+    return {"workload": "4096 squares A_i^2 mod p_i of symmetric 0/1 adjacency matrices, n_i log-uniform in "
+                        "[16,512], p_i in {3,5,7}", "problems": cnt, "sum_2n3": flops, "ms": round(ms, 4),
+            "value": round(flops / ms / 1e9, 3), "unit": UNIT,
+            "engines": batched_engines(gfp, table, [A.shape[0] for _, A in probs])}
+
+
+def algo_admits(algo: str, p: int) -> bool:
+    """Primes each tensor-core algorithm takes (include/gfp.h): e2m1 holds the
+    centred residues of p <= 7 exactly, e4m3 those of p <= 31."""
+    return {"tc_e2m1": p <= 7, "tc_f8": p <= 31}.get(algo, True)
+
+
+def batched_engines(gfp, table, sizes):
+    """The tile kind that ran each size bucket holding problems: the
+    autotuner's pick, or the library's default (tcgen05 tiles) where it kept
+    the default.  Buckets are by the problem's largest extent."""
+    edges = [(32, "n<=32"), (64, "n<=64"), (128, "n<=128"), (256, "n<=256"), (512, "n<=512"),
+             (2048, "n<=2048"), (1 << 62, "n>2048")]
+    used = {}
+    for n in sizes:
+        b = next(i for i, (e, _) in enumerate(edges) if n <= e)
+        used[b] = used.get(b, 0) + 1
+    out = {}
+    for b, cnt in sorted(used.items()):
+        v = table[b] if b < len(table) else -1
+        kind = gfp.BATCHED_KINDS.get(v if v >= 0 else 4, str(v))
+        out[edges[b][1]] = {"problems": cnt, "engine": kind, "tuned": v >= 0}
+    return out
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_rate(A, B, budget_s=10.0):
-    """The oracle (plain C triple loop over all host cores) on the same
-    product; repeated until about budget_s of CPU time."""
+# the CPU oracle beside it
+# ---------------------------------------------------------------------------
+def sample_rows(count):
+    """`count` rows of the product spread evenly over m (first and last included)."""
+    return np.unique(np.linspace(0, M - 1, count).round().astype(np.int64))
+
+
+def cpu_oracle_rate(A, B, budget_s=12.0):
+    """The oracle (the plain C triple loop over all host cores) on sampled
+    rows of the same 16384^3 product, scaled to about budget_s of CPU time."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
+    rows = sample_rows(cores)
     t0 = time.time()
-    oracle.gemm(P, A, B, threads=cores)
+    oracle.gemm_rows(P, rows, A, B, threads=cores)
     one = time.time() - t0
-    reps = max(1, int(budget_s / max(one, 1e-3)) - 1)
-    reps = min(reps, 50)
+    count = int(min(1024, max(rows.size, rows.size * budget_s / max(one, 1e-3))))
+    rows = sample_rows(count)
     t0 = time.time()
-    for _ in range(reps):
-        oracle.gemm(P, A, B, threads=cores)
-    per = (time.time() - t0) / reps
-    return FLOP / per / 1e12, cores, "%d full %dx%dx%d products (p=%d) after one untimed" % (reps, M, K, N, P), per
+    oracle.gemm_rows(P, rows, A, B, threads=cores)
+    per = time.time() - t0
+    v = rows.size * 2.0 * K * N / per / 1e12
+    return v, cores, "%d of the %d rows of the p=%d %dx%dx%d product (rows spread evenly), %.1f s" % (
+        rows.size, M, P, M, K, N, per)
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle as it stands, timed on the host cores."""
+    """--impl reference: the oracle as it stands, timed on the host cores on
+    --oracle-rows sampled rows of the same product per step."""
     if rank != 0:
         return
     from paper_0803_1975_gb300 import inputs
     import oracle
     oracle.build()
-    g = inputs.rng(2, 0)
+    g = inputs.rng(*SEED)
     A = inputs.residues(g, P, M, K)
     B = inputs.residues(g, P, K, N)
     cores = os.cpu_count() or 1
+    rows = sample_rows(args.oracle_rows)
     for _ in range(args.warmup):
-        oracle.gemm(P, A, B, threads=cores)
+        oracle.gemm_rows(P, rows, A, B, threads=cores)
     ts = []
     for _ in range(args.steps):
         t0 = time.time()
-        oracle.gemm(P, A, B, threads=cores)
+        oracle.gemm_rows(P, rows, A, B, threads=cores)
         ts.append(time.time() - t0)
     per = float(np.sum(ts)) / args.steps
-    v = FLOP / per / 1e12
-    line = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "impl": "reference", "n_gpus": world,
+    v = rows.size * 2.0 * K * N / per / 1e12
+    sample = "%d of the %d rows of the product per step (rows spread evenly)" % (rows.size, M)
+    line = {"metric": METRIC, "value": round(v, 5), "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "p": P, "m": M, "k": K, "n": N},
-            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "one full %dx%dx%d product per step" % (M, K, N)},
-            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": config_dict(),
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# DRAM bytes (read + written) of one launch of a step kernel, from an ncu
+# capture of that kernel on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum); None where no capture of the current kernel exists.
+TRAFFIC = {}
+
+KERNEL_NAMES = {"plain": "simt_gemm_kernel<PlainP>", "dp4a": "simt_gemm_kernel<Dp4aT>",
+                "dot_u64": "simt_gemm_kernel<DotU64>", "mixed_u64": "simt_gemm_kernel<MixedU64>",
+                "tc_mma_s8": "mma_s8_kernel", "tc_f16": "tc_f16_kernel<TcCfg<256, fp16>>",
+                "tc_f8": "tc_f16_kernel<TcCfg<256, e4m3>>", "tc_e2m1": "tc_e2m1_kernel"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gfp", choices=["gfp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the per-form and batched breakdowns")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
+    ap.add_argument("--oracle-rows", type=int, default=ORACLE_ROWS,
+                    help="--impl reference: rows of the product the oracle computes per step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -441,51 +566,62 @@ def main():
         torch.cuda.synchronize()
 
     # every rank runs its own replica of the workload (independent products)
-    g = inputs.rng(2, 0)
+    g = inputs.rng(*SEED)
     A_h = inputs.residues(g, P, M, K)
     B_h = inputs.residues(g, P, K, N)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
-    step = Step(gfp, torch, A, B)
+    best, _ = gfp.gfp_dot_autotune(P, M, K, N)          # untimed: word, d, Q, k-block for this shape
+    tuned = (best["word"], best["d"], best["Q"], best["kb"])
+    step = Step(gfp, torch, A, B, tuned)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
         step.run()
     torch.cuda.synchronize()
 
-    # correctness of the step's outputs (cheap check against one oracle product on rank 0)
+    # the outputs are the unique product: every form equal, and sampled rows
+    # equal to the oracle's (the tests check the full products)
     import oracle
     oracle.build()
-    ref = oracle.gemm(P, A_h, B_h, threads=os.cpu_count() or 1)
+    rows = sample_rows(16)
+    ref_rows = torch.from_numpy(oracle.gemm_rows(P, rows, A_h, B_h, threads=os.cpu_count() or 1)).cuda()
+    first = None
     for name, C in step.outs.items():
-        if not (C.cpu().numpy() == ref).all():
+        if not torch.equal(C[torch.from_numpy(rows).cuda()], ref_rows):
             raise SystemExit("bench: %s result differs from the oracle" % name)
+        if first is not None and not torch.equal(C, first):
+            raise SystemExit("bench: %s result differs from %s" % (name, next(iter(step.outs))))
+        first = C if first is None else first
 
     clocks = Clocks(local)
     clocks.start()
     barrier()
-    step_ms, dom_ms = [], []
+    step_ms = []
+    form_ms = {n: [] for n in step.forms}
+    prod_ms = {n: [] for n in step.forms}
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        d0 = torch.cuda.Event(enable_timing=True)
-        d1 = torch.cuda.Event(enable_timing=True)
+        ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(4)] for n in step.forms}
         e0.record()
-        step.run(dom_events=(d0, d1))
+        step.run(ev=ev)
         e1.record()
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        dom_ms.append(d0.elapsed_time(d1))
+        for n, e4 in ev.items():
+            form_ms[n].append(e4[0].elapsed_time(e4[3]))
+            prod_ms[n].append(e4[1].elapsed_time(e4[2]))
     barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(float(np.sum(step_ms)), device="cuda")
     ms_per_step = total_ms / args.steps
     value = world * step.products * FLOP / ms_per_step / 1e9
 
-    # end to end: pinned host inputs -> device -> all forms -> results to pinned host memory;
-    # each result is copied on a second stream as soon as its product is done
-    # (ordered by an event), overlapping the copies with the later products
+    # end to end: pinned host inputs -> device -> every form -> results to
+    # pinned host memory; each result is copied on a second stream as soon as
+    # its form is done (ordered by an event), overlapping the later forms
     A_pin = torch.from_numpy(A_h).pin_memory()
     B_pin = torch.from_numpy(B_h).pin_memory()
     outs_pin = {k: torch.empty((M, N), dtype=torch.uint8).pin_memory() for k in step.outs}
@@ -515,54 +651,67 @@ def main():
     barrier()
     e2e_per = max_over_ranks(float(np.mean(e2e_ms)), device="cuda")
     for k_, C in outs_pin.items():
-        if not (C.numpy() == ref).all():
+        if not (C.numpy()[rows] == ref_rows.cpu().numpy()).all():
             raise SystemExit("bench: end-to-end %s result differs from the oracle" % k_)
 
-    # roofline of the dominant kernel: the FP64 dot product (DFMA pipe)
-    kcf = -(-K // (step.df + 1))
-    dfma = M * N * kcf
-    dom_avg = float(np.mean(dom_ms))
-    achieved = 2.0 * dfma / dom_avg / 1e9            # TFLOP/s (FP64, 2 per fused multiply-add)
-    fp64_peak = 1.25                                   # nominal FP64 of GB300 (TFLOP/s)
-    roofline = {"kernel": "simt_gemm_kernel<DotF64> (dot form, FP64 words)", "bound": "alu",
-                "achieved": round(achieved, 4), "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": round(achieved / fp64_peak, 4), "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak in MEASURED_PEAKS.json)",
-                "traffic": DOTF64_TRAFFIC, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
-                "one launch of this kernel in this step; algorithmic operand bytes %d" % (8 * kcf * (M + N)), "launch_ms": round(dom_avg, 5),
-                "algorithmic_flops_per_launch": 2 * dfma,
-                "share_of_step": round(dom_avg / (float(np.mean(step_ms))), 3)}
+    # each form inside the step; the dominant kernel is the product launch
+    # with the largest share of the step
+    step_mean = float(np.mean(step_ms))
+    f64_peak = fp64_peak(torch) if rank == 0 else None
+    forms = {}
+    plain_ms = float(np.mean(form_ms["plain"]))
+    dp4a_ms = float(np.mean(form_ms["dp4a"]))
+    for n, (_, _, _, work, pipe, launches) in step.forms.items():
+        fm = float(np.mean(form_ms[n]))
+        pm = float(np.mean(prod_ms[n]))
+        peak, unit = PIPES[pipe] if isinstance(pipe, str) else pipe
+        r = {"ms": round(fm, 3), "value": round(FLOP / fm / 1e9, 3), "kernel_ms": round(pm, 3),
+             "speedup_vs_plain": round(plain_ms / fm, 3), "speedup_vs_dp4a": round(dp4a_ms / fm, 3),
+             "launches": launches, "share_of_step": round(fm / step_mean, 4),
+             "roofline": form_roofline(pm, work, peak=peak, unit=unit)}
+        r.update(step.dot.get(n, {}))
+        forms[n] = r
+    dom = max(step.forms, key=lambda n: np.mean(prod_ms[n]))
+    dwork, dpipe = step.forms[dom][3], step.forms[dom][4]
+    dpeak, dunit = PIPES[dpipe] if isinstance(dpipe, str) else dpipe
+    dms = float(np.mean(prod_ms[dom]))
+    tensor = dom.startswith("tc_")
+    roofline = {"kernel": KERNEL_NAMES.get(dom, dom) + " (form %s)" % dom,
+                "bound": "tensor" if tensor else "alu",
+                "achieved": round(dwork / (dms * 1e-3) / 1e12, 4), "peak": round(dpeak / 1e12, 4),
+                "unit": "TFLOP/s" if tensor else "T %s" % dunit.split(" (")[0],
+                "frac": round(dwork / (dms * 1e-3) / dpeak, 4),
+                "peak_source": dunit, "traffic": TRAFFIC.get(dom),
+                "launch_ms": round(dms, 4), "work_per_launch": dwork,
+                "share_of_step": round(dms / step_mean, 4)}
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        plain_ms = event_time(torch, lambda: gfp.gfp_gemm(P, A, B, "plain", out=step.outs["plain"]), 7, flush)
-        extras["forms"] = forms_breakdown(gfp, torch, A, B, flush, plain_ms)
+        extras["fp64_dgemm_tflops"] = round(f64_peak / 1e12, 4)
+        extras["compressed_1024"] = compressed_1024(gfp, torch, inputs, flush, f64_peak)
+        extras["tensor_core_8192"] = tensor_core_8192(gfp, torch, inputs, flush)
         try:
-            extras["batched"] = batched_measure(gfp, torch, flush)
+            extras["batched"] = batched_measure(gfp, torch, inputs, flush)
         except gfp.GfpError as e:
             extras["batched"] = {"unavailable": str(e)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample, _ = cpu_oracle_rate(A_h, B_h)
+        v, cores, sample = cpu_oracle_rate(A_h, B_h)
         cpu = {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         peaks = measured_peaks()
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/u32/u64/f64/f16",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "p": P, "m": M, "k": K, "n": N,
-                           "products_per_step": step.products,
-                           "l2": "256 MiB buffer written between timed steps (flush)",
-                           "replicas": world},
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u8/u32/u64/f16/e4m3/s8", "data": "synthetic", "config": config_dict(),
+                "products_per_step": step.products, "replicas": world,
                 "e2e": {"value": round(world * step.products * FLOP / e2e_per / 1e9, 3), "unit": UNIT,
-                        "ms_per_step": round(e2e_per, 5),
+                        "ms_per_step": round(e2e_per, 3),
                         "h2d_bytes_per_step": 2 * M * K, "d2h_bytes_per_step": step.products * M * N},
-                "gpu_launches": Step.LAUNCHES * args.steps,
-                "roofline": roofline,
-                "clocks": clk,
-                "cpu_baseline": cpu,
+                "gpu_launches": step.launches * args.steps,
+                "roofline": roofline, "forms": forms, "clocks": clk, "cpu_baseline": cpu,
                 "measured_peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}}
         line.update(extras)
         print(json.dumps(line), flush=True)

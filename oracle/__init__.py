@@ -11,7 +11,8 @@ Multiplication" (arXiv 0803.1975).
 Contents, each written from the cited passage:
 
 * `gemm`, `gemm_rows`: the definition C = A B mod p, as a plain C triple loop
-  (gfp_oracle.c).  Every form of the paper must reach this result exactly
+  (gfp_oracle.c); `gemm_matmul`, the same definition with the sum formed by a
+  library matrix product in exact binary64 arithmetic, for the largest sizes.  Every form of the paper must reach this result exactly
   (Section 2.2: the compressed product recovers the same dot products).
 * `pack_rows_rev`, `pack_cols`, `pack_rows` and their inverses: the Q-adic
   words of Section 2.1 (reversed rows of A, forward columns of B), the zero
@@ -115,6 +116,22 @@ def gemm_rows(p: int, rows, A: np.ndarray, B: np.ndarray, threads: int = 1) -> n
                                       k, n, _u8(A), max(k, 1), _u8(B), max(n, 1), _u8(out),
                                       max(n, 1), threads)
     return out
+
+
+def gemm_matmul(p: int, A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """The same definition with the sum formed by a library matrix product in
+    binary64: every product A[i][l] B[l][j] and every partial sum is an
+    integer below k (p-1)^2 + 1, so while k (p-1)^2 < 2^53 each one is exact
+    in any order of summation, and C = (A B) mod p exactly.  It serves the
+    sizes the triple loop cannot finish (8192^3 and beyond); the tests pin it
+    to `gemm` and `gemm_rows`.  Raises where the bound fails."""
+    _check_operands(p, A, B)
+    m, k = A.shape
+    n = B.shape[1]
+    if k * (p - 1) ** 2 >= 2 ** 53:
+        raise ValueError("k (p-1)^2 >= 2^53: binary64 sums would not be exact")
+    S = np.matmul(A.astype(np.float64), B.astype(np.float64))
+    return np.fmod(S, float(p)).astype(np.uint8).reshape(m, n)
 
 
 # --------------------------------------------------------------------------

@@ -1,19 +1,22 @@
 """GPU parity at the full sizes of the workloads, in the launch configurations
-the benchmark uses: sampled rows against the oracle (which computes them one
-by one) and Freivalds' test on the whole product (a property of any correct
-product, independent of how it was computed).
+the benchmark uses, element by element against the oracle's full product.
+
+The full products come from `oracle.gemm_matmul` (the definition with the
+sum formed by a binary64 matrix product, exact while k (p-1)^2 < 2^53); at
+each full size a few rows of the plain triple loop (`oracle.gemm_rows`) pin
+that product too, so that the comparison rests on two independent forms of
+the definition.
 
 - tensor-core forms, p in {3, 31, 251}, m = k = n = 8192, and ragged sizes
   over the 256-column tiles;
 - every form, p = 5, m = k = n = 16384."""
 import numpy as np
 import pytest
-import torch
 
 import oracle
 from paper_0803_1975_gb300 import gfp, inputs
 
-from helpers import THREADS, dev, ensure_built, freivalds, host
+from helpers import THREADS, dev, ensure_built, host
 
 pytestmark = pytest.mark.gpu
 
@@ -23,9 +26,24 @@ def _built():
     ensure_built()
 
 
-def check(p, A, B, C, rows, rounds=2):
-    assert (C[rows] == oracle.gemm_rows(p, rows, A, B, threads=THREADS)).all()
-    assert freivalds(p, A, B, C, rounds=rounds)
+def full_oracle(p, A, B, pin_rows):
+    """The oracle's whole product, with rows `pin_rows` of it checked against
+    the triple loop."""
+    C = oracle.gemm_matmul(p, A, B)
+    assert (C[pin_rows] == oracle.gemm_rows(p, pin_rows, A, B, threads=THREADS)).all()
+    return C
+
+
+def assert_equal(name, got, ref):
+    if not np.array_equal(got, ref):
+        bad = np.argwhere(got != ref)
+        raise AssertionError("%s: %d entries differ from the oracle, first at %s (got %d, want %d)"
+                             % (name, len(bad), tuple(bad[0]), got[tuple(bad[0])], ref[tuple(bad[0])]))
+
+
+def tc_algos(p):
+    return [a for a in ("tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1")
+            if a in gfp.ALGOS and {"tc_e2m1": p <= 7, "tc_f8": p <= 31}.get(a, True)]
 
 
 @pytest.mark.parametrize("p", [3, 31, 251])
@@ -34,12 +52,10 @@ def test_tc_8192(p):
     g = inputs.rng(3, p)
     A = inputs.residues(g, p, n, n)
     B = inputs.residues(g, p, n, n)
+    ref = full_oracle(p, A, B, [0, 4097, 8191])
     Ad, Bd = dev(A), dev(B)
-    rows = [0, 1, 127, 128, 4095, 8191]
-    for algo in ("tc_f16", "tc_mma_s8") + (("tc_f8",) if p <= 31 else ()):
-        C = host(gfp.gfp_gemm(p, Ad, Bd, algo))
-        check(p, A, B, C, rows)
-        del C
+    for algo in tc_algos(p):
+        assert_equal(algo, host(gfp.gfp_gemm(p, Ad, Bd, algo)), ref)
 
 
 @pytest.mark.parametrize("p", [7, 31, 251])
@@ -51,46 +67,31 @@ def test_tc_ragged_256_column_tiles(p):
     g = inputs.rng(3, 100 + p)
     A = inputs.residues(g, p, m, k)
     B = inputs.residues(g, p, k, n)
+    ref = full_oracle(p, A, B, [0, 128, m - 1])
     Ad, Bd = dev(A), dev(B)
-    rows = [0, 127, 128, 255, 256, 4095, 4096, m - 2, m - 1]
-    for algo in ("tc_f16",) + (("tc_f8",) if p <= 31 else ()):
-        C = host(gfp.gfp_gemm(p, Ad, Bd, algo))
-        check(p, A, B, C, rows, rounds=3)
+    for algo in tc_algos(p):
+        assert_equal(algo, host(gfp.gfp_gemm(p, Ad, Bd, algo)), ref)
 
 
-@pytest.fixture(scope="module")
-def big5():
-    n = 16384
-    g = inputs.rng(5, 0)
-    A = inputs.residues(g, 5, n, n)
-    B = inputs.residues(g, 5, n, n)
-    return A, B
-
-
-def test_all_forms_16384(big5):
+def test_all_forms_16384():
+    """p = 5, m = k = n = 16384: every form of the benchmark's step, each
+    compared entry by entry with the oracle's product."""
     p, n = 5, 16384
-    A, B = big5
+    g = inputs.rng(5, 0)
+    A = inputs.residues(g, p, n, n)
+    B = inputs.residues(g, p, n, n)
+    ref = full_oracle(p, A, B, [0, 5000, 16383])
     Ad, Bd = dev(A), dev(B)
-    rows = [0, 5000, 16383]
-    results = {}
-    for algo in ("plain", "tc_f16", "tc_f8", "tc_mma_s8"):
-        results[algo] = host(gfp.gfp_gemm(p, Ad, Bd, algo))
-    d, Q, _ = gfp.gfp_params(p, n, n, n, "dot", "u64")
-    CA = gfp.gfp_pack(p, Ad, d, Q, "rows_rev", "u64")
-    CB = gfp.gfp_pack(p, Bd, d, Q, "cols", "u64")
-    results["dot_u64"] = host(gfp.gfp_gemm_compressed(p, n, n, n, d, Q, "dot", "u64", CA, CB))
-    del CA, CB
+    for algo in ("plain", "dp4a") + tuple(tc_algos(p)):
+        assert_equal(algo, host(gfp.gfp_gemm(p, Ad, Bd, algo)), ref)
+    best, _ = gfp.gfp_dot_autotune(p, n, n, n)
+    for name, (word, d, Q, kb) in (("dot_u64", ("u64",) + gfp.gfp_params(p, n, n, n, "dot", "u64")),
+                                   ("dot_tuned", (best["word"], best["d"], best["Q"], best["kb"]))):
+        CA = gfp.gfp_pack(p, Ad, d, Q, "rows_rev", word)
+        CB = gfp.gfp_pack(p, Bd, d, Q, "cols", word)
+        assert_equal(name, host(gfp.gfp_gemm_compressed(p, n, n, n, d, Q, "dot", word, CA, CB, kb=kb)), ref)
+        del CA, CB
     d, Q, _ = gfp.gfp_params(p, n, n, n, "mixed", "u64")
     CB = gfp.gfp_pack(p, Bd, d, Q, "rows", "u64")
     CC = gfp.gfp_gemm_compressed(p, n, n, n, d, Q, "mixed", "u64", Ad, CB)
-    results["mixed_u64"] = host(gfp.gfp_unpack(p, CC, n, n, d, Q, "rows", "u64"))
-    del CB, CC
-    ref_rows = oracle.gemm_rows(p, rows, A, B, threads=THREADS)
-    first = None
-    for name, C in results.items():
-        assert (C[rows] == ref_rows).all(), name
-        if first is None:
-            assert freivalds(p, A, B, C, rounds=2), name
-            first = C
-        else:
-            assert (C == first).all(), name       # every form gives the same unique product
+    assert_equal("mixed_u64", host(gfp.gfp_unpack(p, CC, n, n, d, Q, "rows", "u64")), ref)

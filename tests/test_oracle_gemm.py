@@ -123,3 +123,55 @@ def test_planted_mistake_is_caught():
     B = inputs.residues(g, 3, 9, 8)
     wrong = (A[:, :-1].astype(np.int64) @ B[:-1].astype(np.int64)) % 3
     assert not (oracle.gemm(3, A, B) == wrong).all()
+
+
+# ---------------------------------------------------------------------------
+# gemm_matmul: the definition with the sum formed by a binary64 matrix product
+# ---------------------------------------------------------------------------
+def test_matmul_form_worked_example_2x2_exhaustive_mod3():
+    """Section 2.2's 2x2 example over all 3^8 instances, as for the triple loop."""
+    ex = load_examples()
+    for vals in itertools.product(range(3), repeat=8):
+        env = dict(zip("abcdefgh", vals))
+        a = np.asarray(eval(ex["A"], {}, env), np.uint8)
+        b = np.asarray(eval(ex["B"], {}, env), np.uint8)
+        c = np.asarray(eval(ex["C"], {}, env)) % 3
+        assert (oracle.gemm_matmul(3, a, b) == c).all()
+
+
+@pytest.mark.parametrize("p,m,k,n", [(3, 17, 33, 9), (5, 64, 100, 31), (251, 20, 3000, 40),
+                                      (2, 5, 1, 7), (7, 1, 129, 1), (31, 133, 640, 65)])
+def test_matmul_form_matches_triple_loop(p, m, k, n):
+    g = inputs.rng(95, p + m + k + n)
+    A = inputs.residues(g, p, m, k)
+    B = inputs.residues(g, p, k, n)
+    assert (oracle.gemm_matmul(p, A, B) == oracle.gemm(p, A, B, threads=4)).all()
+
+
+def test_matmul_form_largest_sums_exact():
+    """All entries p - 1 = 250 with k = 8192: every dot product is
+    8192 * 250^2 = 512,000,000; its residue is computed with Python integers."""
+    p, k = 251, 8192
+    A = np.full((3, k), p - 1, np.uint8)
+    B = np.full((k, 5), p - 1, np.uint8)
+    assert (oracle.gemm_matmul(p, A, B) == (k * (p - 1) ** 2) % p).all()
+    assert (oracle.gemm_rows(p, [0, 2], A, B) == (k * (p - 1) ** 2) % p).all()
+
+
+def test_matmul_form_rejects_inexact_sizes():
+    """k (p-1)^2 >= 2^53 is refused (zero-sized operands: nothing is allocated)."""
+    k = -(-2 ** 53 // 250 ** 2)
+    with pytest.raises(ValueError):
+        oracle.gemm_matmul(251, np.zeros((0, k), np.uint8), np.zeros((k, 0), np.uint8))
+    k -= 1
+    assert oracle.gemm_matmul(251, np.zeros((0, k), np.uint8), np.zeros((k, 0), np.uint8)).shape == (0, 0)
+
+
+def test_matmul_form_planted_mistake_is_caught():
+    """A dropped term changes the matmul form's result; the comparison with
+    the triple loop sees it."""
+    g = inputs.rng(96, 0)
+    A = inputs.residues(g, 5, 30, 40)
+    B = inputs.residues(g, 5, 40, 20)
+    wrong = oracle.gemm_matmul(5, A[:, :-1], B[:-1])
+    assert not (wrong == oracle.gemm(5, A, B)).all()
