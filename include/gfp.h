@@ -134,6 +134,15 @@ typedef enum gfp_layout {
  *                        (kind::f8f6f4), which hold the centred residues of
  *                        p <= 31 exactly (|c| <= 15); twice the fp16 rate.
  *                        GFP_EUNSUPPORTED for p > 31.  Same status word.
+ *  GFP_ALGO_TC_E2M1    : as GFP_ALGO_TC_F16 with fp4 e2m1 operands on the
+ *                        block-scaled tcgen05 MMA (kind::mxf4, every scale
+ *                        factor 1), which hold the centred residues of p <= 7
+ *                        exactly (|c| <= 3): products are integers of
+ *                        magnitude <= 9 and the k-block is the largest kb
+ *                        with kb ((p-1)/2)^2 + p < 2^24 (a multiple of 256).
+ *                        The workspace holds both operands packed two values
+ *                        per byte.  GFP_EUNSUPPORTED for p > 7.  Same status
+ *                        word.
  *  GFP_ALGO_AUTO       : GFP_ALGO_TC_F8 for p <= 31, else GFP_ALGO_TC_F16 (the
  *                        fastest exact forms measured on GB300). */
 typedef enum gfp_algo {
@@ -143,7 +152,8 @@ typedef enum gfp_algo {
     GFP_ALGO_TC_MMA_S8 = 3,
     GFP_ALGO_TC_F16 = 4,
     GFP_ALGO_DOT32 = 5,     /* batched only: Q-adic dot form in 32-bit words */
-    GFP_ALGO_TC_F8 = 6
+    GFP_ALGO_TC_F8 = 6,
+    GFP_ALGO_TC_E2M1 = 7
 } gfp_algo;
 
 /* ------------------------------------------------------------------------ */

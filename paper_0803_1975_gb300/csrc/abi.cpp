@@ -99,6 +99,10 @@ static gfp_status resolve_algo(uint32_t p, int64_t m, int64_t k, int64_t n, gfp_
             if (p > 31) return GFP_EUNSUPPORTED;
             *out = algo;
             return GFP_OK;
+        case GFP_ALGO_TC_E2M1:
+            if (p > 7) return GFP_EUNSUPPORTED;
+            *out = algo;
+            return GFP_OK;
         case GFP_ALGO_AUTO: {
             // Measured on GB300: tcgen05 with fp8 operands (p <= 31) or fp16
             // operands is the fastest exact form at every size worth a launch.
@@ -122,6 +126,7 @@ GFP_API gfp_status gfp_gemm_workspace_size(uint32_t p, int64_t m, int64_t k, int
     if (a == GFP_ALGO_TC_MMA_S8) *bytes = tc_mma_workspace(m, k, n);
     if (a == GFP_ALGO_TC_F16) *bytes = tc_f16_workspace(m, k, n);
     if (a == GFP_ALGO_TC_F8) *bytes = tc_f8_workspace(m, k, n);
+    if (a == GFP_ALGO_TC_E2M1) *bytes = tc_e2m1_workspace(m, k, n);
     return GFP_OK;
 }
 
@@ -152,6 +157,7 @@ GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n, const u
     }
     const size_t need = a == GFP_ALGO_TC_MMA_S8 ? tc_mma_workspace(m, k, n)
                         : a == GFP_ALGO_TC_F8   ? tc_f8_workspace(m, k, n)
+                        : a == GFP_ALGO_TC_E2M1 ? tc_e2m1_workspace(m, k, n)
                                                 : tc_f16_workspace(m, k, n);
     if (need > 0 && (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255)))
         return GFP_EWORKSPACE;
@@ -159,6 +165,8 @@ GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n, const u
         return launch_tc_mma(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
     if (a == GFP_ALGO_TC_F8)
         return launch_tc_f8(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
+    if (a == GFP_ALGO_TC_E2M1)
+        return launch_tc_e2m1(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
     return launch_tc_f16(p, m, k, n, A, lda, B, ldb, C, ldc, workspace, ws_bytes, s);
 }
 

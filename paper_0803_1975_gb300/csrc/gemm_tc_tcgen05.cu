@@ -45,15 +45,20 @@ constexpr int BM = 128;
 constexpr int ROWB = 128;                               // bytes of k per operand row per stage
 constexpr int NTHREADS = 192;
 
-template <int BN_, bool FP8_, int STAGES_ = 4>
+template <int BN_, bool FP8_, int STAGES_ = 4, bool FP4_ = false>
 struct TcCfg {
     static constexpr int BN = BN_;
     static constexpr bool FP8 = FP8_;
+    static constexpr bool FP4 = FP4_;                  // packed e2m1 operands, block-scaled MMA
     static constexpr int STAGES = STAGES_;
-    static constexpr int BKE = FP8 ? 128 : 64;         // k elements per stage
+    static constexpr int BKE = FP4 ? 256 : FP8 ? 128 : 64;   // k elements per stage
     static constexpr int A_BYTES = BM * ROWB, B_BYTES = BN * ROWB;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // multiple of 1024
-    static constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulators
+    // two accumulators; the e2m1 form also keeps its unit scale factors in
+    // tensor memory, columns SF_COL .. 511 (A's from SF_COL, B's 64 further)
+    static constexpr uint32_t TMEM_COLS = FP4 ? 512 : 2 * BN;
+    static constexpr uint32_t SF_COL = 2 * BN;
+    static_assert(!FP4 || 2 * BN + 128 <= 512, "e2m1 tiles leave 128 columns for the scale factors");
     // [stages][barriers, 1 KB][store staging of the 4 epilogue warps][alignment slack]
     static constexpr int STG_BYTES = 4 * 32 * 9 * 4;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + STG_BYTES + 1024;
@@ -64,7 +69,12 @@ struct TcCfg {
     // fp32 accumulator (bits 4-5 = 1), A and B types 0 (fp16, resp. e4m3) in
     // bits 7-9 and 10-12, both K-major (bits 15, 16 = 0), N >> 3 in bits
     // 17-22, M >> 4 in bits 24-28.
-    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    // The block-scaled kind::mxf4 descriptor: A and B e2m1 (type 1 in bits
+    // 7-9 and 10-11), scale factors ue8m0 (bit 23), scale-factor byte 0 of A
+    // and B (bits 29-30, 4-5), dense K = 64 (bit 31 = 0), N and M as above.
+    static constexpr uint32_t IDESC =
+        FP4 ? (1u << 7) | (1u << 10) | (1u << 23) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24)
+            : (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;   // 4 s: the default bound of every wait
 
@@ -143,10 +153,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;
 }
 
-template <bool FP8>
+// KIND 0: kind::f16; 1: kind::f8f6f4; 2: kind::mxf4 with scale factors
+// (ue8m0, one per 32 values of k) read from tensor memory at sfa, sfb.
+template <int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accum) {
-    if constexpr (FP8)
+                                          uint32_t accum, uint32_t sfa = 0, uint32_t sfb = 0) {
+    if constexpr (KIND == 2)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum), "r"(sfa), "r"(sfb)
+            : "memory");
+    else if constexpr (KIND == 1)
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
@@ -382,6 +400,24 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
+    if constexpr (CFG::FP4) {
+        // unit scale factors (ue8m0 127 = 2^0 in every byte) in columns
+        // SF_COL .. 511, written once by the epilogue warps, each to its lanes;
+        // every scale factor is 1, so the MMA reads 1 wherever it looks there
+        if (warp >= 2) {
+            const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+            for (uint32_t c = CFG::SF_COL; c < 512; c += 8)
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+                        tmem + lanes + c),
+                    "r"(0x7F7F7F7Fu)
+                    : "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        fence_before();
+        __syncthreads();
+        fence_after();
+    }
 
     if (warp == 0) {
         if (lane == 0) {
@@ -479,8 +515,9 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             // grouped tiles pick the kind per problem: fp16 operands carry
                             // scale 1, raw e4m3 ones 2^18 (the instruction descriptor is the
                             // same: type fields 0 are f16 and e4m3)
-                            if (GROUPED && ti.scale == 1.0f) mma_issue<false>(d, da, db, CFG::IDESC, acc);
-                            else mma_issue<CFG::FP8>(d, da, db, CFG::IDESC, acc);
+                            if (GROUPED && ti.scale == 1.0f) mma_issue<0>(d, da, db, CFG::IDESC, acc);
+                            else mma_issue<CFG::FP4 ? 2 : CFG::FP8 ? 1 : 0>(d, da, db, CFG::IDESC, acc,
+                                                                          tmem + CFG::SF_COL, tmem + CFG::SF_COL + 64);
                         }
                         mma_commit(empty_bar(stage));
                         if (++stage == STAGES) {
@@ -734,6 +771,67 @@ __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ld
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// e2m1 code of a centred residue |c| <= 3, exact: 0, 1, 2, 3 are the codes
+// 0x0, 0x2, 0x4, 0x5 (1 = 2^0 x 1.0, 2 = 2^1 x 1.0, 3 = 2^1 x 1.5), bit 3
+// the sign.
+__device__ __forceinline__ uint32_t e2m1_code(int c) {
+    const uint32_t a = (uint32_t)(c < 0 ? -c : c);
+    return (a == 3u ? 5u : 2u * a) | (c < 0 ? 8u : 0u);
+}
+
+// Packed e2m1 operands, two values per byte (value 2e in the low nibble of
+// byte e, 2e + 1 in the high one), rows of kp / 2 bytes.
+// out[i][l] = code(centre(A[i][l])) for i < m, l < k; zero elsewhere in mp x kp.
+// One thread per 32 consecutive values of a row.
+__global__ void to_e2m1_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m, int64_t k,
+                                    uint8_t *__restrict__ out, int64_t kp, int64_t mp, uint32_t p, uint32_t h) {
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 32;
+    if (l >= kp) return;
+    for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
+        uint32_t r0[16], r1[16];
+        load16(A + i * lda + l, l, k, i < m, r0);
+        load16(A + i * lda + l + 16, l + 16, k, i < m, r1);
+        uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            w[e >> 3] |= e2m1_code(centre_i(r0[e], p, h)) << (4 * (e & 7));
+            w[2 + (e >> 3)] |= e2m1_code(centre_i(r1[e], p, h)) << (4 * (e & 7));
+        }
+        *reinterpret_cast<uint4 *>(out + i * (kp / 2) + l / 2) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// out[j][l] = code(centre(B[l][j])) for l < k, j < n; zero elsewhere in np x kp.
+// 64 x 64 tiles through shared memory as in to_op_transpose_kernel; each
+// thread writes 16 values (8 bytes) of one row of B^T.
+__global__ void to_e2m1_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k, int64_t n,
+                                         uint8_t *__restrict__ out, int64_t kp, int64_t np, uint32_t p,
+                                         uint32_t h) {
+    __shared__ uint8_t tile[64][64 + 4];
+    const int64_t l0 = (int64_t)blockIdx.x * 64;
+    const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
+    for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
+        const int64_t j0 = jt * 64;
+        {
+            const int64_t l = l0 + r;
+            uint32_t v[16];
+            load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) tile[r][q + e] = (uint8_t)e2m1_code(centre_i(v[e], p, h));
+        }
+        __syncthreads();
+        const int64_t j = j0 + r;
+        if (j < np) {
+            uint32_t w[2] = {0, 0};
+#pragma unroll
+            for (int e = 0; e < 16; ++e) w[e >> 3] |= (uint32_t)tile[q + e][r] << (4 * (e & 7));
+            *reinterpret_cast<uint2 *>(out + j * (kp / 2) + (l0 + q) / 2) = make_uint2(w[0], w[1]);
+        }
+        __syncthreads();   // the tile is refilled by the next iteration
+    }
+}
+
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -976,6 +1074,81 @@ gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8
                         size_t ws_bytes, cudaStream_t s) {
     if (p > 31) return GFP_EUNSUPPORTED;   // |c| <= 15 is what e4m3 holds exactly
     return launch_tc(p, m, k, n, A, lda, B, ldb, C, ldc, ws, ws_bytes, s, true);
+}
+
+// ---- e2m1 operands on the block-scaled tensor-core MMA (kind::mxf4)
+//
+// For p <= 7 the centred residues |c| <= 3 are e2m1 values exactly, and with
+// every scale factor 1 (ue8m0 code 127) the block-scaled MMA multiplies them
+// as they are: products are integers of magnitude <= 9 and each k-block sum
+// stays an integer below 2^24 in the fp32 accumulator (kb 9 + p < 2^24), as
+// for the fp16 and e4m3 forms.  Tiles of 128 x 192 outputs: two accumulators
+// of 192 columns and the scale factors fill the 512 columns of tensor memory.
+using TcE2m1Cfg = TcCfg<192, true, 5, true>;
+constexpr int E2M1_BKE = 256;              // k values per 128-byte stage row
+
+// largest multiple of 256 with kb h^2 + p < 2^24
+int64_t tc_kblock_e2m1(uint32_t p) {
+    const int64_t h = p == 2 ? 1 : (p - 1) / 2;
+    return ((int64_t(1) << 24) - 1 - p) / (h * h) / E2M1_BKE * E2M1_BKE;
+}
+
+// workspace: [status word, 256 B][A: mp x kp/2 bytes][B^T: np x kp/2 bytes]
+size_t tc_e2m1_workspace(int64_t m, int64_t k, int64_t n) {
+    const int64_t kp = round_up(k > 0 ? k : 1, E2M1_BKE);
+    return 256 + (size_t)(round_up(m, BM) + round_up(n, 256)) * (size_t)(kp / 2);
+}
+
+gfp_status launch_tc_e2m1(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
+                          const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,
+                          size_t ws_bytes, cudaStream_t s) {
+    if (p > 7) return GFP_EUNSUPPORTED;    // |c| <= 3 is what e2m1 holds exactly
+    constexpr int BN = TcE2m1Cfg::BN;
+    const int64_t kp = round_up(k, E2M1_BKE), mp = round_up(m, BM), np = round_up(n, 256);
+    const int64_t rowb = kp / 2;
+    if (tc_e2m1_workspace(m, k, n) > ws_bytes) return GFP_EWORKSPACE;
+    if (mp / BM > (int64_t)1 << 30 || (n + BN - 1) / BN > (int64_t)1 << 30 || kp / E2M1_BKE > (int64_t)1 << 30)
+        return GFP_EINVAL;
+    int *status = static_cast<int *>(ws);
+    uint8_t *Aop = static_cast<uint8_t *>(ws) + 256;
+    uint8_t *Bop = Aop + mp * rowb;
+    const uint32_t h = p == 2 ? 1u : (p - 1) / 2;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    {
+        dim3 grid((unsigned)((kp / 32 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
+        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
+        to_e2m1_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, p, h);
+        to_e2m1_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Aop, mp, rowb, BM, true) || !make_map(&mb, Bop, np, rowb, BN, true))
+        return GFP_EUNSUPPORTED;
+    TcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.C = C;
+    g.ldc = ldc;
+    g.m = m;
+    g.n = n;
+    g.tiles_m = (int)(mp / BM);
+    g.tiles_n = (int)((n + BN - 1) / BN);
+    g.ktiles = (int)(kp / E2M1_BKE);
+    g.kb_tiles = (int)(tc_kblock_e2m1(p) / E2M1_BKE);
+    if (g.kb_tiles < 1) g.kb_tiles = 1;
+    g.kblocks = (g.ktiles + g.kb_tiles - 1) / g.kb_tiles;
+    g.p = p;
+    g.off = (uint32_t)((((int64_t)1 << 24) + p - 1) / p * p);
+    g.m32 = (uint32_t)(0xFFFFFFFFull / p + 1);
+    g.red = 0;
+    g.scale = 1.0f;
+    g.status = status;
+    g.limit_ns = WAIT_LIMIT_NS;
+    g.stall = 0;
+    const int tiles = g.tiles_m * g.tiles_n;
+    const int grid = tiles < num_sms() ? tiles : num_sms();
+    if (g.kblocks > 1) launch_cfg<TcE2m1Cfg, true>(ma, mb, g, grid, s);
+    else launch_cfg<TcE2m1Cfg, false>(ma, mb, g, grid, s);
+    return check_launch();
 }
 
 }  // namespace gfp

@@ -25,7 +25,7 @@ STATUS = {0: "GFP_OK", 1: "GFP_EINVAL", 2: "GFP_EPRIME", 3: "GFP_EBOUND", 4: "GF
 FORMS = {"dot": 0, "mixed": 1, "left": 2}
 WORDS = {"u64": 0, "u64x128": 1, "u32w": 2, "u32": 3, "f64": 4}
 LAYOUTS = {"rows_rev": 0, "cols": 1, "rows": 2}
-ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4, "dot32": 5, "tc_f8": 6}
+ALGOS = {"auto": 0, "plain": 1, "dp4a": 2, "tc_mma_s8": 3, "tc_f16": 4, "dot32": 5, "tc_f8": 6, "tc_e2m1": 7}
 BATCHED_KINDS = {0: "hmma64", 1: "hmma32", 2: "dot32", 3: "hmma128", 4: "tcgen05"}
 WORD_DTYPE = {"u64": torch.int64, "u64x128": torch.int64, "u32w": torch.int32, "u32": torch.int32,
               "f64": torch.float64}
