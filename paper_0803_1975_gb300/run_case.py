@@ -4,7 +4,7 @@ time (CUDA events, L2 flushed between repetitions) and effective 2mnk/s.
     python -m paper_0803_1975_gb300.run_case --form tc_f16 --p 3 --size 8192 --reps 3
     python -m paper_0803_1975_gb300.run_case --form dot --word u32 --kb 60 --size 1024
 
-Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8 (gfp_gemm); dot, mixed, left
+Forms: plain, dp4a, tc_mma_s8, tc_f16, tc_f8, tc_e2m1 (gfp_gemm); dot, mixed, left
 (gfp_gemm_compressed, after packing); full (gfp_gemm_full, 64-bit words); winograd (the 64-bit dot form with
 --levels of Strassen-Winograd on the words); batched (the 4096-problem adjacency
 workload, one prepared launch); pack_rows_rev, pack_cols, pack_rows,
@@ -50,7 +50,7 @@ def main():
     A = torch.from_numpy(inputs.residues(g, p, m, k)).cuda()
     B = torch.from_numpy(inputs.residues(g, p, k, n)).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    if a.form in ("plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8"):
+    if a.form in ("plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1"):
         ws = torch.empty(max(1, gfp.gfp_gemm_workspace_size(p, m, k, n, a.form)), dtype=torch.uint8,
                          device="cuda")
         C = torch.empty((m, n), dtype=torch.uint8, device="cuda")

@@ -213,3 +213,18 @@ def test_value_aware_chooser_and_validator_match_oracle(L):
         with pytest.raises(gfp.GfpError) as e:
             gfp.gfp_params_vb(5, 8, 1000, 8, a, b)
         assert e.value.status == 1
+
+
+def test_e2m1_workspace_and_prime_limit(L):
+    # both operands packed two values per byte, k padded to 256, after 256 bytes
+    assert gfp.gfp_gemm_workspace_size(7, 100, 70, 200, "tc_e2m1") == 256 + (128 + 256) * 128
+    assert gfp.gfp_gemm_workspace_size(2, 129, 300, 257, "tc_e2m1") == 256 + (256 + 512) * 256
+    # e2m1 holds the centred residues of p <= 7 only: rejected before any launch
+    a = ctypes.c_void_p(0x1000)
+    for p in (11, 13, 31, 251):
+        with pytest.raises(gfp.GfpError) as e:
+            gfp.gfp_gemm_workspace_size(p, 8, 8, 8, "tc_e2m1")
+        assert e.value.status == 5
+        assert L.gfp_gemm(p, 8, 8, 8, a, 8, a, 8, a, 8, gfp.ALGOS["tc_e2m1"], a, 1 << 20, None) == 5
+    # without its workspace
+    assert L.gfp_gemm(5, 64, 64, 64, a, 64, a, 64, a, 64, gfp.ALGOS["tc_e2m1"], None, 0, None) == 7

@@ -107,7 +107,7 @@ def test_dp4a_aligned_rows_with_a_partial_last_group():
     assert (host(C) == oracle.gemm(p, np.ascontiguousarray(wide[:, :k]), B, threads=THREADS)).all()
 
 
-@pytest.mark.parametrize("algo", ["dp4a", "tc_mma_s8", "tc_f16", "tc_f8"])
+@pytest.mark.parametrize("algo", ["dp4a", "tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1"])
 def test_wider_than_the_grid_limit(algo):
     """n = 4,300,000 columns: more 64-column tiles of B^T (67,188) than a grid's y
     dimension holds (65,535); the operand transposes loop over them."""
@@ -151,15 +151,16 @@ GEMM_CASES = [(3, 256, 256, 256), (3, 1024, 1024, 1024), (5, 129, 300, 77), (251
               (2, 65, 64, 63), (7, 1, 1, 1), (31, 3, 1000, 5), (13, 128, 17, 128), (3, 300, 1, 299)]
 
 
-ALGOS = ["plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8"]
+ALGOS = ["plain", "dp4a", "tc_mma_s8", "tc_f16", "tc_f8", "tc_e2m1"]
 
 
 def skip_unsupported(algo, p):
-    if algo == "tc_f8" and p > 31:
+    limit = {"tc_f8": 31, "tc_e2m1": 7}.get(algo)
+    if limit is not None and p > limit:
         with pytest.raises(gfp.GfpError) as e:
             gfp.gfp_gemm_workspace_size(p, 8, 8, 8, algo)
         assert e.value.status == 5
-        pytest.skip("fp8 operands hold the centred residues of p <= 31 only")
+        pytest.skip("%s operands hold the centred residues of p <= %d only" % (algo, limit))
 
 
 @pytest.mark.parametrize("algo", ALGOS)
@@ -172,7 +173,7 @@ def test_gemm_matches_oracle(algo, p, m, k, n):
 
 
 @pytest.mark.parametrize("algo", ALGOS)
-@pytest.mark.parametrize("p", [3, 31, 251])
+@pytest.mark.parametrize("p", [3, 7, 31, 251])
 def test_gemm_worst_case(algo, p):
     """All entries p-1 (largest sums); for the centred form also the largest
     centred magnitude h = (p-1)/2 with both signs."""
@@ -235,6 +236,43 @@ def test_tc_exact_accumulation(algo, p):
         C = host(gfp.gfp_gemm(p, dev(A), dev(B), algo, workspace=ws))
         assert tc_f16_status(ws) == 0
         assert (C == oracle.gemm(p, A[:2], B)[0]).all(), name   # rows are identical
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7])
+def test_tc_e2m1_exact_accumulation(p):
+    """The block-scaled e2m1 MMA (unit scale factors) with fp32 accumulation at
+    its k-block bound kb (kb h^2 + p < 2^24; h = 3 at p = 7: kb = 1,864,192):
+    all products +h^2 (the sums reach kb h^2 ~ 2^24), products of both signs,
+    a large accumulator followed by small addends, and one k-block and a
+    ragged tail past the bound (the blocked path).  Every row and every column
+    of each pattern is the same, so one oracle dot product is the expected
+    value of all of C."""
+    h = 1 if p == 2 else (p - 1) // 2
+    kb = ((1 << 24) - 1 - p) // (h * h) // 256 * 256
+    k = min(kb, 1 << 21)
+    m, n = 128, 192
+    pos, neg = h, (p - h if p > 2 else 1)      # centred +h and -h (p = 2: 0/1 only)
+    pats = {
+        "all+": (np.full((m, k), pos, np.uint8), np.full((k, n), pos, np.uint8)),
+        "all-+": (np.full((m, k), neg, np.uint8), np.full((k, n), pos, np.uint8)),
+        "alt": (np.full((m, k), pos, np.uint8),
+                np.where((np.arange(k) % 2)[:, None] == 0, pos, neg).astype(np.uint8).repeat(n, 1)),
+    }
+    big_then_small = np.full((m, k), pos, np.uint8)
+    big_then_small[:, k // 2:] = 1
+    pats["big-then-small"] = (big_then_small, np.full((k, n), pos, np.uint8))
+    if kb <= 1 << 21:                          # p = 7: the bound itself is in reach
+        k2 = kb + 300
+        pats["past-the-block"] = (np.full((m, k2), pos, np.uint8), np.full((k2, n), pos, np.uint8))
+    for name, (A, B) in pats.items():
+        mk, kk = A.shape
+        ws = torch.empty(gfp.gfp_gemm_workspace_size(p, mk, kk, n, "tc_e2m1"), dtype=torch.uint8,
+                         device="cuda")
+        C = host(gfp.gfp_gemm(p, dev(A), dev(B), "tc_e2m1", workspace=ws))
+        assert tc_f16_status(ws) == 0
+        want = oracle.gemm(p, A[:1], np.ascontiguousarray(B[:, :1]))[0, 0]
+        assert (C == want).all(), name
+        del ws, C
 
 
 def test_tc_f16_blocked_path():
