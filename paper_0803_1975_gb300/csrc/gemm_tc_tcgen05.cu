@@ -52,6 +52,9 @@ struct TcCfg {
     static constexpr bool FP4 = FP4_;                  // packed e2m1 operands, block-scaled MMA
     static constexpr int STAGES = STAGES_;
     static constexpr int BKE = FP4 ? 256 : FP8 ? 128 : 64;   // k elements per stage
+    // stage step along the tensor map's inner dimension, in the map's elements
+    // (the e2m1 maps are bytes holding two values each)
+    static constexpr int MAP_X = FP4 ? ROWB : BKE;
     static constexpr int A_BYTES = BM * ROWB, B_BYTES = BN * ROWB;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // multiple of 1024
     // two accumulators; the e2m1 form also keeps its unit scale factors in
@@ -457,8 +460,8 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         }
                         continue;
                     }
-                    tma_load_2d(sa, mA, kt * CFG::BKE, ti.rowA0 + tm * BM, full_bar(stage));
-                    tma_load_2d(sb, mB, kt * CFG::BKE, ti.rowB0 + tn * BN, full_bar(stage));
+                    tma_load_2d(sa, mA, kt * CFG::MAP_X, ti.rowA0 + tm * BM, full_bar(stage));
+                    tma_load_2d(sb, mB, kt * CFG::MAP_X, ti.rowB0 + tn * BN, full_bar(stage));
                     issued[stage] = true;
                     issued_parity[stage] = phase;
                     if (++stage == STAGES) {
