@@ -292,7 +292,9 @@ GFP_API gfp_status gfp_gemm(uint32_t p, int64_t m, int64_t k, int64_t n,
  *  rejected with GFP_EWORKSPACE before anything is launched.
  *  The first call on a device, with that device current, looks up the
  *  scratch's device address (one-time set-up); make that first call before
- *  any stream capture.  Every call uses the same scratch, so calls whose
+ *  any stream capture.  The address is kept with the context it was found
+ *  in: after cudaDeviceReset the next call (again before any capture) looks
+ *  it up anew.  Every call uses the same scratch, so calls whose
  *  kernels overlap on the GPU (other streams, other host threads) race on it
  *  and must be serialized by the caller.  Errors as gfp_gemm. */
 GFP_API gfp_status gfp_gemm_noalloc(uint32_t p, int64_t m, int64_t k, int64_t n,

@@ -125,6 +125,7 @@ struct MmaArgs {
     int64_t kb_tiles;   // k-block in BK slices
     uint32_t p, off;
     uint64_t M;
+    int64_t tile_m0;    // first row tile of this launch (grids hold at most 65,535 row tiles)
 };
 
 __global__ void __launch_bounds__(NT) mma_s8_kernel(MmaArgs g) {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(NT) mma_s8_kernel(MmaArgs g) {
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 2, wn = warp & 3;           // 2 x 4 warps
-    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+    const int64_t m0 = ((int64_t)blockIdx.y + g.tile_m0) * BM, n0 = (int64_t)blockIdx.x * BN;
     const int8_t *Ag = g.Ac + m0 * g.kp;
     const int8_t *Bg = g.Bt + n0 * g.kp;
     const int64_t ktiles = g.kp / BK;
@@ -279,9 +280,15 @@ gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint
     static std::atomic<uint64_t> attr{0};
     const cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(mma_s8_kernel), smem, attr);
     if (ea != cudaSuccess) return cuda_fail(ea);
-    dim3 grid((unsigned)(np / BN), (unsigned)(mp / BM));
-    mma_s8_kernel<<<grid, NT, smem, s>>>(g);
-    return check_launch();
+    // products taller than 65,535 row tiles run as several launches
+    for (int64_t t0 = 0; t0 < mp / BM; t0 += 65535) {
+        g.tile_m0 = t0;
+        const int64_t rows = mp / BM - t0 < 65535 ? mp / BM - t0 : 65535;
+        mma_s8_kernel<<<dim3((unsigned)(np / BN), (unsigned)rows), NT, smem, s>>>(g);
+        const gfp_status st = check_launch();
+        if (st != GFP_OK) return st;
+    }
+    return GFP_OK;
 }
 
 }  // namespace gfp

@@ -10,11 +10,16 @@
 // every GPU that loads the library keeps it for the life of the process.  In
 // host code the array's name does not denote a device address, so the first
 // call on each device (with that device current) looks the address up with
-// cudaGetSymbolAddress and caches it; later calls on that device reuse it.
+// cudaGetSymbolAddress and caches it with the device's current context; later
+// calls in the same context reuse it.  A call that finds another context
+// current (the primary context was destroyed by cudaDeviceReset and created
+// again, which loads the module, and so the array, anew) looks it up again.
 // All calls share the array, so calls whose kernels overlap on the GPU race
 // on it.  The two preprocessing kernels rewrite every byte of the scratch a
 // call uses (padding included), so nothing has to be cleared between calls.
 #include <mutex>
+
+#include <cuda.h>
 
 #include "gfp_internal.h"
 
@@ -25,19 +30,43 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[GFP_NOALLOC_SCRATCH_B
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[64] = {nullptr};
+CUcontext g_noalloc_ctx[64] = {nullptr};
 
-// Device address of the scratch on the current device (looked up once).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+CtxGetCurrentFn ctx_get_current_fn() {
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
+
+// Device address of the scratch in the current context of the current device
+// (looked up once per context).
 gfp_status noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
     if (dev < 0 || dev >= 64) return GFP_EUNSUPPORTED;
+    CtxGetCurrentFn get = ctx_get_current_fn();
+    if (!get) return GFP_EUNSUPPORTED;
+    CUcontext ctx = nullptr;
+    if (get(&ctx) != CUDA_SUCCESS) return GFP_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!ctx || !g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
+        // the lookup also makes the device's primary context current if none is
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        if (get(&ctx) != CUDA_SUCCESS || !ctx) return GFP_EUNSUPPORTED;
         g_noalloc_ptr[dev] = ptr;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_ptr[dev];
     return GFP_OK;

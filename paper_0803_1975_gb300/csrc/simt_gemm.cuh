@@ -207,13 +207,21 @@ cudaError_t simt_gemm_launch(const typename P::GA *A, int64_t lda, const typenam
     constexpr int NT = (BM / TM) * (BN / TN);
     const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
     if (gx <= 0 || gy <= 0) return cudaSuccess;
-    if (gy > 65535 || gx > 2147483647 || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
+    if (gx > 2147483647 || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
     int64_t kchunk = 0;
     if (splits > 1) kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
     const unsigned gz = kchunk > 0 ? (unsigned)((K + kchunk - 1) / kchunk) : 1u;
-    simt_gemm_kernel<P, BM, BN, BK, TM, TN>
-        <<<dim3((unsigned)gx, (unsigned)gy, gz), NT, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K, prm, kchunk);
-    return cudaGetLastError();
+    // a grid holds at most 65,535 row tiles: taller products run as several
+    // launches over bands of rows (row i of A gives row i of C)
+    constexpr int64_t band = (int64_t)65535 * BM;
+    for (int64_t r0 = 0; r0 < M; r0 += band) {
+        const int64_t rows = M - r0 < band ? M - r0 : band;
+        simt_gemm_kernel<P, BM, BN, BK, TM, TN><<<dim3((unsigned)gx, (unsigned)((rows + BM - 1) / BM), gz), NT, 0, s>>>(
+            A + r0 * lda, lda, B, ldb, C + r0 * ldc, ldc, rows, N, K, prm, kchunk);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Default element fetch: a guarded load converted to the shared-memory type.

@@ -117,6 +117,29 @@ def test_wider_than_the_grid_limit(algo):
     assert (host(C) == oracle.gemm(p, A, B, threads=THREADS)).all()
 
 
+def test_taller_than_the_grid_limit():
+    """m = 8,400,000 rows: more row tiles than a grid's y dimension holds
+    (65,535 tiles of 128 rows, or of the CUDA-core kernels' tiles); the
+    launches run over bands of rows.  Every uncompressed algorithm, the dot
+    form in 32- and 64-bit words and the right-compressed form."""
+    p, m, k, n = 5, 8_400_000, 5, 3
+    A, B = operands(10, 2, p, m, k, n)
+    ref = oracle.gemm(p, A, B, threads=THREADS)
+    Ad, Bd = dev(A), dev(B)
+    for algo in ALGOS:
+        assert (host(gfp.gfp_gemm(p, Ad, Bd, algo)) == ref).all(), algo
+    for word in ("u32", "u64"):
+        d, Q, _ = gfp.gfp_params(p, m, k, n, "dot", word)
+        CA = gfp.gfp_pack(p, Ad, d, Q, "rows_rev", word)
+        CB = gfp.gfp_pack(p, Bd, d, Q, "cols", word)
+        assert (host(gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "dot", word, CA, CB)) == ref).all(), word
+        del CA, CB
+    d, Q, _ = gfp.gfp_params(p, m, k, n, "mixed", "u64")
+    CB = gfp.gfp_pack(p, Bd, d, Q, "rows", "u64")
+    CC = gfp.gfp_gemm_compressed(p, m, k, n, d, Q, "mixed", "u64", Ad, CB)
+    assert (host(gfp.gfp_unpack(p, CC, m, n, d, Q, "rows", "u64")) == ref).all()
+
+
 # Results spanning at least two waves of the 128 x 128 and 128 x 64 register tiles
 # of the CUDA-core kernels (the only shapes that use them), ragged in both
 # dimensions: at 4001 x 3999 the classical and dp4a products run on 128 x 128

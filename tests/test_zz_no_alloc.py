@@ -44,6 +44,30 @@ def test_noalloc_matches_workspace_entry_point_twice():
         assert (got == oracle.gemm(p, A_h, B_h)).all(), call
 
 
+def test_noalloc_larger_call_then_smaller_ragged_call():
+    """The shared scratch keeps the previous call's bytes.  A call that fills
+    nearly all of it with nonzero operands (k = 8000) is followed by a smaller
+    call with another padded k and ragged m, n, k: the smaller call must
+    rewrite every byte it reads (padding included) and match gfp_gemm's
+    int8 tensor-core form and the oracle bit for bit."""
+    ensure_built()
+    L = gfp.load()
+    for call, (p, m, k, n) in enumerate([(251, 1024, 8000, 1000), (7, 131, 999, 77)]):
+        g = inputs.rng(61, call)
+        A_h = inputs.residues(g, p, m, k)
+        B_h = inputs.residues(g, p, k, n)
+        if call == 0:
+            A_h |= 1            # nonzero everywhere
+            B_h |= 1
+        A, B = dev(A_h), dev(B_h)
+        ref = host(gfp.gfp_gemm(p, A, B, "tc_mma_s8"))
+        C = torch.full((m, n), 255, dtype=torch.uint8, device="cuda")
+        assert call_noalloc(L, p, A, B, C) == 0
+        got = host(C)
+        assert (got == ref).all(), call
+        assert (got == oracle.gemm(p, A_h, B_h, threads=8)).all(), call
+
+
 def test_noalloc_rejects_problems_beyond_the_scratch():
     ensure_built()
     L = gfp.load()
