@@ -877,6 +877,447 @@ void launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, i
     tc_f16_kernel<CFG, BLOCKED, GROUPED><<<grid, NTHREADS, CFG::SMEM_BYTES, s>>>(ma, mb, g, grp);
 }
 
+// ---------------------------------------------------------------------------
+// CTA pairs: the same product on 256-row tiles, each MMA issued once for two
+// SMs (tcgen05 cta_group::2).  The two CTAs of a cluster hold the two 128-row
+// halves of the A tile and the two halves of the B^T tile in their own shared
+// memory, at the same offsets; one thread of the even CTA (the leader) issues
+// 256 x BN x k MMAs that read both CTAs' operands and write each CTA's
+// 128 x BN accumulator into that CTA's tensor memory.  Per SM this moves half
+// the B bytes of a 128 x BN tile of the one-SM kernel for the same flops, the
+// relief the shared-memory port needs (the one-SM kernels keep it about 95%
+// busy with TMA writes and MMA reads).
+//
+// Synchronisation (every wait bounded as in the one-SM kernel):
+//   full[s]  : each CTA's copies complete on its own barrier; the odd CTA's
+//              warp 1 waits for them and arrives on the leader's full[s]
+//              (count 2: the leader's own expect-tx arrival and that one);
+//   empty[s] : the leader's MMA commit arrives on empty[s] of both CTAs;
+//   accf[b]  : likewise for a finished accumulator (both epilogues wait);
+//   acce[b]  : the 4 epilogue warps of both CTAs arrive on the leader's
+//              (count 8) once they have read their accumulator.
+// Tensor memory is allocated by warp 1 of both CTAs together (cta_group::2),
+// 512 columns: two accumulators of BN columns and, for e2m1 operands, the
+// unit scale factors.  Both CTAs check that they received the same address.
+template <int BN_, int KIND_, int STAGES_, int TMEM_ = 512>
+struct PairCfg {
+    static constexpr int BN = BN_;                      // pair tile: 256 x BN
+    static constexpr int KIND = KIND_;                  // 0 fp16, 1 e4m3, 2 e2m1
+    static constexpr int STAGES = STAGES_;
+    static constexpr int BKE = KIND == 2 ? 256 : KIND == 1 ? 128 : 64;
+    static constexpr int MAP_X = KIND == 2 ? ROWB : BKE;
+    static constexpr int A_BYTES = BM * ROWB, B_BYTES = (BN / 2) * ROWB;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static_assert(B_BYTES % 1024 == 0, "operand tiles start on 1024-byte swizzle atoms");
+    static constexpr uint32_t TMEM_COLS = TMEM_;
+    static constexpr uint32_t SF_COL = 2 * BN;
+    static_assert(2 * BN <= TMEM_ && (KIND != 2 || 2 * BN + 64 <= TMEM_), "tensor memory columns");
+    static constexpr int STG_BYTES = 4 * 32 * 9 * 4;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + STG_BYTES + 1024;
+    // M = 256 (bits 24-28 hold M >> 4), N >> 3 in bits 17-22; kinds as TcCfg
+    static constexpr uint32_t IDESC =
+        (KIND == 2 ? (1u << 7) | (1u << 10) | (1u << 23) : (1u << 4)) | ((uint32_t)(BN >> 3) << 17) |
+        ((uint32_t)(256 >> 4) << 24);
+};
+
+constexpr int ST_PAIR_TMEM = 5;   // status: the two CTAs received different tensor memory
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared::cta offset in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t cluster_addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
+    return v;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma_issue_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accum, uint32_t sfa, uint32_t sfb) {
+    if constexpr (KIND == 2)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum), "r"(sfa), "r"(sfb)
+            : "memory");
+    else if constexpr (KIND == 1)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+}
+// arrives on the barrier at offset `bar` in both CTAs of the pair once every
+// MMA this thread issued before has completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+template <class CFG, bool BLOCKED>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
+    constexpr int BN = CFG::BN, HB = BN / 2, STAGE_BYTES = CFG::STAGE_BYTES, A_BYTES = CFG::A_BYTES;
+    constexpr int STAGES = CFG::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;     // same offset in both CTAs of the pair
+    uint8_t *gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 5));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const uint32_t slot_addr = (uint32_t)__cvta_generic_to_shared(tmem_slot);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), leader ? 2 : 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 8);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_addr),
+                     "r"(CFG::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    cluster_sync();     // both CTAs' barriers initialised and tensor memory allocated
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // the leader's MMAs write the same columns in both CTAs: they must agree
+    const bool bad = ld_cluster_u32(mapa_rank(slot_addr, rank ^ 1u)) != tmem;
+    if (bad && threadIdx.x == 0 && g.status) atomicCAS(g.status, 0, ST_PAIR_TMEM);
+    if constexpr (CFG::KIND == 2) {
+        // unit scale factors (ue8m0 127) in columns SF_COL .. TMEM_COLS - 1 of both CTAs
+        if (warp >= 2 && !bad) {
+            const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+            for (uint32_t c = CFG::SF_COL; c < CFG::TMEM_COLS; c += 8)
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+                        tmem + lanes + c),
+                    "r"(0x7F7F7F7Fu)
+                    : "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        fence_before();
+        cluster_sync();
+        fence_after();
+    }
+
+    const int nclusters = (int)(gridDim.x / 2), cid = (int)(blockIdx.x / 2);
+    const int tiles = g.tiles_m * g.tiles_n;    // tiles_m counts 256-row tiles
+
+    if (warp == 0) {
+        if (lane == 0 && !bad) {
+            // ---------------- TMA producer (both CTAs): this CTA's halves, its own barrier
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_parity[STAGES];
+            bool issued[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = false;
+            bool ok = true;
+            for (int t = cid; ok && t < tiles; t += nclusters) {
+                int tm, tn;
+                tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
+                for (int kt = 0; kt < g.ktiles; ++kt) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER, g.limit_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+                    mbar_expect_tx(full_bar(stage), STAGE_BYTES);
+                    tma_load_2d(sa, &tmA, kt * CFG::MAP_X, tm * 256 + (int)rank * BM, full_bar(stage));
+                    tma_load_2d(sb, &tmB, kt * CFG::MAP_X, tn * BN + (int)rank * HB, full_bar(stage));
+                    issued[stage] = true;
+                    issued_parity[stage] = phase;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits (one
+                // deadline for all: the leader's barriers also wait for the peer)
+                const uint64_t t0 = globaltimer();
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued[s])
+                        while (!mbar_try(full_bar(s), issued_parity[s]) && globaltimer() - t0 < g.limit_ns) {
+                        }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && !bad && leader) {
+            // ---------------- MMA issuer (leader only)
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t unit = 0;
+            bool ok = true;
+            for (int t = cid; ok && t < tiles; t += nclusters) {
+                for (int j = 0; j < g.kblocks && ok; ++j, ++unit) {
+                    const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
+                    if (!mbar_wait(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t d = tmem + buf * (uint32_t)BN;
+                    const int k0 = j * g.kb_tiles;
+                    const int k1 = min(g.ktiles, k0 + g.kb_tiles);
+                    for (int kt = k0; kt < k1; ++kt) {
+                        if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < ROWB / 32; ++kk) {
+                            const uint32_t acc = (kt > k0 || kk > 0) ? 1u : 0u;
+                            mma_issue_pair<CFG::KIND>(d, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), CFG::IDESC,
+                                                      acc, tmem + CFG::SF_COL, tmem + CFG::SF_COL + 32);
+                        }
+                        mma_commit_pair(empty_bar(stage));
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                    if (ok) mma_commit_pair(accf_bar(buf));
+                }
+            }
+        } else if (lane == 0 && !bad) {
+            // ---------------- forwarder (odd CTA): its stage landed -> the leader's full barrier
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = cid; ok && t < tiles; t += nclusters)
+                for (int kt = 0; kt < g.ktiles; ++kt) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_rank(full_bar(stage), 0));
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+        }
+        if (lane == 0) {
+            // every MMA of the pair completes before either CTA frees tensor memory
+            if (leader) mma_commit_pair(drain_bar);
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try(drain_bar, 0)) {
+                if (globaltimer() - t0 > g.limit_ns) {
+                    if (g.status) atomicCAS(g.status, 0, ST_TIMEOUT_DRAIN);
+                    break;
+                }
+            }
+        }
+    } else if (!bad) {
+        // ---------------- epilogue: 4 warps per CTA, this CTA's 128 rows of the tile
+        const int q = warp & 3;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        uint32_t *stg = reinterpret_cast<uint32_t *>(gbase + STAGES * STAGE_BYTES + 1024) + q * 32 * 9;
+        const uint8_t *stg8 = reinterpret_cast<const uint8_t *>(stg);
+        uint32_t unit = 0;
+        bool ok = true;
+        uint32_t run[BLOCKED ? BN / 4 : 1];
+        for (int t = cid; ok && t < tiles; t += nclusters) {
+            int tm, tn;
+            tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
+            const int64_t row0 = (int64_t)tm * 256 + (int64_t)rank * BM + q * 32;
+            const int64_t row = row0 + lane;
+            const int64_t col0 = (int64_t)tn * BN;
+            if constexpr (BLOCKED) {
+#pragma unroll
+                for (int i = 0; i < BN / 4; ++i) run[i] = 0;
+            }
+            for (int j = 0; j < g.kblocks; ++j, ++unit) {
+                const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
+                int got = 0;
+                if (lane == 0) got = mbar_wait(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI, g.limit_ns);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const bool last = (j == g.kblocks - 1);
+                const int nchunks = row0 >= g.m ? 0 : (int)min((int64_t)(BN / 32), (g.n - col0 + 31) / 32);
+                auto store_chunk = [&](int c, const uint32_t(&w)[8]) {
+                    const int64_t col = col0 + c * 32;
+                    const bool vec = col + 32 <= g.n &&
+                                     ((reinterpret_cast<uintptr_t>(g.C) | (uintptr_t)g.ldc) & 15) == 0;
+                    if (vec) {
+                        if (row < g.m) {
+                            uint8_t *dst = g.C + row * g.ldc + col;
+                            reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) stg[lane * 9 + e] = w[e];
+                        __syncwarp();
+                        const int nr = (int)min((int64_t)32, g.m - row0);
+                        if (col + lane < g.n) {
+                            uint8_t bt[32];
+#pragma unroll
+                            for (int rr = 0; rr < 32; ++rr) bt[rr] = stg8[rr * 36 + lane];
+                            uint8_t *dst = g.C + row0 * g.ldc + col + lane;
+#pragma unroll
+                            for (int rr = 0; rr < 32; ++rr, dst += g.ldc)
+                                if (rr < nr) *dst = bt[rr];
+                        }
+                        __syncwarp();
+                    }
+                };
+                uint32_t vn[32];
+                if (nchunks > 0) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN, vn);
+#pragma unroll
+                for (int c = 0; c < BN / 32; ++c) {
+                    if (c >= nchunks) break;
+                    uint32_t v[32];
+                    tmem_wait(vn);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = vn[i];
+                    if (c + 1 < nchunks) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN + (c + 1) * 32, vn);
+                    uint32_t rr32[32];
+                    if (g.red) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u;
+                            rr32[i] = x - __umulhi(x, g.m32) * g.p;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * g.scale), g.off, g.m32, g.p);
+                    }
+                    uint32_t w[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        uint32_t r[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            r[b] = rr32[e * 4 + b];
+                            if constexpr (BLOCKED) {
+                                r[b] += (run[c * 8 + e] >> (8 * b)) & 0xffu;
+                                r[b] = r[b] >= g.p ? r[b] - g.p : r[b];
+                            }
+                        }
+                        const uint32_t packed =
+                            __byte_perm(__byte_perm(r[0], r[1], 0x0040), __byte_perm(r[2], r[3], 0x0040), 0x5410);
+                        w[e] = packed;
+                        if constexpr (BLOCKED) run[c * 8 + e] = packed;
+                    }
+                    if (last) store_chunk(c, w);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader) mbar_arrive(acce_bar(buf));
+                    else mbar_arrive_cluster(mapa_rank(acce_bar(buf), 0));
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    cluster_sync();     // neither CTA leaves while the other may still reach its shared memory
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CFG::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Clusters of two that can be resident at once (cached per device and kernel).
+template <class CFG, bool BLOCKED>
+int pair_clusters() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int v = cached[dev].load();
+    if (v > 0) return v;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(2 * (unsigned)num_sms(), 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = CFG::SMEM_BYTES;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<CFG, BLOCKED>, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    cached[dev].store(n);
+    return n;
+}
+
+template <class CFG, bool BLOCKED>
+gfp_status launch_pair(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, cudaStream_t s) {
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t ea =
+        smem_attr_once(reinterpret_cast<const void *>(tc_pair_kernel<CFG, BLOCKED>), CFG::SMEM_BYTES, attr);
+    if (ea != cudaSuccess) return cuda_fail(ea);
+    const int nc = pair_clusters<CFG, BLOCKED>();
+    if (nc <= 0) return GFP_EUNSUPPORTED;
+    const int tiles = g.tiles_m * g.tiles_n;
+    const int clusters = tiles < nc ? tiles : nc;
+    tc_pair_kernel<CFG, BLOCKED><<<2 * clusters, NTHREADS, CFG::SMEM_BYTES, s>>>(ma, mb, g);
+    return check_launch();
+}
+
+// Pair tiles: 256 x PAIR_BN (fp16, e4m3) and 256 x PAIR_BN_E2M1 outputs,
+// PAIR_TMEM columns of tensor memory per CTA.
+constexpr int PAIR_TMEM = 256, PAIR_BN = 128, PAIR_BN_E2M1 = 96;
+
+// CTA pairs when their 256 x bn tiles give every SM pair a tile.
+bool use_pairs(int64_t m, int64_t n, int bn) {
+    return ((m + 255) / 256) * ((n + bn - 1) / bn) >= num_sms() / 2;
+}
+
 // Tile width: 256 columns when those tiles fill the GPU, else 128.
 int pick_bn(int64_t m, int64_t n) {
     const int64_t t256 = ((m + BM - 1) / BM) * ((n + 255) / 256);
@@ -934,6 +1375,7 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     const bool ok_a = raw ? make_map(&ma, A, m, k, BM, true, lda) : make_map(&ma, Aop, mp, kp, BM, fp8);
     if (!ok_a || !make_map(&mb, Bop, np, kp, bn, fp8)) return GFP_EUNSUPPORTED;
     TcArgs g;
+    std::memset(&g, 0, sizeof(g));
     g.C = C;
     g.ldc = ldc;
     g.m = m;
@@ -955,9 +1397,20 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     g.status = status;
     g.limit_ns = WAIT_LIMIT_NS;
     g.stall = 0;
+    const bool blk = g.kblocks > 1;
+    if (use_pairs(m, n, PAIR_BN)) {
+        // CTA pairs on 256 x PAIR_BN tiles: each CTA loads PAIR_BN / 2 rows of B^T
+        CUtensorMap mb2;
+        if (!make_map(&mb2, Bop, np, kp, PAIR_BN / 2, fp8)) return GFP_EUNSUPPORTED;
+        g.tiles_m = (int)((m + 255) / 256);
+        g.tiles_n = (int)((n + PAIR_BN - 1) / PAIR_BN);
+        using PF8 = PairCfg<PAIR_BN, 1, 6, PAIR_TMEM>;
+        using PF16 = PairCfg<PAIR_BN, 0, 6, PAIR_TMEM>;
+        if (fp8) return blk ? launch_pair<PF8, true>(ma, mb2, g, s) : launch_pair<PF8, false>(ma, mb2, g, s);
+        return blk ? launch_pair<PF16, true>(ma, mb2, g, s) : launch_pair<PF16, false>(ma, mb2, g, s);
+    }
     const int tiles = g.tiles_m * g.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();
-    const bool blk = g.kblocks > 1;
     if (fp8) {
         if (bn == 256) blk ? launch_cfg<TcCfg<256, true>, true>(ma, mb, g, grid, s) : launch_cfg<TcCfg<256, true>, false>(ma, mb, g, grid, s);
         else blk ? launch_cfg<TcCfg<128, true>, true>(ma, mb, g, grid, s) : launch_cfg<TcCfg<128, true>, false>(ma, mb, g, grid, s);
@@ -1147,6 +1600,15 @@ gfp_status launch_tc_e2m1(uint32_t p, int64_t m, int64_t k, int64_t n, const uin
     g.status = status;
     g.limit_ns = WAIT_LIMIT_NS;
     g.stall = 0;
+    using PairE2m1 = PairCfg<PAIR_BN_E2M1, 2, 7, PAIR_TMEM>;
+    if (use_pairs(m, n, PairE2m1::BN)) {
+        // CTA pairs on 256 x PAIR_BN_E2M1 tiles: each CTA loads half of those rows of B^T
+        CUtensorMap mb2;
+        if (!make_map(&mb2, Bop, np, rowb, PairE2m1::BN / 2, true)) return GFP_EUNSUPPORTED;
+        g.tiles_m = (int)((m + 255) / 256);
+        g.tiles_n = (int)((n + PairE2m1::BN - 1) / PairE2m1::BN);
+        return g.kblocks > 1 ? launch_pair<PairE2m1, true>(ma, mb2, g, s) : launch_pair<PairE2m1, false>(ma, mb2, g, s);
+    }
     const int tiles = g.tiles_m * g.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();
     if (g.kblocks > 1) launch_cfg<TcE2m1Cfg, true>(ma, mb, g, grid, s);

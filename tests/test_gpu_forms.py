@@ -298,6 +298,36 @@ def test_tc_e2m1_exact_accumulation(p):
         del ws, C
 
 
+@pytest.mark.parametrize("algo,p", [("tc_f16", 251), ("tc_f8", 31), ("tc_e2m1", 7)])
+def test_tc_pairs_exact_accumulation(algo, p):
+    """The CTA-pair kernels (chosen when the 256-row tiles give every pair of
+    SMs a tile: here m = 256, n = 19456) with fp32 accumulation at the k-block
+    bound kb: all products +h^2, products of both signs, a large accumulator
+    followed by small addends; fp16 at p = 251 also runs two k-blocks and a
+    ragged tail (the blocked path).  Operands are built on the GPU (B is up to
+    36 GB for e2m1 at p = 7, kb = 1,864,192); every entry of C has the same
+    expected value, one oracle dot product."""
+    h = (p - 1) // 2
+    step = 256 if algo == "tc_e2m1" else 128
+    kb = ((1 << 24) - 1 - p) // (h * h) // step * step
+    k = 2 * kb + 300 if algo == "tc_f16" else kb
+    m, n = 256, 19456
+    pos, neg = h, h + 1                       # centred +h and -h
+    col = {"all+": np.full(k, pos, np.uint8), "alt": np.where(np.arange(k) % 2 == 0, pos, neg).astype(np.uint8)}
+    row = {"all+": np.full(k, pos, np.uint8), "alt": np.full(k, pos, np.uint8),
+           "big-then-small": np.where(np.arange(k) < k // 2, pos, 1).astype(np.uint8)}
+    for name, bname in (("all+", "all+"), ("alt", "alt"), ("big-then-small", "all+")):
+        A = dev(row[name])[None, :].expand(m, k).contiguous()
+        B = dev(col[bname])[:, None].expand(k, n).contiguous()
+        ws = torch.empty(gfp.gfp_gemm_workspace_size(p, m, k, n, algo), dtype=torch.uint8, device="cuda")
+        C = host(gfp.gfp_gemm(p, A, B, algo, workspace=ws))
+        assert tc_f16_status(ws) == 0, name
+        want = oracle.gemm(p, row[name][None, :], col[bname][:, None])[0, 0]
+        assert (C == want).all(), name
+        del A, B, ws
+        torch.cuda.empty_cache()
+
+
 def test_tc_f16_blocked_path():
     """p = 251 beyond one fp32 k-block (kb = 1024): running residues across
     k-blocks, random and worst-case inputs."""
