@@ -889,9 +889,9 @@ void launch_cfg(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &g, i
 // busy with TMA writes and MMA reads).
 //
 // Synchronisation (every wait bounded as in the one-SM kernel):
-//   full[s]  : each CTA's copies complete on its own barrier; the odd CTA's
-//              warp 1 waits for them and arrives on the leader's full[s]
-//              (count 2: the leader's own expect-tx arrival and that one);
+//   full[s]  : the copies of both CTAs complete on the leader's full[s] (the
+//              leader expects both CTAs' bytes; the odd CTA's copies name the
+//              leader's barrier);
 //   empty[s] : the leader's MMA commit arrives on empty[s] of both CTAs;
 //   accf[b]  : likewise for a finished accumulator (both epilogues wait);
 //   acce[b]  : the 4 epilogue warps of both CTAs arrive on the leader's
@@ -943,6 +943,47 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t cluster_addr) {
     uint32_t v;
     asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
     return v;
+}
+
+// copy into this CTA's shared memory, completion signalled on the barrier at
+// shared::cluster address `bar` (the leader's)
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait as mbar_wait, polling without suspending the thread: the
+// waits of the CTA pairs, whose barriers are completed from the other CTA
+// (its copies, its MMA commits, its threads' arrivals).
+__device__ __noinline__ bool mbar_wait_spin(uint32_t a, uint32_t parity, volatile int *abort_flag, int *status,
+                                            int code, uint64_t limit_ns) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_test(a, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            const uint64_t now = globaltimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit_ns) {
+                *abort_flag = 1;
+                if (status) atomicCAS(status, 0, code);
+                return false;
+            }
+        }
+    }
 }
 
 template <int KIND>
@@ -1001,7 +1042,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full_bar(s), leader ? 2 : 1);
+            mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -1048,7 +1089,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (warp == 0) {
         if (lane == 0 && !bad) {
-            // ---------------- TMA producer (both CTAs): this CTA's halves, its own barrier
+            // ---------------- TMA producer (both CTAs): this CTA's halves, the leader's barrier
             int stage = 0;
             uint32_t phase = 0;
             uint32_t issued_parity[STAGES];
@@ -1059,14 +1100,15 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int tm, tn;
                 tile_coords(t, g.tiles_m, g.tiles_n, tm, tn);
                 for (int kt = 0; kt < g.ktiles; ++kt) {
-                    if (!mbar_wait(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER, g.limit_ns)) {
+                    if (!mbar_wait_spin(empty_bar(stage), phase ^ 1, abort_flag, g.status, ST_TIMEOUT_PRODUCER, g.limit_ns)) {
                         ok = false;
                         break;
                     }
                     const uint32_t sa = base + stage * STAGE_BYTES, sb = sa + A_BYTES;
-                    mbar_expect_tx(full_bar(stage), STAGE_BYTES);
-                    tma_load_2d(sa, &tmA, kt * CFG::MAP_X, tm * 256 + (int)rank * BM, full_bar(stage));
-                    tma_load_2d(sb, &tmB, kt * CFG::MAP_X, tn * BN + (int)rank * HB, full_bar(stage));
+                    const uint32_t fb = mapa_rank(full_bar(stage), 0);
+                    if (leader) mbar_expect_tx(full_bar(stage), 2 * STAGE_BYTES);
+                    tma_load_2d_pair(sa, &tmA, kt * CFG::MAP_X, tm * 256 + (int)rank * BM, fb);
+                    tma_load_2d_pair(sb, &tmB, kt * CFG::MAP_X, tn * BN + (int)rank * HB, fb);
                     issued[stage] = true;
                     issued_parity[stage] = phase;
                     if (++stage == STAGES) {
@@ -1076,13 +1118,20 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             }
             if (!ok) {
-                // let the copies already issued land before the CTA exits (one
-                // deadline for all: the leader's barriers also wait for the peer)
+                // let the copies already issued land before the CTA exits: the
+                // leader sees its barriers complete (one deadline for all); the
+                // odd CTA, whose copies complete on the leader's barriers, waits
+                // a fixed 2 ms, far longer than any copy takes
                 const uint64_t t0 = globaltimer();
-                for (int s = 0; s < STAGES; ++s)
-                    if (issued[s])
-                        while (!mbar_try(full_bar(s), issued_parity[s]) && globaltimer() - t0 < g.limit_ns) {
-                        }
+                if (leader) {
+                    for (int s = 0; s < STAGES; ++s)
+                        if (issued[s])
+                            while (!mbar_try(full_bar(s), issued_parity[s]) && globaltimer() - t0 < g.limit_ns) {
+                            }
+                } else {
+                    while (globaltimer() - t0 < 2000000ull) {
+                    }
+                }
             }
         }
     } else if (warp == 1) {
@@ -1095,7 +1144,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int t = cid; ok && t < tiles; t += nclusters) {
                 for (int j = 0; j < g.kblocks && ok; ++j, ++unit) {
                     const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
-                    if (!mbar_wait(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
+                    if (!mbar_wait_spin(acce_bar(buf), accp ^ 1, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
                         ok = false;
                         break;
                     }
@@ -1104,7 +1153,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const int k0 = j * g.kb_tiles;
                     const int k1 = min(g.ktiles, k0 + g.kb_tiles);
                     for (int kt = k0; kt < k1; ++kt) {
-                        if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
+                        if (!mbar_wait_spin(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
                             ok = false;
                             break;
                         }
@@ -1125,23 +1174,6 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     if (ok) mma_commit_pair(accf_bar(buf));
                 }
             }
-        } else if (lane == 0 && !bad) {
-            // ---------------- forwarder (odd CTA): its stage landed -> the leader's full barrier
-            int stage = 0;
-            uint32_t phase = 0;
-            bool ok = true;
-            for (int t = cid; ok && t < tiles; t += nclusters)
-                for (int kt = 0; kt < g.ktiles; ++kt) {
-                    if (!mbar_wait(full_bar(stage), phase, abort_flag, g.status, ST_TIMEOUT_MMA, g.limit_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_cluster(mapa_rank(full_bar(stage), 0));
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
-                }
         }
         if (lane == 0) {
             // every MMA of the pair completes before either CTA frees tensor memory
@@ -1176,7 +1208,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int j = 0; j < g.kblocks; ++j, ++unit) {
                 const uint32_t buf = unit & 1, accp = (unit >> 1) & 1;
                 int got = 0;
-                if (lane == 0) got = mbar_wait(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI, g.limit_ns);
+                if (lane == 0) got = mbar_wait_spin(accf_bar(buf), accp, abort_flag, g.status, ST_TIMEOUT_EPI, g.limit_ns);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
