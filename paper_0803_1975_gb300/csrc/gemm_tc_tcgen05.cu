@@ -1343,7 +1343,7 @@ gfp_status launch_pair(const CUtensorMap &ma, const CUtensorMap &mb, const TcArg
 
 // Pair tiles: 256 x PAIR_BN (fp16, e4m3) and 256 x PAIR_BN_E2M1 outputs,
 // PAIR_TMEM columns of tensor memory per CTA.
-constexpr int PAIR_TMEM = 256, PAIR_BN = 128, PAIR_BN_E2M1 = 96;
+constexpr int PAIR_TMEM = 512, PAIR_BN = 256, PAIR_BN_E2M1 = 192;
 
 // CTA pairs when their 256 x bn tiles give every SM pair a tile.
 bool use_pairs(int64_t m, int64_t n, int bn) {
