@@ -62,22 +62,27 @@ def config_dict():
             "l2": "operands of 256 MiB each (larger than L2) and a 256 MiB buffer written between steps"}
 
 
-# Throughput ceilings of the pipes the CUDA-core forms run on.  GB300: 152
-# SMs at up to 2.07 GHz.  The per-SM instruction rates were measured on this
-# pool's GB300 with chains of one instruction over 4 CTAs per SM: 64 32-bit
-# multiply-adds (IMAD, IMAD.WIDE) or dp4a per SM per clock, and 7.2e12/s for
-# the 64-bit multiply-add as the compiler lowers it.  Each form's work is
-# counted in the unit its inner loop issues.
-SMS, CLOCK = 152, 2.07e9
-PIPES = {
-    "imad": (SMS * 64 * CLOCK, "IMAD/s (152 SMs x 64 lanes x 2.07 GHz)"),
-    "imad_wide": (SMS * 64 * CLOCK, "IMAD.WIDE/s (152 SMs x 64 lanes x 2.07 GHz)"),
-    "dp4a": (SMS * 64 * CLOCK, "dp4a/s (152 SMs x 64 lanes x 2.07 GHz)"),
-    "mad64": (7.2e12, "64-bit mad.lo/s (measured chain rate)"),
-    "mad64x2": (3.6e12, "64x64->128 multiply-adds/s (two 64-bit mads each)"),
-    "mad64x32": (SMS * 64 * CLOCK / 2, "64x32-bit multiply-adds/s (two IMADs each)"),
-    "mma_s8": (158e12, "int8 mma.sync ops/s (measured)"),
-}
+# Throughput ceilings of the pipes the CUDA-core forms run on, measured on
+# this GPU by the library's instruction-rate probe (gfp_pipe_rates: chains of
+# one instruction, 32 warps per SM).  Each form's work is counted in the unit
+# its inner loop issues.
+PIPES = {}
+
+
+def set_pipes(rates):
+    """The ceilings from the measured rates (operations per second)."""
+    imad, wide = rates["imad"], rates["imad_wide"]
+    PIPES.update({
+        "imad": (imad, "IMAD/s (mad.lo.u32, measured)"),
+        "imad_wide": (wide, "IMAD.WIDE/s (mad.wide.u32, measured)"),
+        "dp4a": (rates["dp4a"], "dp4a/s (measured)"),
+        "mad64": (rates["mad64"], "64-bit mad.lo/s (mad.lo.u64, measured)"),
+        "mad64x2": (rates["mad64"] / 2, "64x64->128 multiply-adds/s (two 64-bit mads each, measured rate / 2)"),
+        "mad64x32": (1.0 / (1.0 / wide + 1.0 / imad),
+                     "64x32-bit multiply-adds/s (a widening and a 32-bit multiply-add each, measured rates)"),
+        "dfma": (rates["dfma"], "DFMA/s (fma.rn.f64, measured)"),
+        "mma_s8": (rates["mma_s8"], "int8 mma.sync ops/s (m16n8k32, measured)"),
+    })
 
 
 def measured_peaks():
@@ -313,7 +318,7 @@ def compressed_1024(gfp, torch, inputs, flush, f64_peak):
     dev = A.device
     out = {"workload": "Q-adic compressed GEMM and all forms, p=3, m=k=n=1024, uniform residues"}
     tpk = tensor_peaks()
-    pipes = dict(PIPES, dfma=(f64_peak / 2, "DFMA/s (half the measured cuBLAS DGEMM flops/s)"))
+    pipes = PIPES
     base = {}
 
     def rec(name, ms, work=None, pipe=None, **extra):
@@ -523,8 +528,8 @@ TRAFFIC = {}
 
 KERNEL_NAMES = {"plain": "simt_gemm_kernel<PlainP>", "dp4a": "simt_gemm_kernel<Dp4aT>",
                 "dot_u64": "simt_gemm_kernel<DotU64>", "mixed_u64": "simt_gemm_kernel<MixedU64>",
-                "tc_mma_s8": "mma_s8_kernel", "tc_f16": "tc_f16_kernel<TcCfg<256, fp16>>",
-                "tc_f8": "tc_f16_kernel<TcCfg<256, e4m3>>", "tc_e2m1": "tc_e2m1_kernel"}
+                "tc_mma_s8": "mma_s8_kernel", "tc_f16": "tc_pair_kernel<PairCfg<256, fp16>>",
+                "tc_f8": "tc_pair_kernel<PairCfg<256, e4m3>>", "tc_e2m1": "tc_pair_kernel<PairCfg<192, e2m1>>"}
 
 
 def main():
@@ -571,6 +576,8 @@ def main():
     B_h = inputs.residues(g, P, K, N)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
+    rates = gfp.gfp_pipe_rates()                        # untimed: measured instruction rates
+    set_pipes(rates)
     best, _ = gfp.gfp_dot_autotune(P, M, K, N)          # untimed: word, d, Q, k-block for this shape
     tuned = (best["word"], best["d"], best["Q"], best["kb"])
     step = Step(gfp, torch, A, B, tuned)
@@ -712,6 +719,7 @@ def main():
                         "h2d_bytes_per_step": 2 * M * K, "d2h_bytes_per_step": step.products * M * N},
                 "gpu_launches": step.launches * args.steps,
                 "roofline": roofline, "forms": forms, "clocks": clk, "cpu_baseline": cpu,
+                "pipe_rates": {k: round(v / 1e12, 4) for k, v in rates.items()},
                 "measured_peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}}
         line.update(extras)
         print(json.dumps(line), flush=True)

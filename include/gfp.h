@@ -357,6 +357,21 @@ GFP_API gfp_status gfp_gemm_compressed_vb(uint32_t p, int64_t m, int64_t k, int6
 GFP_API gfp_status gfp_selftest_wait_limit(void *workspace, size_t ws_bytes, uint32_t limit_ms, int *status,
                                            void *stream);
 
+/* Measured instruction rates of this GPU (no counterpart in the paper): the
+ * ceilings against which the CUDA-core forms are reported.  rates[i]
+ * receives operations per second of, in order: 0 the 32-bit multiply-add
+ * (mad.lo.u32), 1 the widening 32 x 32 -> 64-bit multiply-add
+ * (mad.wide.u32), 2 the 64-bit multiply-add keeping the low 64 bits
+ * (mad.lo.u64, one step of the dot form in 64-bit words), 3 the four-byte
+ * dot product (dp4a), 4 the double-precision fused multiply-add (fma.rn.f64),
+ * 5 the int8 warp MMA (mma.sync m16n8k32 s8, counted as 2 x 16 x 8 x 32
+ * operations each); the first min(n_rates, 6) are written.  Each is 8 independent chains of
+ * the instruction per thread on 4 CTAs of 256 threads per SM, best of three
+ * timed runs.  workspace: >= 256 bytes of device memory, 256-byte aligned
+ * (a sink for the chains' values).  Synchronizes the stream; takes a few
+ * milliseconds.  Errors: GFP_EINVAL, GFP_EWORKSPACE, GFP_ECUDA. */
+GFP_API gfp_status gfp_pipe_rates(double *rates, int n_rates, void *workspace, size_t ws_bytes, void *stream);
+
 /* Autotuner of the dot form for one product (no counterpart in the paper,
  * which fixes the word): a smaller Q -- the bound of eq. (lower) applied to
  * a k-block kb -- leaves room for more coefficients per word at the price of

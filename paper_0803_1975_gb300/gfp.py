@@ -38,7 +38,7 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
            "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax",
            "gfp_winograd_workspace_size", "gfp_gemm_compressed_winograd", "gfp_dot_autotune_workspace_size",
-           "gfp_dot_autotune", "gfp_selftest_wait_limit")
+           "gfp_dot_autotune", "gfp_selftest_wait_limit", "gfp_pipe_rates")
 
 
 class GfpError(RuntimeError):
@@ -108,6 +108,8 @@ def load():
     L.gfp_dot_autotune.restype = st
     L.gfp_selftest_wait_limit.argtypes = [vp, ctypes.c_size_t, u32, ctypes.POINTER(ip), vp]
     L.gfp_selftest_wait_limit.restype = st
+    L.gfp_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ip, vp, ctypes.c_size_t, vp]
+    L.gfp_pipe_rates.restype = st
     L.gfp_winograd_workspace_size.argtypes = [i64, i64, i64, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
     L.gfp_winograd_workspace_size.restype = st
     L.gfp_gemm_compressed_winograd.argtypes = [u32, i64, i64, i64, ip, u64, vp, i64, vp, i64, vp, i64, ip, vp,
@@ -420,6 +422,20 @@ def gfp_selftest_wait_limit(limit_ms: int = 100, device=None, stream=None) -> in
     _check(L.gfp_selftest_wait_limit(ctypes.c_void_p(ws.data_ptr()), ws.numel(), limit_ms, ctypes.byref(out),
                                      _stream(ws, stream)), "gfp_selftest_wait_limit")
     return out.value
+
+
+PIPE_RATES = ("imad", "imad_wide", "mad64", "dp4a", "dfma", "mma_s8")
+
+
+def gfp_pipe_rates(device=None, stream=None) -> dict:
+    """Measured instruction rates (operations per second) of the current GPU:
+    {"imad", "imad_wide", "mad64", "dp4a", "dfma", "mma_s8"}."""
+    L = load()
+    ws = torch.empty(256, dtype=torch.uint8, device=device or "cuda")
+    out = (ctypes.c_double * len(PIPE_RATES))()
+    _check(L.gfp_pipe_rates(out, len(PIPE_RATES), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(ws, stream)),
+           "gfp_pipe_rates")
+    return dict(zip(PIPE_RATES, list(out)))
 
 
 def gfp_winograd_workspace_size(m: int, k: int, n: int, d: int, levels: int) -> int:

@@ -228,3 +228,13 @@ def test_e2m1_workspace_and_prime_limit(L):
         assert L.gfp_gemm(p, 8, 8, 8, a, 8, a, 8, a, 8, gfp.ALGOS["tc_e2m1"], a, 1 << 20, None) == 5
     # without its workspace
     assert L.gfp_gemm(5, 64, 64, 64, a, 64, a, 64, a, 64, gfp.ALGOS["tc_e2m1"], None, 0, None) == 7
+
+
+def test_pipe_rates_rejects_bad_arguments(L):
+    # host-side checks, before any CUDA call
+    out = (ctypes.c_double * 5)()
+    assert L.gfp_pipe_rates(None, 5, ctypes.c_void_p(256), 256, None) == 1          # GFP_EINVAL
+    assert L.gfp_pipe_rates(out, 0, ctypes.c_void_p(256), 256, None) == 1
+    assert L.gfp_pipe_rates(out, 5, None, 256, None) == 7                            # GFP_EWORKSPACE
+    assert L.gfp_pipe_rates(out, 5, ctypes.c_void_p(256), 255, None) == 7
+    assert L.gfp_pipe_rates(out, 5, ctypes.c_void_p(257), 256, None) == 7
