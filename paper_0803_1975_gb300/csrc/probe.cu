@@ -2,12 +2,14 @@
 // forms are built from, measured on the GPU at hand, so that their kernels
 // can be reported against measured ceilings (no counterpart in the paper).
 //
-// Each probe runs 8 independent dependency chains of one instruction per
-// thread (4 chains of int8 warp MMAs per warp), `iters` steps each, on 4 CTAs
-// of 256 threads per SM (32 warps per SM hide the instruction latencies),
-// timed with CUDA events (best of 3 after one untimed run).  Every chain feeds the next step of itself, so no
-// step can be hoisted or folded; the chains' values reach a conditional
-// store that never happens but that the compiler cannot rule out.
+// Each probe runs independent dependency chains of one instruction per
+// thread (8; 16 for the double-precision FMA, whose latency is longer; 4
+// chains of int8 warp MMAs per warp), `iters` steps each, on 4 CTAs of 256
+// threads per SM (32 warps per SM hide the instruction latencies), timed
+// with CUDA events (best of 3 after one untimed run).  Every chain feeds the
+// next step of itself, so no step can be hoisted or folded; the chains'
+// values reach a conditional store that never happens but that the compiler
+// cannot rule out.
 #include <cstdint>
 
 #include "gfp_internal.h"
@@ -16,19 +18,21 @@ namespace gfp {
 namespace {
 
 constexpr int kChains = 8;
+constexpr int kFpChains = 16;
 
 template <int OP>
 __global__ void __launch_bounds__(256) pipe_probe_kernel(uint64_t *sink, uint32_t seed, int iters) {
     const uint32_t x = seed | 1u, y = seed * 2654435761u;
     uint32_t a[kChains];
     uint64_t w[kChains];
-    double f[kChains];
+    double f[kFpChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) {
         a[c] = threadIdx.x * 97u + c;
         w[c] = ((uint64_t)blockIdx.x << 32) | (threadIdx.x + c);
-        f[c] = 1.0 + 1e-9 * (threadIdx.x + c);
     }
+#pragma unroll
+    for (int c = 0; c < kFpChains; ++c) f[c] = 1.0 + 1e-9 * (threadIdx.x + c);
     const double fx = 0.999999, fy = 1e-7;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
@@ -41,7 +45,10 @@ __global__ void __launch_bounds__(256) pipe_probe_kernel(uint64_t *sink, uint32_
                 asm volatile("mad.lo.u64 %0, %0, %1, %2;" : "+l"(w[c]) : "l"((uint64_t)x), "l"((uint64_t)y));
             else if constexpr (OP == 3)   // four byte products and their sum (dp4a)
                 asm volatile("dp4a.u32.u32 %0, %0, %1, %0;" : "+r"(a[c]) : "r"(x));
-            else if constexpr (OP == 4)   // double-precision fused multiply-add
+        }
+        if constexpr (OP == 4) {          // double-precision fused multiply-add
+#pragma unroll
+            for (int c = 0; c < kFpChains; ++c)
                 asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(f[c]) : "d"(fx), "d"(fy));
         }
         if constexpr (OP == 5) {
@@ -64,7 +71,9 @@ __global__ void __launch_bounds__(256) pipe_probe_kernel(uint64_t *sink, uint32_
     }
     uint64_t v = 0;
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) v += a[c] + w[c] + (uint64_t)__double_as_longlong(f[c]);
+    for (int c = 0; c < kChains; ++c) v += a[c] + w[c];
+#pragma unroll
+    for (int c = 0; c < kFpChains; ++c) v += (uint64_t)__double_as_longlong(f[c]);
     if (v == 0x9E3779B97F4A7C15ull) sink[0] = v;
 }
 
@@ -97,7 +106,9 @@ gfp_status time_probe(uint64_t *sink, int grid, int iters, cudaStream_t s, doubl
     cudaEventDestroy(e1);
     // OP 5 counts operations of the MMA: each warp issues kChains / 2 MMAs
     // of 2 x 16 x 8 x 32 per step
-    const double per_step = OP == 5 ? (double)grid * 8.0 * (kChains / 2) * 2.0 * 16 * 8 * 32 : (double)grid * 256.0 * kChains;
+    const double per_step = OP == 5   ? (double)grid * 8.0 * (kChains / 2) * 2.0 * 16 * 8 * 32
+                            : OP == 4 ? (double)grid * 256.0 * kFpChains
+                                      : (double)grid * 256.0 * kChains;
     if (st == GFP_OK) *per_s = per_step * iters / (best * 1e-3);
     return st;
 }
