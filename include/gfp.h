@@ -333,6 +333,30 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
                                        void *C, int64_t ldc, int64_t kb,
                                        void *stream);
 
+/* ReduceAndCompress fused into the dot form: procedure (compC) of Section
+ * 2.2, equation (1), CC = ReduceAndCompress(CA x CB), in one launch.  The
+ * product is that of gfp_gemm_compressed(GFP_FORM_DOT, word) -- CA m x
+ * ceil(k/(d+1)) words (ROWS_REV of A, lda words), CB ceil(k/(d+1)) x n words
+ * (COLS of B, ldb words), (d, Q, kb) within the bounds of gfp_params -- and
+ * its residues C = A B mod p, instead of being stored as bytes, are written
+ * as reversed-row words of the same machine word (Section 2.1, missing
+ * entries zero as in Section 2.3):
+ *     CC[i][w] = sum_{s=0..d_out} C[i][w(d_out+1)+s] Q_out^(d_out-s),
+ * m x ceil(n/(d_out+1)) words, ldcc words: the left operand (layout
+ * ROWS_REV) of a further product with C on the left, e.g. the next power of
+ * a chain A^l (a (d, Q) valid for every product of the chain may serve as
+ * both (d, Q) and (d_out, Q_out)).  word: GFP_WORD_U64 or GFP_WORD_U32
+ * (GFP_EUNSUPPORTED otherwise); (d_out, Q_out) must give words that `word`
+ * holds (the rule of gfp_pack).  Nothing is allocated; one kernel launch.
+ * Errors: GFP_EINVAL, GFP_EPRIME, GFP_EQ, GFP_EBOUND, GFP_EUNSUPPORTED,
+ * GFP_ECUDA. */
+GFP_API gfp_status gfp_gemm_compressed_compc(uint32_t p, int64_t m, int64_t k, int64_t n,
+                                             int d, uint64_t Q, gfp_word word,
+                                             const void *CA, int64_t lda,
+                                             const void *CB, int64_t ldb, int64_t kb,
+                                             int d_out, uint64_t Q_out,
+                                             void *CC, int64_t ldcc, void *stream);
+
 /* gfp_gemm_compressed with (d, Q, kb) validated against the value-aware bound
  * k amax_a amax_b < Q of gfp_params_vb (entries of A at most amax_a, of B at
  * most amax_b, a precondition).  The kernels are the same. */

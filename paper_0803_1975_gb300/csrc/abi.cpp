@@ -179,6 +179,26 @@ GFP_API gfp_status gfp_gemm_compressed(uint32_t p, int64_t m, int64_t k, int64_t
                                   ldc, kb, stream);
 }
 
+GFP_API gfp_status gfp_gemm_compressed_compc(uint32_t p, int64_t m, int64_t k, int64_t n, int d, uint64_t Q,
+                                             gfp_word word, const void *CA, int64_t lda, const void *CB,
+                                             int64_t ldb, int64_t kb, int d_out, uint64_t Q_out, void *CC,
+                                             int64_t ldcc, void *stream) {
+    if (m < 0 || k < 0 || n < 0 || kb < 0 || d_out < 0) return GFP_EINVAL;
+    if (word_bytes(word) == 0) return GFP_EINVAL;
+    if (word != GFP_WORD_U64 && word != GFP_WORD_U32) return GFP_EUNSUPPORTED;
+    gfp_status st = check_dqt(p, k, d, Q, GFP_FORM_DOT, word, kb);
+    if (st != GFP_OK) return st;
+    st = check_pack(p, d_out, Q_out, word);
+    if (st != GFP_OK) return st;
+    if (m == 0 || n == 0) return GFP_OK;
+    const int64_t kc = cdiv(k, d + 1), wc = cdiv(n, d_out + 1);
+    if (!CC || ldcc < wc) return GFP_EINVAL;
+    if (kc > 0 && (!CA || !CB || lda < kc || ldb < n)) return GFP_EINVAL;
+    const int64_t kbw = (kb > 0 && kb < k) ? kb / (d + 1) : 0;
+    return launch_dot_compc(p, m, kc, n, d, log2_exact(Q), word, CA, lda, CB, ldb, kbw, d_out, log2_exact(Q_out),
+                            CC, ldcc, (cudaStream_t)stream);
+}
+
 GFP_API gfp_status gfp_amax(int64_t rows, int64_t cols, const uint8_t *X, int64_t ldx, uint32_t *out,
                             void *stream) {
     if (rows < 0 || cols < 0 || !out) return GFP_EINVAL;

@@ -100,6 +100,12 @@ struct DotParams {
     uint64_t mask;    // Q - 1
     double inv;       // 2^(-t d), exact
     int64_t kbw;      // words per k-block (blocked variants)
+    // ReduceAndCompress output (PackRowsRev): pd + 1 residues per word in
+    // base 2^pt, out_words words per row, bn_eff columns per CTA (set at launch)
+    int32_t pd;
+    uint32_t pt;
+    int64_t out_words;
+    int64_t bn_eff;
 };
 
 __device__ __forceinline__ uint32_t dot_reduce(uint64_t digit, uint32_t sum, const DotParams &prm,
@@ -185,6 +191,18 @@ struct DotU64Raw : DotBase<uint64_t, CarrySum, false> {
     __device__ static void mac(CarrySum &acc, uint64_t a, uint64_t b) { acc.mad64(a, b); }
     __device__ static uint32_t extract(const CarrySum &, const DotParams &) { return 0; }
     __device__ static uint64_t finish(const CarrySum &acc, uint32_t, const DotParams &) { return acc.value(); }
+};
+
+// ReduceAndCompress fused into the dot form (procedure (compC) of Section
+// 2.2, equation (1)): the product's residues, reduced mod p as the dot
+// policy's finish gives them, are written as reversed-row words
+// CC[i][w] = sum_s C[i][w(pd+1)+s] 2^(pt (pd - s)) (Section 2.1; missing
+// entries of the last word are zero, Section 2.3) -- the left operand of the
+// next product of a chain -- instead of bytes.
+template <class Inner, class OutW>
+struct PackRowsRev : Inner {
+    using GC = OutW;
+    static constexpr bool kPackOut = true;
 };
 
 // 64-bit words, 128-bit accumulator (largest word < 2^64, t(d+1) <= 128).
@@ -606,6 +624,10 @@ DotParams dot_params(uint32_t p, int d, int t, int64_t kbw) {
     prm.inv = 1.0;
     for (int i = 0; i < t * d; ++i) prm.inv *= 0.5;
     prm.kbw = kbw;
+    prm.pd = 0;
+    prm.pt = 0;
+    prm.out_words = 0;
+    prm.bn_eff = 0;
     return prm;
 }
 
@@ -662,6 +684,36 @@ gfp_status launch_dot(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t
         case GFP_WORD_U32W: e = run_dot<DotU32W>(CA, lda, CB, ldb, C, ldc, m, n, kc, prm, blocked, s); break;
         case GFP_WORD_U32: e = run_dot<DotU32>(CA, lda, CB, ldb, C, ldc, m, n, kc, prm, blocked, s); break;
         case GFP_WORD_F64: e = run_dot<DotF64>(CA, lda, CB, ldb, C, ldc, m, n, kc, prm, blocked, s); break;
+    }
+    return e == cudaSuccess ? GFP_OK : cuda_fail(e);
+}
+
+// The dot form with ReduceAndCompress in its epilogue: 64-bit or 32-bit
+// words in (blocked or not), words of the same width out.
+gfp_status launch_dot_compc(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t, gfp_word word,
+                            const void *CA, int64_t lda, const void *CB, int64_t ldb, int64_t kbw, int d_out,
+                            int t_out, void *CC, int64_t ldcc, cudaStream_t s) {
+    const bool blocked = kbw > 0 && kbw < kc;
+    DotParams prm = dot_params(p, d, t, blocked ? kbw : 0);
+    prm.pd = d_out;
+    prm.pt = (uint32_t)t_out;
+    prm.out_words = (n + d_out) / (d_out + 1);
+    prm.bn_eff = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (word == GFP_WORD_U64) {
+        auto a = static_cast<const uint64_t *>(CA);
+        auto b = static_cast<const uint64_t *>(CB);
+        auto c = static_cast<uint64_t *>(CC);
+        e = blocked ? run_simt<PackRowsRev<DotU64<true>, uint64_t>>(a, lda, b, ldb, c, ldcc, m, n, kc, prm, s)
+                    : run_simt<PackRowsRev<DotU64<false>, uint64_t>>(a, lda, b, ldb, c, ldcc, m, n, kc, prm, s);
+    } else if (word == GFP_WORD_U32) {
+        auto a = static_cast<const uint32_t *>(CA);
+        auto b = static_cast<const uint32_t *>(CB);
+        auto c = static_cast<uint32_t *>(CC);
+        e = blocked ? run_simt<PackRowsRev<DotU32<true>, uint32_t>>(a, lda, b, ldb, c, ldcc, m, n, kc, prm, s)
+                    : run_simt<PackRowsRev<DotU32<false>, uint32_t>>(a, lda, b, ldb, c, ldcc, m, n, kc, prm, s);
+    } else {
+        return GFP_EUNSUPPORTED;
     }
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
 }

@@ -99,6 +99,10 @@ gfp_status launch_block(bool pack, int64_t rows, int64_t cols, const uint8_t *X,
                         int64_t ldw, cudaStream_t s);
 gfp_status check_full(uint32_t p, int64_t k, int dq, int dth, uint64_t Q, gfp_word word);
 
+gfp_status launch_dot_compc(uint32_t p, int64_t m, int64_t kc, int64_t n, int d, int t, gfp_word word,
+                            const void *CA, int64_t lda, const void *CB, int64_t ldb, int64_t kbw, int d_out,
+                            int t_out, void *CC, int64_t ldcc, cudaStream_t s);
+
 // tensor-core forms (gemm_tc_mma.cu, gemm_tc_tcgen05.cu)
 size_t tc_mma_workspace(int64_t m, int64_t k, int64_t n);
 gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,

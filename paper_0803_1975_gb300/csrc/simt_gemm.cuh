@@ -23,13 +23,32 @@
 //   kBKMajor when true B is stored k-contiguous (element (k, j) of the
 //            product's B lies in row j of the stored matrix): its tile is
 //            read along k like A's, consecutive threads on consecutive k.
+//   kPackOut (optional, false when absent) when true the result residues
+//            P::finish gives are packed, in the epilogue, into reversed-row
+//            words of prm.pd + 1 residues in base 2^prm.pt (C then holds
+//            words of type P::GC, prm.out_words per row): a CTA covers
+//            prm.bn_eff = whole words' worth of columns, its residues pass
+//            through shared memory and each word is built by Horner.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
 namespace gfp {
+
+template <class P, class = void>
+struct pack_out_of : std::false_type {};
+template <class P>
+struct pack_out_of<P, std::void_t<decltype(P::kPackOut)>> : std::integral_constant<bool, P::kPackOut> {};
+
+// columns of the result one CTA covers
+template <class P, int BN>
+__host__ __device__ __forceinline__ int64_t tile_cols(const typename P::Params &prm) {
+    if constexpr (pack_out_of<P>::value) return prm.bn_eff;
+    else return BN;
+}
 
 // Read n contiguous elements of shared memory into registers with the widest
 // vector loads the run allows (the run starts on a 16-byte boundary when its
@@ -89,7 +108,7 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
     const int tid = threadIdx.x;
     const int tx = tid % NTX, ty = tid / NTX;
     const int64_t m0 = (int64_t)blockIdx.y * BM;
-    const int64_t n0 = (int64_t)blockIdx.x * BN;
+    const int64_t n0 = (int64_t)blockIdx.x * tile_cols<P, BN>(prm);
     // split k: slice z of the grid covers [kz0, kz1); the slices' raw sums
     // are added atomically (policies with kAtomic only)
     const int64_t kz0 = kchunk > 0 ? (int64_t)blockIdx.z * kchunk : 0;
@@ -182,18 +201,53 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
         }
     }
 
+    if constexpr (pack_out_of<P>::value) {
+        // ReduceAndCompress: the residues of the tile through shared memory
+        // (the operand tiles are free now), then whole reversed-row words
+        static_assert(sizeof(As) >= BM * BN, "the residue tile fits the A buffers");
+        __syncthreads();
+        uint8_t *res = reinterpret_cast<uint8_t *>(&As[0][0][0]);
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int64_t gi = m0 + (i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM));
-        if (gi >= M) continue;
+        for (int i = 0; i < TM; ++i) {
+            const int r = i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM);
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int64_t gj = n0 + (j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN));
-            if (gj < N) {
-                uint32_t s = 0;
-                if constexpr (P::kBlocked) s = sum[i][j];
-                if constexpr (P::kAtomic) atomicAdd(&C[gi * ldc + gj], P::finish(acc[i][j], s, prm));
-                else C[gi * ldc + gj] = P::finish(acc[i][j], s, prm);
+            for (int j = 0; j < TN; ++j) {
+                const int c = j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN);
+                uint32_t sm = 0;
+                if constexpr (P::kBlocked) sm = sum[i][j];
+                res[r * BN + c] = (uint8_t)P::finish(acc[i][j], sm, prm);
+            }
+        }
+        __syncthreads();
+        const int dp1 = prm.pd + 1;
+        const int W = (int)(prm.bn_eff / dp1);
+        const int64_t w0 = n0 / dp1;
+        for (int e = tid; e < BM * W; e += NT) {
+            const int r = e / W, w = e % W;
+            const int64_t gi = m0 + r, gw = w0 + w;
+            if (gi >= M || gw >= prm.out_words) continue;
+            uint64_t word = 0;
+            for (int q = 0; q < dp1; ++q) {
+                const int c = w * dp1 + q;
+                const uint64_t v = n0 + c < N ? res[r * BN + c] : 0u;   // missing entries count as zero
+                word = q ? (word << prm.pt) | v : v;
+            }
+            C[gi * ldc + gw] = (typename P::GC)word;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gi = m0 + (i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM));
+            if (gi >= M) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t gj = n0 + (j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN));
+                if (gj < N) {
+                    uint32_t s = 0;
+                    if constexpr (P::kBlocked) s = sum[i][j];
+                    if constexpr (P::kAtomic) atomicAdd(&C[gi * ldc + gj], P::finish(acc[i][j], s, prm));
+                    else C[gi * ldc + gj] = P::finish(acc[i][j], s, prm);
+                }
             }
         }
     }
@@ -205,7 +259,13 @@ cudaError_t simt_gemm_launch(const typename P::GA *A, int64_t lda, const typenam
                              int64_t K, const typename P::Params &prm, cudaStream_t s,
                              int splits = 1) {
     constexpr int NT = (BM / TM) * (BN / TN);
-    const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
+    typename P::Params prm2 = prm;
+    if constexpr (pack_out_of<P>::value) {
+        if (prm.pd < 0 || prm.pd + 1 > BN) return cudaErrorInvalidValue;
+        prm2.bn_eff = BN / (prm.pd + 1) * (prm.pd + 1);     // whole words per CTA
+    }
+    const int64_t cols = tile_cols<P, BN>(prm2);
+    const int64_t gx = (N + cols - 1) / cols, gy = (M + BM - 1) / BM;
     if (gx <= 0 || gy <= 0) return cudaSuccess;
     if (gx > 2147483647 || splits < 1 || splits > 65535) return cudaErrorInvalidConfiguration;
     int64_t kchunk = 0;
@@ -217,7 +277,7 @@ cudaError_t simt_gemm_launch(const typename P::GA *A, int64_t lda, const typenam
     for (int64_t r0 = 0; r0 < M; r0 += band) {
         const int64_t rows = M - r0 < band ? M - r0 : band;
         simt_gemm_kernel<P, BM, BN, BK, TM, TN><<<dim3((unsigned)gx, (unsigned)((rows + BM - 1) / BM), gz), NT, 0, s>>>(
-            A + r0 * lda, lda, B, ldb, C + r0 * ldc, ldc, rows, N, K, prm, kchunk);
+            A + r0 * lda, lda, B, ldb, C + r0 * ldc, ldc, rows, N, K, prm2, kchunk);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

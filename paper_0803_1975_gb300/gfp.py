@@ -38,7 +38,7 @@ EXPORTS = ("gfp_status_string", "gfp_last_cuda_error", "gfp_word_bytes", "gfp_pa
            "gfp_gemm_noalloc", "gfp_gemm_full", "gfp_params_full", "gfp_pack_block",
            "gfp_unpack_block", "gfp_params_vb", "gfp_pack_vb", "gfp_gemm_compressed_vb", "gfp_amax",
            "gfp_winograd_workspace_size", "gfp_gemm_compressed_winograd", "gfp_dot_autotune_workspace_size",
-           "gfp_dot_autotune", "gfp_selftest_wait_limit", "gfp_pipe_rates")
+           "gfp_dot_autotune", "gfp_selftest_wait_limit", "gfp_pipe_rates", "gfp_gemm_compressed_compc")
 
 
 class GfpError(RuntimeError):
@@ -110,6 +110,9 @@ def load():
     L.gfp_selftest_wait_limit.restype = st
     L.gfp_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ip, vp, ctypes.c_size_t, vp]
     L.gfp_pipe_rates.restype = st
+    L.gfp_gemm_compressed_compc.argtypes = [u32, i64, i64, i64, ip, u64, ip, vp, i64, vp, i64, i64, ip, u64, vp,
+                                            i64, vp]
+    L.gfp_gemm_compressed_compc.restype = st
     L.gfp_winograd_workspace_size.argtypes = [i64, i64, i64, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
     L.gfp_winograd_workspace_size.restype = st
     L.gfp_gemm_compressed_winograd.argtypes = [u32, i64, i64, i64, ip, u64, vp, i64, vp, i64, vp, i64, ip, vp,
@@ -422,6 +425,26 @@ def gfp_selftest_wait_limit(limit_ms: int = 100, device=None, stream=None) -> in
     _check(L.gfp_selftest_wait_limit(ctypes.c_void_p(ws.data_ptr()), ws.numel(), limit_ms, ctypes.byref(out),
                                      _stream(ws, stream)), "gfp_selftest_wait_limit")
     return out.value
+
+
+def gfp_gemm_compressed_compc(p: int, m: int, k: int, n: int, d: int, Q: int, word: str, CA: torch.Tensor,
+                              CB: torch.Tensor, d_out: int, Q_out: int, kb: int = 0,
+                              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ReduceAndCompress fused into the dot form: the residues of CA x CB
+    (gfp_gemm_compressed(dot, word)) as reversed-row words of (d_out, Q_out).
+    Returns (or fills) an m x ceil(n/(d_out+1)) tensor of words."""
+    L = load()
+    dt = WORD_DTYPE[word]
+    if out is None:
+        out = torch.empty((m, cdiv(n, d_out + 1)), dtype=dt, device=CA.device)
+    _mat(CA, dt, "CA")
+    _mat(CB, dt, "CB")
+    _mat(out, dt, "out")
+    _check(L.gfp_gemm_compressed_compc(p, m, k, n, d, Q, WORDS[word], ctypes.c_void_p(CA.data_ptr()), CA.stride(0),
+                                       ctypes.c_void_p(CB.data_ptr()), CB.stride(0), kb, d_out, Q_out,
+                                       ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream(out, stream)),
+           "gfp_gemm_compressed_compc")
+    return out
 
 
 PIPE_RATES = ("imad", "imad_wide", "mad64", "dp4a", "dfma", "mma_s8")

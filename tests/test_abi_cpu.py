@@ -238,3 +238,24 @@ def test_pipe_rates_rejects_bad_arguments(L):
     assert L.gfp_pipe_rates(out, 5, None, 256, None) == 7                            # GFP_EWORKSPACE
     assert L.gfp_pipe_rates(out, 5, ctypes.c_void_p(256), 255, None) == 7
     assert L.gfp_pipe_rates(out, 5, ctypes.c_void_p(257), 256, None) == 7
+
+
+def test_compc_rejects_before_any_launch(L):
+    """ReduceAndCompress entry point: host-side checks only (no GPU here)."""
+    a = ctypes.c_void_p(0x1000)
+    d, Q, _ = gfp.gfp_params(5, 64, 64, 64, "dot", "u64")
+    W = gfp.WORDS
+    # words other than u64 / u32
+    for word in ("u32w", "u64x128", "f64"):
+        assert L.gfp_gemm_compressed_compc(5, 64, 64, 64, d, Q, W[word], a, 64, a, 64, 0, d, Q, a, 64, None) == 5
+    # output words that do not fit the word (50 residues of 13 bits), Q_out not a power of two
+    assert L.gfp_gemm_compressed_compc(5, 64, 64, 64, d, Q, W["u64"], a, 64, a, 64, 0, 49, 2 ** 13, a, 64, None) == 3
+    assert L.gfp_gemm_compressed_compc(5, 64, 64, 64, d, Q, W["u64"], a, 64, a, 64, 0, d, 1000, a, 64, None) == 4
+    # input parameters outside eq. (lower)
+    assert L.gfp_gemm_compressed_compc(5, 64, 4096, 64, 1, 2 ** 10, W["u64"], a, 4096, a, 64, 0, 1, 2 ** 10, a, 64,
+                                       None) == 3
+    # output leading dimension below ceil(n / (d_out + 1)), null output
+    assert L.gfp_gemm_compressed_compc(5, 64, 64, 64, d, Q, W["u64"], a, 64, a, 64, 0, 1, 2 ** 13, a, 31, None) == 1
+    assert L.gfp_gemm_compressed_compc(5, 64, 64, 64, d, Q, W["u64"], a, 64, a, 64, 0, 1, 2 ** 13, None, 64, None) == 1
+    # empty products launch nothing
+    assert L.gfp_gemm_compressed_compc(5, 0, 64, 64, d, Q, W["u64"], None, 64, None, 64, 0, d, Q, None, 64, None) == 0
