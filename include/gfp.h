@@ -386,7 +386,8 @@ GFP_API gfp_status gfp_selftest_wait_limit(void *workspace, size_t ws_bytes, uin
  * receives operations per second of, in order: 0 the 32-bit multiply-add
  * (mad.lo.u32), 1 the widening 32 x 32 -> 64-bit multiply-add
  * (mad.wide.u32), 2 the 64-bit multiply-add keeping the low 64 bits
- * (mad.lo.u64, one step of the dot form in 64-bit words), 3 the four-byte
+ * (mad.lo.u64 of full 64-bit operands, one step of the dot form in 64-bit
+ * words), 3 the four-byte
  * dot product (dp4a), 4 the double-precision fused multiply-add (fma.rn.f64),
  * 5 the int8 warp MMA (mma.sync m16n8k32 s8, counted as 2 x 16 x 8 x 32
  * operations each); the first min(n_rates, 6) are written.  Each is 8 independent chains of

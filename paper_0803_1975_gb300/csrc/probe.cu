@@ -21,7 +21,8 @@ constexpr int kChains = 8;
 constexpr int kFpChains = 16;
 
 template <int OP>
-__global__ void __launch_bounds__(256) pipe_probe_kernel(uint64_t *sink, uint32_t seed, int iters) {
+__global__ void __launch_bounds__(256) pipe_probe_kernel(uint64_t *sink, uint32_t seed, uint64_t x64, uint64_t y64,
+                                                         int iters) {
     const uint32_t x = seed | 1u, y = seed * 2654435761u;
     uint32_t a[kChains];
     uint64_t w[kChains];
@@ -41,8 +42,9 @@ __global__ void __launch_bounds__(256) pipe_probe_kernel(uint64_t *sink, uint32_
                 asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[c]) : "r"(x), "r"(y));
             else if constexpr (OP == 1)   // 32 x 32 -> 64-bit multiply-add (IMAD.WIDE)
                 asm volatile("{\n.reg .u32 lo;\ncvt.u32.u64 lo, %0;\nmad.wide.u32 %0, lo, %1, %0;\n}" : "+l"(w[c]) : "r"(x));
-            else if constexpr (OP == 2)   // 64-bit multiply-add, low half (the dot form's word step)
-                asm volatile("mad.lo.u64 %0, %0, %1, %2;" : "+l"(w[c]) : "l"((uint64_t)x), "l"((uint64_t)y));
+            else if constexpr (OP == 2)   // 64-bit multiply-add, low half (the dot form's word step);
+                                          // both factors full 64-bit values the compiler cannot see
+                asm volatile("mad.lo.u64 %0, %0, %1, %2;" : "+l"(w[c]) : "l"(x64), "l"(y64));
             else if constexpr (OP == 3)   // four byte products and their sum (dp4a)
                 asm volatile("dp4a.u32.u32 %0, %0, %1, %0;" : "+r"(a[c]) : "r"(x));
         }
@@ -89,7 +91,8 @@ gfp_status time_probe(uint64_t *sink, int grid, int iters, cudaStream_t s, doubl
     gfp_status st = GFP_OK;
     for (int rep = 0; rep < 4 && st == GFP_OK; ++rep) {
         cudaEventRecord(e0, s);
-        pipe_probe_kernel<OP><<<grid, 256, 0, s>>>(sink, 0x12345u + rep, iters);
+        const uint64_t x64 = 0x9E3779B97F4A7C15ull ^ ((uint64_t)rep << 40), y64 = 0xD1B54A32D192ED03ull + rep;
+        pipe_probe_kernel<OP><<<grid, 256, 0, s>>>(sink, 0x12345u + rep, x64, y64, iters);
         cudaEventRecord(e1, s);
         st = check_launch();
         if (st != GFP_OK) break;

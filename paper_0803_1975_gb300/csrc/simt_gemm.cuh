@@ -107,8 +107,22 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
 
     const int tid = threadIdx.x;
     const int tx = tid % NTX, ty = tid / NTX;
-    const int64_t m0 = (int64_t)blockIdx.y * BM;
-    const int64_t n0 = (int64_t)blockIdx.x * tile_cols<P, BN>(prm);
+    // Tile order: groups of 16 tile-rows walk the tile-columns together, so
+    // that the B panels a group shares are read from DRAM once per group
+    // instead of once per tile-row (at 16384^3 in 64-bit words the row-major
+    // order read 185 GB per launch for 1.4 GB of operands).
+    int64_t by, bx;
+    {
+        const int64_t gxn = gridDim.x, gyn = gridDim.y, G = 16;
+        const int64_t lin = (int64_t)blockIdx.y * gxn + blockIdx.x;
+        const int64_t first = lin / (G * gxn) * G;
+        const int64_t gsize = gyn - first < G ? gyn - first : G;
+        const int64_t r = lin % (G * gxn);
+        by = first + r % gsize;
+        bx = r / gsize;
+    }
+    const int64_t m0 = by * BM;
+    const int64_t n0 = bx * tile_cols<P, BN>(prm);
     // split k: slice z of the grid covers [kz0, kz1); the slices' raw sums
     // are added atomically (policies with kAtomic only)
     const int64_t kz0 = kchunk > 0 ? (int64_t)blockIdx.z * kchunk : 0;
