@@ -79,8 +79,8 @@ def set_pipes(rates):
         "dp4a": (rates["dp4a"], "dp4a/s (measured)"),
         "mad64": (rates["mad64"], "64-bit mad.lo/s (mad.lo.u64, measured)"),
         "mad64x2": (rates["mad64"] / 2, "64x64->128 multiply-adds/s (two 64-bit mads each, measured rate / 2)"),
-        "mad64x32": (1.0 / (1.0 / wide + 1.0 / imad),
-                     "64x32-bit multiply-adds/s (a widening and a 32-bit multiply-add each, measured rates)"),
+        "mad64x32": (imad / 3, "64x32-bit multiply-adds/s (three 32-bit multiply-adds each: low and high "
+                               "halves of residue x low word half with its carry, residue x high half; measured IMAD / 3)"),
         "dfma": (rates["dfma"], "DFMA/s (fma.rn.f64, measured)"),
         "mma_s8": (rates["mma_s8"], "int8 mma.sync ops/s (m16n8k32, measured)"),
     })
