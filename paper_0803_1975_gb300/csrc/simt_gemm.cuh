@@ -114,11 +114,11 @@ simt_gemm_kernel(const typename P::GA *__restrict__ A, int64_t lda,
     // grouped one 23.5 GB; the right-compressed form ran 9% faster).  Byte
     // and 32-bit operands keep the row-major order, measured faster for them
     // (the classical product at 16384^3: 274 against 312 ms).
-    int64_t by, bx;
-    {
-        constexpr int64_t G = (sizeof(SA) == 8 || sizeof(SB) == 8) ? 16 : 1;
+    int64_t by = blockIdx.y, bx = blockIdx.x;
+    if constexpr (sizeof(SA) == 8 || sizeof(SB) == 8) {
+        constexpr int64_t G = 16;
         const int64_t gxn = gridDim.x, gyn = gridDim.y;
-        const int64_t lin = (int64_t)blockIdx.y * gxn + blockIdx.x;
+        const int64_t lin = by * gxn + bx;
         const int64_t first = lin / (G * gxn) * G;
         const int64_t gsize = gyn - first < G ? gyn - first : G;
         const int64_t r = lin % (G * gxn);
