@@ -774,12 +774,47 @@ __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ld
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// e2m1 code of a centred residue |c| <= 3, exact: 0, 1, 2, 3 are the codes
-// 0x0, 0x2, 0x4, 0x5 (1 = 2^0 x 1.0, 2 = 2^1 x 1.0, 3 = 2^1 x 1.5), bit 3
-// the sign.
-__device__ __forceinline__ uint32_t e2m1_code(int c) {
-    const uint32_t a = (uint32_t)(c < 0 ? -c : c);
-    return (a == 3u ? 5u : 2u * a) | (c < 0 ? 8u : 0u);
+// e2m1 codes of the residues 0..7 of p, centred (c = r - p [r > (p-1)/2]),
+// as the 8 bytes of a lookup table (lo: residues 0-3, hi: 4-7).  The
+// centred residues |c| <= 3 are e2m1 values exactly: 0, 1, 2, 3 are the
+// codes 0x0, 0x2, 0x4, 0x5 (1 = 2^0 x 1.0, 2 = 2^1 x 1.0, 3 = 2^1 x 1.5),
+// bit 3 the sign.
+void e2m1_table(uint32_t p, uint32_t *lo, uint32_t *hi) {
+    const int h = p == 2 ? 1 : (int)(p - 1) / 2;
+    uint32_t t[2] = {0, 0};
+    for (int r = 0; r < 8 && r < (int)p; ++r) {
+        const int c = r > h ? r - (int)p : r;
+        const uint32_t a = (uint32_t)(c < 0 ? -c : c);
+        const uint32_t code = (a == 3u ? 5u : 2u * a) | (c < 0 ? 8u : 0u);
+        t[r >> 2] |= code << (8 * (r & 3));
+    }
+    *lo = t[0];
+    *hi = t[1];
+}
+
+// Four bytes, each below 16, as the four nibbles of the low 16 bits.
+__device__ __forceinline__ uint32_t nib4(uint32_t w) {
+    return (w & 0xFu) | ((w >> 4) & 0xF0u) | ((w >> 8) & 0xF00u) | ((w >> 12) & 0xF000u);
+}
+// The e2m1 codes of four residue bytes (each below 8): one byte permute
+// selecting from the table, the residues as selectors.
+__device__ __forceinline__ uint32_t codes4(uint32_t w, uint32_t lo, uint32_t hi) {
+    return __byte_perm(lo, hi, nib4(w));
+}
+// 16 consecutive residues as four words (zero outside [c0, limit) or when
+// !row_ok): one 16-byte load when the run is inside the row and aligned.
+__device__ __forceinline__ uint4 load16w(const uint8_t *src, int64_t c0, int64_t limit, bool row_ok) {
+    if (row_ok && c0 + 16 <= limit && (reinterpret_cast<uintptr_t>(src) & 15) == 0)
+        return *reinterpret_cast<const uint4 *>(src);
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        if (row_ok && c0 + e < limit) w[e >> 2] |= (uint32_t)src[e] << (8 * (e & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+// eight residues (two words) as eight packed codes, value e in nibble e
+__device__ __forceinline__ uint32_t pack8(uint32_t x, uint32_t y, uint32_t lo, uint32_t hi) {
+    return nib4(codes4(x, lo, hi)) | (nib4(codes4(y, lo, hi)) << 16);
 }
 
 // Packed e2m1 operands, two values per byte (value 2e in the low nibble of
@@ -787,40 +822,38 @@ __device__ __forceinline__ uint32_t e2m1_code(int c) {
 // out[i][l] = code(centre(A[i][l])) for i < m, l < k; zero elsewhere in mp x kp.
 // One thread per 32 consecutive values of a row.
 __global__ void to_e2m1_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m, int64_t k,
-                                    uint8_t *__restrict__ out, int64_t kp, int64_t mp, uint32_t p, uint32_t h) {
+                                    uint8_t *__restrict__ out, int64_t kp, int64_t mp, uint32_t lo, uint32_t hi) {
     const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 32;
     if (l >= kp) return;
     for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
-        uint32_t r0[16], r1[16];
-        load16(A + i * lda + l, l, k, i < m, r0);
-        load16(A + i * lda + l + 16, l + 16, k, i < m, r1);
-        uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            w[e >> 3] |= e2m1_code(centre_i(r0[e], p, h)) << (4 * (e & 7));
-            w[2 + (e >> 3)] |= e2m1_code(centre_i(r1[e], p, h)) << (4 * (e & 7));
-        }
-        *reinterpret_cast<uint4 *>(out + i * (kp / 2) + l / 2) = make_uint4(w[0], w[1], w[2], w[3]);
+        const uint4 a = load16w(A + i * lda + l, l, k, i < m);
+        const uint4 b = load16w(A + i * lda + l + 16, l + 16, k, i < m);
+        *reinterpret_cast<uint4 *>(out + i * (kp / 2) + l / 2) =
+            make_uint4(pack8(a.x, a.y, lo, hi), pack8(a.z, a.w, lo, hi), pack8(b.x, b.y, lo, hi),
+                       pack8(b.z, b.w, lo, hi));
     }
 }
 
 // out[j][l] = code(centre(B[l][j])) for l < k, j < n; zero elsewhere in np x kp.
-// 64 x 64 tiles through shared memory as in to_op_transpose_kernel; each
-// thread writes 16 values (8 bytes) of one row of B^T.
+// 64 x 64 tiles through shared memory as in to_op_transpose_kernel (codes
+// written four at a time); each thread writes 16 values (8 bytes) of one row
+// of B^T.
 __global__ void to_e2m1_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k, int64_t n,
-                                         uint8_t *__restrict__ out, int64_t kp, int64_t np, uint32_t p,
-                                         uint32_t h) {
-    __shared__ uint8_t tile[64][64 + 4];
+                                         uint8_t *__restrict__ out, int64_t kp, int64_t np, uint32_t lo,
+                                         uint32_t hi) {
+    __shared__ __align__(16) uint8_t tile[64][64 + 4];
     const int64_t l0 = (int64_t)blockIdx.x * 64;
     const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
     for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
         const int64_t j0 = jt * 64;
         {
             const int64_t l = l0 + r;
-            uint32_t v[16];
-            load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) tile[r][q + e] = (uint8_t)e2m1_code(centre_i(v[e], p, h));
+            const uint4 v = load16w(B + l * ldb + j0 + q, j0 + q, n, l < k);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&tile[r][q]);
+            dst[0] = codes4(v.x, lo, hi);
+            dst[1] = codes4(v.y, lo, hi);
+            dst[2] = codes4(v.z, lo, hi);
+            dst[3] = codes4(v.w, lo, hi);
         }
         __syncthreads();
         const int64_t j = j0 + r;
@@ -1600,14 +1633,15 @@ gfp_status launch_tc_e2m1(uint32_t p, int64_t m, int64_t k, int64_t n, const uin
     int *status = static_cast<int *>(ws);
     uint8_t *Aop = static_cast<uint8_t *>(ws) + 256;
     uint8_t *Bop = Aop + mp * rowb;
-    const uint32_t h = p == 2 ? 1u : (p - 1) / 2;
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e);
     {
         dim3 grid((unsigned)((kp / 32 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
         dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
-        to_e2m1_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, p, h);
-        to_e2m1_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
+        uint32_t lo, hi;
+        e2m1_table(p, &lo, &hi);
+        to_e2m1_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, lo, hi);
+        to_e2m1_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, lo, hi);
     }
     CUtensorMap ma, mb;
     if (!make_map(&ma, Aop, mp, rowb, BM, true) || !make_map(&mb, Bop, np, rowb, BN, true))
