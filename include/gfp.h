@@ -390,11 +390,16 @@ GFP_API gfp_status gfp_selftest_wait_limit(void *workspace, size_t ws_bytes, uin
  * words), 3 the four-byte
  * dot product (dp4a), 4 the double-precision fused multiply-add (fma.rn.f64),
  * 5 the int8 warp MMA (mma.sync m16n8k32 s8, counted as 2 x 16 x 8 x 32
- * operations each); the first min(n_rates, 6) are written.  Each is 8 independent chains of
+ * operations each); and, in flops per second, the dense rates of the
+ * tcgen05 MMA kinds the tensor-core forms use -- 6 kind::f16 (fp16),
+ * 7 kind::f8f6f4 (e4m3), 8 the block-scaled kind::mxf4 (e2m1) -- each
+ * measured with 128 x 256 MMAs issued back to back by one thread per SM from
+ * fixed tiles in shared memory (0 if its bounded wait ran out); the first
+ * min(n_rates, 9) are written.  Each is 8 independent chains of
  * the instruction per thread on 4 CTAs of 256 threads per SM, best of three
  * timed runs.  workspace: >= 256 bytes of device memory, 256-byte aligned
- * (a sink for the chains' values).  Synchronizes the stream; takes a few
- * milliseconds.  Errors: GFP_EINVAL, GFP_EWORKSPACE, GFP_ECUDA. */
+ * (a sink for the chains' values and a status word).  Synchronizes the
+ * stream; takes about 0.1 s.  Errors: GFP_EINVAL, GFP_EWORKSPACE, GFP_ECUDA. */
 GFP_API gfp_status gfp_pipe_rates(double *rates, int n_rates, void *workspace, size_t ws_bytes, void *stream);
 
 /* Autotuner of the dot form for one product (no counterpart in the paper,

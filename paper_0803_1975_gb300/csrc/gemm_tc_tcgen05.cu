@@ -1590,6 +1590,137 @@ gfp_status tc_selftest_wait_limit(void *ws, size_t ws_bytes, uint64_t limit_ns, 
     return e == cudaSuccess ? GFP_OK : cuda_fail(e);
 }
 
+namespace {
+
+// ---- throughput probe of the tcgen05 MMA kinds the tensor-core forms use
+//
+// One CTA per SM; one thread issues `iters` x 4 MMAs of 128 x 256 x (16 fp16 |
+// 32 e4m3 | 64 e2m1 with unit scale factors) from fixed zero tiles in shared
+// memory, back to back into one accumulator, then waits (bounded) for them:
+// the dense rate of the tensor pipe for that kind with no operand traffic.
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) tc_rate_kernel(int iters, int *status, uint64_t limit_ns) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    constexpr int TILE_BYTES = (128 + 256) * ROWB;      // A 128 rows, B 256 rows of 128 bytes
+    const uint32_t bar = base + TILE_BYTES;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(gbase + TILE_BYTES + 8);
+    for (int i = threadIdx.x; i < TILE_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(gbase)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *slot;
+    if constexpr (KIND == 2) {
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        for (uint32_t c = 256; c < 512; c += 8)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+                             tmem + lanes + c),
+                         "r"(0x7F7F7F7Fu)
+                         : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        __syncthreads();
+        fence_after();
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = KIND == 2 ? (1u << 7) | (1u << 10) | (1u << 23) | (32u << 17) | (8u << 24)
+                                         : (1u << 4) | (32u << 17) | (8u << 24);
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_issue<KIND>(tmem, smem_desc(base + kk * 32), smem_desc(base + 128 * ROWB + kk * 32), idesc,
+                                (it | kk) ? 1u : 0u, tmem + 256, tmem + 288);
+        mma_commit(bar);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try(bar, 0))
+            if (globaltimer() - t0 > limit_ns) {
+                atomicCAS(status, 0, 1);
+                break;
+            }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
+template <int KIND>
+gfp_status tc_rate_one(int *status, cudaStream_t s, double *flops_per_s) {
+    constexpr int SMEM = (128 + 256) * ROWB + 1024 + 64;
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(tc_rate_kernel<KIND>), SMEM, attr);
+    if (ea != cudaSuccess) return cuda_fail(ea);
+    constexpr int iters = 20000;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError());
+    }
+    gfp_status st = GFP_OK;
+    float best = 0;
+    for (int rep = 0; rep < 4 && st == GFP_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        tc_rate_kernel<KIND><<<num_sms(), 128, SMEM, s>>>(iters, status, 2000000000ull);
+        cudaEventRecord(e1, s);
+        st = check_launch();
+        if (st != GFP_OK) break;
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e);
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0 || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double kdim = KIND == 2 ? 64 : KIND == 1 ? 32 : 16;
+    if (st == GFP_OK) *flops_per_s = (double)num_sms() * iters * 4 * 2.0 * 128 * 256 * kdim / (best * 1e-3);
+    return st;
+}
+
+}  // namespace
+
+// Dense tcgen05 rates (flops/s) of kind::f16, kind::f8f6f4 (e4m3) and the
+// block-scaled kind::mxf4 (e2m1); a kind whose bounded wait ran out gets 0.
+gfp_status tc_mma_rates(double *out, int *status_dev, cudaStream_t s) {
+    int status_host = 0;
+    gfp_status st = GFP_OK;
+    double r[3] = {0, 0, 0};
+    for (int kind = 0; kind < 3 && st == GFP_OK; ++kind) {
+        cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int), s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        st = kind == 0 ? tc_rate_one<0>(status_dev, s, &r[0])
+                       : kind == 1 ? tc_rate_one<1>(status_dev, s, &r[1]) : tc_rate_one<2>(status_dev, s, &r[2]);
+        if (st != GFP_OK) break;
+        e = cudaMemcpyAsync(&status_host, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (status_host != 0) r[kind] = 0;
+    }
+    for (int i = 0; i < 3; ++i) out[i] = r[i];
+    return st;
+}
+
 gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A, int64_t lda,
                         const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws,
                         size_t ws_bytes, cudaStream_t s) {

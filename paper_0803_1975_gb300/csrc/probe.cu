@@ -1,6 +1,8 @@
 // Instruction-rate probes: the throughput of the instructions the CUDA-core
 // forms are built from, measured on the GPU at hand, so that their kernels
 // can be reported against measured ceilings (no counterpart in the paper).
+// The dense rates of the tcgen05 kinds come from tc_mma_rates
+// (gemm_tc_tcgen05.cu).
 //
 // Each probe runs independent dependency chains of one instruction per
 // thread (8; 16 for the double-precision FMA, whose latency is longer; 4
@@ -131,15 +133,17 @@ GFP_API gfp_status gfp_pipe_rates(double *rates, int n_rates, void *workspace, s
     const int grid = 4 * num_sms();
     const int iters = 4096;
     gfp_status st = GFP_OK;
-    double r[6] = {0, 0, 0, 0, 0, 0};
+    double r[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (st == GFP_OK && n_rates > 0) st = time_probe<0>(sink, grid, iters, s, &r[0]);
     if (st == GFP_OK && n_rates > 1) st = time_probe<1>(sink, grid, iters, s, &r[1]);
     if (st == GFP_OK && n_rates > 2) st = time_probe<2>(sink, grid, iters, s, &r[2]);
     if (st == GFP_OK && n_rates > 3) st = time_probe<3>(sink, grid, iters, s, &r[3]);
     if (st == GFP_OK && n_rates > 4) st = time_probe<4>(sink, grid, iters / 16, s, &r[4]);
     if (st == GFP_OK && n_rates > 5) st = time_probe<5>(sink, grid, iters / 4, s, &r[5]);
+    if (st == GFP_OK && n_rates > 6)
+        st = tc_mma_rates(&r[6], reinterpret_cast<int *>(static_cast<uint8_t *>(workspace) + 128), s);
     if (st != GFP_OK) return st;
-    for (int i = 0; i < n_rates && i < 6; ++i) rates[i] = r[i];
+    for (int i = 0; i < n_rates && i < 9; ++i) rates[i] = r[i];
     return GFP_OK;
 }
 

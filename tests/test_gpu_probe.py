@@ -19,8 +19,11 @@ def test_pipe_rates_are_plausible():
     props = torch.cuda.get_device_properties(0)
     ceiling = props.multi_processor_count * 128 * 2.2e9
     for name, v in r.items():
-        if name != "mma_s8":
+        if name != "mma_s8" and not name.startswith("tc_"):
             assert 0 < v < ceiling, (name, v)
     assert 0 < r["mma_s8"] < 2.25e15
+    # dense tcgen05 rates: below GB300's nominal dense peaks (2.25 / 4.5 / 13.5
+    # PFLOP/s at the boost clock), each kind faster than the one before
+    assert 0 < r["tc_f16"] < 2.5e15 and r["tc_f16"] < r["tc_f8"] < 5e15 and r["tc_f8"] < r["tc_e2m1"] < 15e15
     assert r["dfma"] < r["imad"] / 4
     assert r["mad64"] < r["imad"]
