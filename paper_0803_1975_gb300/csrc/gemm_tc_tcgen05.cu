@@ -157,11 +157,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 // KIND 0: kind::f16; 1: kind::f8f6f4; 2: kind::mxf4 with scale factors
-// (ue8m0, one per 32 values of k) read from tensor memory at sfa, sfb.
+// (ue8m0, one per 32 values of k) read from tensor memory at sfa, sfb;
+// 3: kind::mxf4nvf4 with ue4m3 scale factors, one per 16 values of k.
 template <int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                           uint32_t accum, uint32_t sfa = 0, uint32_t sfb = 0) {
-    if constexpr (KIND == 2)
+    if constexpr (KIND == 3)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, [%5], [%6], p;\n}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum), "r"(sfa), "r"(sfb)
+            : "memory");
+    else if constexpr (KIND == 2)
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n}\n"
@@ -1626,12 +1633,14 @@ __global__ void __launch_bounds__(128, 1) tc_rate_kernel(int iters, int *status,
     __syncthreads();
     fence_after();
     const uint32_t tmem = *slot;
-    if constexpr (KIND == 2) {
+    if constexpr (KIND >= 2) {
+        // unit scale factors: ue8m0 127 (mxf4) or ue4m3 0x38 (mxf4nvf4) in every byte
         const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        const uint32_t one = KIND == 3 ? 0x38383838u : 0x7F7F7F7Fu;
         for (uint32_t c = 256; c < 512; c += 8)
             asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
                              tmem + lanes + c),
-                         "r"(0x7F7F7F7Fu)
+                         "r"(one)
                          : "memory");
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
@@ -1639,8 +1648,9 @@ __global__ void __launch_bounds__(128, 1) tc_rate_kernel(int iters, int *status,
         fence_after();
     }
     if (threadIdx.x == 0) {
-        const uint32_t idesc = KIND == 2 ? (1u << 7) | (1u << 10) | (1u << 23) | (32u << 17) | (8u << 24)
-                                         : (1u << 4) | (32u << 17) | (8u << 24);
+        const uint32_t idesc = KIND == 2   ? (1u << 7) | (1u << 10) | (1u << 23) | (32u << 17) | (8u << 24)
+                               : KIND == 3 ? (1u << 7) | (1u << 10) | (32u << 17) | (8u << 24)
+                                           : (1u << 4) | (32u << 17) | (8u << 24);
         for (int it = 0; it < iters; ++it)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
@@ -1693,31 +1703,34 @@ gfp_status tc_rate_one(int *status, cudaStream_t s, double *flops_per_s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const double kdim = KIND == 2 ? 64 : KIND == 1 ? 32 : 16;
+    const double kdim = KIND >= 2 ? 64 : KIND == 1 ? 32 : 16;
     if (st == GFP_OK) *flops_per_s = (double)num_sms() * iters * 4 * 2.0 * 128 * 256 * kdim / (best * 1e-3);
     return st;
 }
 
 }  // namespace
 
-// Dense tcgen05 rates (flops/s) of kind::f16, kind::f8f6f4 (e4m3) and the
-// block-scaled kind::mxf4 (e2m1); a kind whose bounded wait ran out gets 0.
+// Dense tcgen05 rates (flops/s) of kind::f16, kind::f8f6f4 (e4m3), the
+// block-scaled kind::mxf4 and kind::mxf4nvf4 (e2m1); a kind whose bounded
+// wait ran out gets 0.
 gfp_status tc_mma_rates(double *out, int *status_dev, cudaStream_t s) {
     int status_host = 0;
     gfp_status st = GFP_OK;
-    double r[3] = {0, 0, 0};
-    for (int kind = 0; kind < 3 && st == GFP_OK; ++kind) {
+    double r[4] = {0, 0, 0, 0};
+    for (int kind = 0; kind < 4 && st == GFP_OK; ++kind) {
         cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int), s);
         if (e != cudaSuccess) return cuda_fail(e);
-        st = kind == 0 ? tc_rate_one<0>(status_dev, s, &r[0])
-                       : kind == 1 ? tc_rate_one<1>(status_dev, s, &r[1]) : tc_rate_one<2>(status_dev, s, &r[2]);
+        st = kind == 0   ? tc_rate_one<0>(status_dev, s, &r[0])
+             : kind == 1 ? tc_rate_one<1>(status_dev, s, &r[1])
+             : kind == 2 ? tc_rate_one<2>(status_dev, s, &r[2])
+                         : tc_rate_one<3>(status_dev, s, &r[3]);
         if (st != GFP_OK) break;
         e = cudaMemcpyAsync(&status_host, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e);
         if (status_host != 0) r[kind] = 0;
     }
-    for (int i = 0; i < 3; ++i) out[i] = r[i];
+    for (int i = 0; i < 4; ++i) out[i] = r[i];
     return st;
 }
 

@@ -118,7 +118,7 @@ gfp_status launch_tc_e2m1(uint32_t p, int64_t m, int64_t k, int64_t n, const uin
                           const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc, void *ws, size_t ws_bytes,
                           cudaStream_t s);
 int64_t tc_kblock_e2m1(uint32_t p);
-gfp_status tc_mma_rates(double *out, int *status_dev, cudaStream_t s);   // fp16, e4m3, e2m1 flops/s     // largest kb (multiple of 256) with kb ((p-1)/2)^2 + p < 2^24
+gfp_status tc_mma_rates(double *out, int *status_dev, cudaStream_t s);   // fp16, e4m3, e2m1 (mxf4, mxf4nvf4) flops/s     // largest kb (multiple of 256) with kb ((p-1)/2)^2 + p < 2^24
 gfp_status launch_tc_f8(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t *A,
                         int64_t lda, const uint8_t *B, int64_t ldb, uint8_t *C, int64_t ldc,
                         void *ws, size_t ws_bytes, cudaStream_t s);
