@@ -395,8 +395,9 @@ GFP_API gfp_status gfp_selftest_wait_limit(void *workspace, size_t ws_bytes, uin
  * 7 kind::f8f6f4 (e4m3), 8 the block-scaled kind::mxf4 (e2m1, ue8m0 scale
  * factors per 32 values), 9 kind::mxf4nvf4 (e2m1, ue4m3 scale factors per 16
  * values) -- each measured with 128 x 256 MMAs issued back to back by one
- * thread per SM from fixed tiles in shared memory (0 if its bounded wait ran
- * out); the first min(n_rates, 10) are written.  Each is 8 independent chains of
+ * thread per SM from fixed tiles in shared memory -- and 10, 11, 12 the
+ * kinds of 6, 7, 8 on CTA pairs (256 x 256 MMAs, cta_group::2); 0 where a
+ * bounded wait ran out.  The first min(n_rates, 13) are written.  Each is 8 independent chains of
  * the instruction per thread on 4 CTAs of 256 threads per SM, best of three
  * timed runs.  workspace: >= 256 bytes of device memory, 256-byte aligned
  * (a sink for the chains' values and a status word).  Synchronizes the

@@ -1673,7 +1673,10 @@ __global__ void __launch_bounds__(128, 1) tc_rate_kernel(int iters, int *status,
 
 template <int KIND>
 gfp_status tc_rate_one(int *status, cudaStream_t s, double *flops_per_s) {
-    constexpr int SMEM = (128 + 256) * ROWB + 1024 + 64;
+    // more than half of an SM's shared memory: one CTA per SM, so that no CTA
+    // waits for another's 512 tensor-memory columns
+    constexpr int SMEM = 120 * 1024;
+    static_assert(SMEM >= (128 + 256) * ROWB + 1024 + 64, "the tiles fit");
     static std::atomic<uint64_t> attr{0};
     const cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(tc_rate_kernel<KIND>), SMEM, attr);
     if (ea != cudaSuccess) return cuda_fail(ea);
@@ -1708,6 +1711,118 @@ gfp_status tc_rate_one(int *status, cudaStream_t s, double *flops_per_s) {
     return st;
 }
 
+// The same probe on CTA pairs: the even CTA of a cluster of two issues
+// 256 x 256 MMAs (cta_group::2) reading both CTAs' zero tiles; the dense
+// rate the CTA-pair kernels can reach.
+template <int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
+tc_pair_rate_kernel(int iters, int *status, uint64_t limit_ns) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    constexpr int TILE_BYTES = (128 + 128) * ROWB;      // A 128 rows, half of B: 128 rows
+    const uint32_t bar = base + TILE_BYTES;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(gbase + TILE_BYTES + 8);
+    for (int i = threadIdx.x; i < TILE_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(gbase)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int warp = threadIdx.x >> 5;
+    const bool leader = cluster_rank() == 0;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    cluster_sync();
+    fence_after();
+    const uint32_t tmem = *slot;
+    if constexpr (KIND == 2) {
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        for (uint32_t c = 256; c < 512; c += 8)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+                             tmem + lanes + c),
+                         "r"(0x7F7F7F7Fu)
+                         : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    cluster_sync();
+    fence_after();
+    if (threadIdx.x == 0) {
+        if (leader) {
+            const uint32_t idesc = (KIND == 2 ? (1u << 7) | (1u << 10) | (1u << 23) : (1u << 4)) | (32u << 17) |
+                                   (16u << 24);
+            for (int it = 0; it < iters; ++it)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_issue_pair<KIND>(tmem, smem_desc(base + kk * 32), smem_desc(base + 128 * ROWB + kk * 32),
+                                         idesc, (it | kk) ? 1u : 0u, tmem + 256, tmem + 288);
+            mma_commit_pair(bar);
+        }
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try(bar, 0))
+            if (globaltimer() - t0 > limit_ns) {
+                atomicCAS(status, 0, 1);
+                break;
+            }
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
+template <int KIND>
+gfp_status tc_pair_rate_one(int *status, cudaStream_t s, double *flops_per_s) {
+    // one CTA per SM (see tc_rate_one): CTAs of different pairs never share an
+    // SM, so no pair's collective allocation can wait on another pair's
+    constexpr int SMEM = 120 * 1024;
+    static_assert(SMEM >= (128 + 128) * ROWB + 1024 + 64, "the tiles fit");
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t ea = smem_attr_once(reinterpret_cast<const void *>(tc_pair_rate_kernel<KIND>), SMEM, attr);
+    if (ea != cudaSuccess) return cuda_fail(ea);
+    constexpr int iters = 10000;
+    const int grid = num_sms() / 2 * 2;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError());
+    }
+    gfp_status st = GFP_OK;
+    float best = 0;
+    for (int rep = 0; rep < 4 && st == GFP_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        tc_pair_rate_kernel<KIND><<<grid, 128, SMEM, s>>>(iters, status, 2000000000ull);
+        cudaEventRecord(e1, s);
+        st = check_launch();
+        if (st != GFP_OK) break;
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e);
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0 || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double kdim = KIND == 2 ? 64 : KIND == 1 ? 32 : 16;
+    if (st == GFP_OK) *flops_per_s = (double)(grid / 2) * iters * 4 * 2.0 * 256 * 256 * kdim / (best * 1e-3);
+    return st;
+}
+
 }  // namespace
 
 // Dense tcgen05 rates (flops/s) of kind::f16, kind::f8f6f4 (e4m3), the
@@ -1716,21 +1831,24 @@ gfp_status tc_rate_one(int *status, cudaStream_t s, double *flops_per_s) {
 gfp_status tc_mma_rates(double *out, int *status_dev, cudaStream_t s) {
     int status_host = 0;
     gfp_status st = GFP_OK;
-    double r[4] = {0, 0, 0, 0};
-    for (int kind = 0; kind < 4 && st == GFP_OK; ++kind) {
+    double r[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int kind = 0; kind < 7 && st == GFP_OK; ++kind) {
         cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int), s);
         if (e != cudaSuccess) return cuda_fail(e);
         st = kind == 0   ? tc_rate_one<0>(status_dev, s, &r[0])
              : kind == 1 ? tc_rate_one<1>(status_dev, s, &r[1])
              : kind == 2 ? tc_rate_one<2>(status_dev, s, &r[2])
-                         : tc_rate_one<3>(status_dev, s, &r[3]);
+             : kind == 3 ? tc_rate_one<3>(status_dev, s, &r[3])
+             : kind == 4 ? tc_pair_rate_one<0>(status_dev, s, &r[4])
+             : kind == 5 ? tc_pair_rate_one<1>(status_dev, s, &r[5])
+                         : tc_pair_rate_one<2>(status_dev, s, &r[6]);
         if (st != GFP_OK) break;
         e = cudaMemcpyAsync(&status_host, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e);
         if (status_host != 0) r[kind] = 0;
     }
-    for (int i = 0; i < 4; ++i) out[i] = r[i];
+    for (int i = 0; i < 7; ++i) out[i] = r[i];
     return st;
 }
 

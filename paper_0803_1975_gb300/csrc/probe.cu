@@ -133,7 +133,7 @@ GFP_API gfp_status gfp_pipe_rates(double *rates, int n_rates, void *workspace, s
     const int grid = 4 * num_sms();
     const int iters = 4096;
     gfp_status st = GFP_OK;
-    double r[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double r[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (st == GFP_OK && n_rates > 0) st = time_probe<0>(sink, grid, iters, s, &r[0]);
     if (st == GFP_OK && n_rates > 1) st = time_probe<1>(sink, grid, iters, s, &r[1]);
     if (st == GFP_OK && n_rates > 2) st = time_probe<2>(sink, grid, iters, s, &r[2]);
@@ -143,7 +143,7 @@ GFP_API gfp_status gfp_pipe_rates(double *rates, int n_rates, void *workspace, s
     if (st == GFP_OK && n_rates > 6)
         st = tc_mma_rates(&r[6], reinterpret_cast<int *>(static_cast<uint8_t *>(workspace) + 128), s);
     if (st != GFP_OK) return st;
-    for (int i = 0; i < n_rates && i < 10; ++i) rates[i] = r[i];
+    for (int i = 0; i < n_rates && i < 13; ++i) rates[i] = r[i];
     return GFP_OK;
 }
 

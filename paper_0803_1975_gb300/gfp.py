@@ -448,14 +448,14 @@ def gfp_gemm_compressed_compc(p: int, m: int, k: int, n: int, d: int, Q: int, wo
 
 
 PIPE_RATES = ("imad", "imad_wide", "mad64", "dp4a", "dfma", "mma_s8", "tc_f16", "tc_f8", "tc_e2m1",
-              "tc_e2m1_nvf4")
+              "tc_e2m1_nvf4", "tc_pair_f16", "tc_pair_f8", "tc_pair_e2m1")
 
 
 def gfp_pipe_rates(device=None, stream=None) -> dict:
     """Measured instruction rates (operations per second) of the current GPU:
     {"imad", "imad_wide", "mad64", "dp4a", "dfma", "mma_s8"} in operations per
-    second and {"tc_f16", "tc_f8", "tc_e2m1", "tc_e2m1_nvf4"} (dense tcgen05
-    rates) in flops
+    second and {"tc_f16", "tc_f8", "tc_e2m1", "tc_e2m1_nvf4", "tc_pair_f16",
+    "tc_pair_f8", "tc_pair_e2m1"} (dense tcgen05 rates) in flops
     per second."""
     L = load()
     ws = torch.empty(256, dtype=torch.uint8, device=device or "cuda")
