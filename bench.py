@@ -707,11 +707,13 @@ def main():
              "launches": launches, "share_of_step": round(fm / step_mean, 4),
              "roofline": form_roofline(pm, work, peak=peak, unit=unit)}
         r.update(step.dot.get(n, {}))
-        if n in ("tc_f16", "tc_f8", "tc_e2m1") and rates.get(n):
-            # cross-check: the dense rate of the same tcgen05 kind measured by the
-            # library's MMA probe on this GPU (no operand traffic)
-            r["roofline"]["mma_probe_peak"] = rates[n]
-            r["roofline"]["frac_of_mma_probe"] = round(work / (pm * 1e-3) / rates[n], 4)
+        if n in ("tc_f16", "tc_f8", "tc_e2m1") and rates.get("tc_pair_" + n[3:]):
+            # cross-check: the dense rate of the same tcgen05 kind on CTA pairs,
+            # measured by the library's MMA probe on this GPU (no operand
+            # traffic, the full 2.07 GHz clock)
+            probe = rates["tc_pair_" + n[3:]]
+            r["roofline"]["mma_probe_peak"] = probe
+            r["roofline"]["frac_of_mma_probe"] = round(work / (pm * 1e-3) / probe, 4)
         forms[n] = r
     dom = max(step.forms, key=lambda n: np.mean(prod_ms[n]))
     dwork, dpipe = step.forms[dom][3], step.forms[dom][4]
