@@ -143,8 +143,10 @@ typedef enum gfp_layout {
  *                        The workspace holds both operands packed two values
  *                        per byte.  GFP_EUNSUPPORTED for p > 7.  Same status
  *                        word.
- *  GFP_ALGO_AUTO       : GFP_ALGO_TC_F8 for p <= 31, else GFP_ALGO_TC_F16 (the
- *                        fastest exact forms measured on GB300). */
+ *  GFP_ALGO_AUTO       : GFP_ALGO_TC_E2M1 for p <= 7 when k >= 6144 and
+ *                        m, n >= 4096; otherwise GFP_ALGO_TC_F8 for p <= 31,
+ *                        else GFP_ALGO_TC_F16 (the fastest exact forms
+ *                        measured on GB300). */
 typedef enum gfp_algo {
     GFP_ALGO_AUTO = 0,
     GFP_ALGO_PLAIN = 1,

@@ -259,3 +259,15 @@ def test_compc_rejects_before_any_launch(L):
     assert L.gfp_gemm_compressed_compc(5, 64, 64, 64, d, Q, W["u64"], a, 64, a, 64, 0, 1, 2 ** 13, None, 64, None) == 1
     # empty products launch nothing
     assert L.gfp_gemm_compressed_compc(5, 0, 64, 64, d, Q, W["u64"], None, 64, None, 64, 0, d, Q, None, 64, None) == 0
+
+
+def test_auto_algorithm_choice(L):
+    """GFP_ALGO_AUTO resolves on the host: its workspace is that of the form it
+    picks (e2m1 for large products with p <= 7 and k >= 6144, else e4m3 for
+    p <= 31, else fp16)."""
+    ws = gfp.gfp_gemm_workspace_size
+    assert ws(5, 8192, 8192, 8192, "auto") == ws(5, 8192, 8192, 8192, "tc_e2m1")
+    assert ws(5, 8192, 4096, 8192, "auto") == ws(5, 8192, 4096, 8192, "tc_f8")
+    assert ws(11, 8192, 8192, 8192, "auto") == ws(11, 8192, 8192, 8192, "tc_f8")
+    assert ws(251, 8192, 8192, 8192, "auto") == ws(251, 8192, 8192, 8192, "tc_f16")
+    assert ws(3, 1024, 8192, 1024, "auto") == ws(3, 1024, 8192, 1024, "tc_f8")
