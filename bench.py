@@ -554,7 +554,12 @@ def run_reference(args, rank, world):
 # DRAM bytes (read + written) of one launch of a step kernel, from an ncu
 # capture of that kernel on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum); None where no capture of the current kernel exists.
-TRAFFIC = {}
+# dot_u64: 17,443,889,920 read + 282,185,472 written, from
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:simt_gemm -c 1 \
+#       python -m paper_0803_1975_gb300.run_case --form dot --word u64 --p 5 --size 16384 --reps 1 --warmup 0
+# (operands 1.43 GB, result 0.27 GB).
+TRAFFIC = {"dot_u64": 17443889920 + 282185472}
 
 KERNEL_NAMES = {"plain": "simt_gemm_kernel<PlainP>", "dp4a": "simt_gemm_kernel<Dp4aT>",
                 "dot_u64": "simt_gemm_kernel<DotU64>", "mixed_u64": "simt_gemm_kernel<MixedU64>",
