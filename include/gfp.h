@@ -500,7 +500,14 @@ GFP_API gfp_status gfp_unpack_block(uint32_t p, int64_t rows, int64_t cols, cons
 
 /* One product of a batch: C = A B mod p with A m x k, B k x n, C m x n uint8
  * row-major device matrices.  (The batched workload of this library squares
- * adjacency matrices: A == B, m == k == n.) */
+ * adjacency matrices: A == B, m == k == n.)
+ * flags: 0, or GFP_PROBLEM_B_IS_A_T when the caller knows that B equals the
+ * transpose of A (n == m, B[l][j] == A[j][l]; e.g. B = A with A symmetric,
+ * the square of an undirected graph's adjacency matrix).  The tensor-core
+ * tiles then stage one copy of A and read it for both operands, with no
+ * transpose.  The flag is a precondition, not checked: if B is not A^T the
+ * result is that of A A^T.  Any other bit: GFP_EINVAL. */
+#define GFP_PROBLEM_B_IS_A_T 1
 typedef struct gfp_problem {
     uint32_t p;
     int32_t m, k, n;
@@ -508,7 +515,7 @@ typedef struct gfp_problem {
     const uint8_t *B;
     uint8_t *C;
     int32_t lda, ldb, ldc;
-    int32_t reserved;       /* must be 0 */
+    int32_t flags;
 } gfp_problem;
 
 /* Bytes of workspace gfp_gemm_batched needs for `count` problems. */

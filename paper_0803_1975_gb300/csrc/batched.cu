@@ -729,7 +729,8 @@ int tc8_bin(int64_t k) {
 
 gfp_status validate_problem(const gfp_problem &q) {
     if (!is_prime_small(q.p)) return GFP_EPRIME;
-    if (q.m < 0 || q.k < 0 || q.n < 0 || q.reserved != 0) return GFP_EINVAL;
+    if (q.m < 0 || q.k < 0 || q.n < 0 || (q.flags & ~GFP_PROBLEM_B_IS_A_T) != 0) return GFP_EINVAL;
+    if ((q.flags & GFP_PROBLEM_B_IS_A_T) && q.n != q.m) return GFP_EINVAL;
     if (q.m == 0 || q.n == 0) return GFP_OK;
     if (!q.C || q.ldc < q.n) return GFP_EINVAL;
     if (q.k > 0 && (!q.A || !q.B || q.lda < q.k || q.ldb < q.n)) return GFP_EINVAL;
@@ -882,7 +883,10 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             T.ktiles = (int32_t)((row_bytes + 127) / 128);
             T.klast = (int32_t)((row_bytes - 128 * (T.ktiles - 1)) / 32);
             T.rowA0 = (int32_t)tc_job(q.A, q.m, q.k, q.lda, q.p, f16 ? CONV_F16 : CONV_RAW, q.k);
-            T.rowB0 = (int32_t)tc_job(q.B, q.k, q.n, q.ldb, q.p, f16 ? CONV_F16_T : CONV_RAW_T, q.k);
+            // B^T rows: when B = A^T (the caller's flag) they are A's rows, staged once
+            T.rowB0 = (q.flags & GFP_PROBLEM_B_IS_A_T)
+                          ? T.rowA0
+                          : (int32_t)tc_job(q.B, q.k, q.n, q.ldb, q.p, f16 ? CONV_F16_T : CONV_RAW_T, q.k);
             T.m = q.m;
             T.n = q.n;
             T.k = q.k;

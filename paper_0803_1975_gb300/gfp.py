@@ -62,7 +62,7 @@ class Problem(ctypes.Structure):
     _fields_ = [("p", ctypes.c_uint32), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("n", ctypes.c_int32), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
                 ("C", ctypes.c_void_p), ("lda", ctypes.c_int32), ("ldb", ctypes.c_int32),
-                ("ldc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ldc", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 def lib_path() -> str:
@@ -492,15 +492,19 @@ def gfp_gemm_compressed_winograd(p: int, m: int, k: int, n: int, d: int, Q: int,
     return out
 
 
-def make_problems(items) -> ctypes.Array:
-    """items: iterable of (p, A, B, C) CUDA uint8 tensors -> gfp_problem array."""
+PROBLEM_B_IS_A_T = 1      # GFP_PROBLEM_B_IS_A_T
+
+
+def make_problems(items, flags: int = 0) -> ctypes.Array:
+    """items: iterable of (p, A, B, C) CUDA uint8 tensors -> gfp_problem array;
+    `flags` (e.g. PROBLEM_B_IS_A_T) is set on every problem."""
     items = list(items)
     arr = (Problem * max(len(items), 1))()
     for i, (p, A, B, C) in enumerate(items):
         m, k = A.shape
         n = B.shape[1]
         arr[i] = Problem(p, m, k, n, A.data_ptr(), B.data_ptr(), C.data_ptr(),
-                         max(A.stride(0), 1), max(B.stride(0), 1), max(C.stride(0), 1), 0)
+                         max(A.stride(0), 1), max(B.stride(0), 1), max(C.stride(0), 1), flags)
     return arr, len(items)
 
 

@@ -239,3 +239,45 @@ def test_batched_tcgen05_fp16_tiles():
     assert int(ws[192:196].cpu().numpy().view(np.int32)[0]) == 0
     for (p, A, B), (_, _, _, C) in zip(host_ops, items):
         assert (host(C) == oracle.gemm(p, A, B)).all(), (p, A.shape, B.shape)
+
+
+def test_adjacency_workload_b_is_a_transpose_flag():
+    """The same workload with each problem flagged B = A^T (true: A is
+    symmetric and B = A): the tensor-core tiles stage one copy of A for both
+    operands.  Every product equals the unflagged launch's bit for bit, and a
+    sample equals the oracle's."""
+    probs = inputs.batched_problems()
+    runs = []
+    for flags in (0, gfp.PROBLEM_B_IS_A_T):
+        items = []
+        for p, A in probs:
+            Ad = dev(A)
+            items.append((p, Ad, Ad, torch.full(A.shape, 255, dtype=torch.uint8, device="cuda")))
+        arr, cnt = gfp.make_problems(items, flags=flags)
+        gfp.gfp_gemm_batched(arr, cnt, "auto")
+        torch.cuda.synchronize()
+        runs.append([it[3].cpu().numpy() for it in items])
+    for i, (C0, C1) in enumerate(zip(*runs)):
+        assert (C0 == C1).all(), i
+    for i in range(0, len(probs), 97):
+        p, A = probs[i]
+        assert (runs[1][i] == oracle.gemm(p, A, A)).all(), i
+
+
+def test_b_is_a_transpose_flag_validation():
+    """The flag needs n == m; unknown bits are rejected (per-problem status
+    GFP_EINVAL); a flagged non-symmetric product gives A A^T, as documented."""
+    g = np.random.Generator(np.random.PCG64(31))
+    A = inputs.residues(g, 5, 40, 30)
+    B = inputs.residues(g, 5, 30, 50)
+    items = [(5, dev(A), dev(B), torch.empty((40, 50), dtype=torch.uint8, device="cuda"))]
+    for flags in (gfp.PROBLEM_B_IS_A_T, 2):
+        arr, cnt = gfp.make_problems(items, flags=flags)
+        _, r, sts = gfp.gfp_gemm_batched(arr, cnt, "auto", statuses=True)
+        torch.cuda.synchronize()
+        assert r == 1 and sts == [1]
+    At = np.ascontiguousarray(A.T)                  # B = A^T: 30 x 40, n = m = 40
+    C = torch.empty((40, 40), dtype=torch.uint8, device="cuda")
+    arr, cnt = gfp.make_problems([(5, dev(A), dev(At), C)], flags=gfp.PROBLEM_B_IS_A_T)
+    gfp.gfp_gemm_batched(arr, cnt, "tc_f8")
+    assert (host(C) == oracle.gemm(5, A, At)).all()
