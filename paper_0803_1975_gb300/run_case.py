@@ -37,6 +37,8 @@ def main():
     ap.add_argument("--levels", type=int, default=1, help="winograd: Strassen-Winograd levels")
     ap.add_argument("--primes", default="", help="batched: comma-separated primes replacing the workload's "
                                                  "p in {3, 5, 7} (cycled; 0/1 matrices are residues for any p)")
+    ap.add_argument("--symmetric", action="store_true",
+                    help="batched: declare B = A^T (true for the adjacency squares), one staged copy of A")
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--graph", type=int, default=0,
                     help="capture this many calls in one CUDA graph and report the time per call of its "
@@ -81,7 +83,7 @@ def main():
                 pp = primes[i % len(primes)]
             Ad = torch.from_numpy(Ah).cuda()
             items.append((pp, Ad, Ad, torch.empty(Ah.shape, dtype=torch.uint8, device="cuda")))
-        arr, cnt = gfp.make_problems(items)
+        arr, cnt = gfp.make_problems(items, flags=gfp.PROBLEM_B_IS_A_T if a.symmetric else 0)
         ws = torch.empty(gfp.gfp_batched_workspace_size(arr, cnt), dtype=torch.uint8, device="cuda")
         gfp.gfp_batched_prepare(arr, cnt, a.algo, ws)
         m = k = n = 0
