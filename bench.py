@@ -25,7 +25,8 @@ products and its kernel's fraction of the pipe it runs on; `roofline` is the
 step's dominant kernel.  Extra keys carry the other workloads:
 `compressed_1024` (p = 3, 1024^3, every machine word including FP64),
 `tensor_core_8192` (p in {3, 31, 251}, 8192^3), `reduce_compress` (the dot
-product with ReduceAndCompress fused, against a separate packing) and
+product with ReduceAndCompress fused, against a separate packing),
+`pack_unpack` (the conversions against HBM) and
 `batched` (4096 adjacency squares in one graph replay).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfp|reference]
@@ -433,6 +434,28 @@ def reduce_compress(gfp, torch, inputs, flush):
             "unit": UNIT}
 
 
+def pack_unpack(gfp, torch, A, flush):
+    """The conversions of the compressed forms at the headline size (p = 5,
+    16384^2, the dot form's u64 words, d+1 = 3): bytes read + written per call
+    against the measured HBM copy rate."""
+    d, Q, _ = gfp.gfp_params(P, M, K, N, "dot", "u64")
+    hbm = (measured_peaks().get("hbm_gbs") or 6800.0) * 1e9
+    CA = gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64")
+    CB = gfp.gfp_pack(P, A, d, Q, "cols", "u64")
+    CR = gfp.gfp_pack(P, A, d, Q, "rows", "u64")
+    X = torch.empty_like(A)
+    out = {"workload": "p=5, 16384^2 residues <-> u64 words of d+1=%d (t=%d)" % (d + 1, Q.bit_length() - 1)}
+    cases = (("pack_rows_rev", lambda: gfp.gfp_pack(P, A, d, Q, "rows_rev", "u64", out=CA), CA),
+             ("pack_cols", lambda: gfp.gfp_pack(P, A, d, Q, "cols", "u64", out=CB), CB),
+             ("unpack_rows", lambda: gfp.gfp_unpack(P, CR, M, N, d, Q, "rows", "u64", out=X), CR))
+    for name, fn, W in cases:
+        ms = event_time(torch, fn, 7, flush)
+        byts = A.numel() + W.numel() * 8
+        out[name] = {"ms": round(ms, 4), "bytes": byts,
+                     "roofline": form_roofline(ms, byts, peak=hbm, unit="bytes/s (MEASURED_PEAKS.json hbm_gbs)")}
+    return out
+
+
 def batched_measure(gfp, torch, inputs, flush, flags=0):
     """4096 squares of adjacency matrices in one grouped launch (CUDA graph).
     flags: gfp.PROBLEM_B_IS_A_T declares B = A^T (true here: A symmetric,
@@ -742,6 +765,7 @@ def main():
         extras["compressed_1024"] = compressed_1024(gfp, torch, inputs, flush, f64_peak)
         extras["tensor_core_8192"] = tensor_core_8192(gfp, torch, inputs, flush)
         extras["reduce_compress"] = reduce_compress(gfp, torch, inputs, flush)
+        extras["pack_unpack"] = pack_unpack(gfp, torch, A, flush)
         try:
             extras["batched"] = batched_measure(gfp, torch, inputs, flush)
             sym = batched_measure(gfp, torch, inputs, flush, flags=gfp.PROBLEM_B_IS_A_T)
