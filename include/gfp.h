@@ -505,8 +505,10 @@ GFP_API gfp_status gfp_unpack_block(uint32_t p, int64_t rows, int64_t cols, cons
  * transpose of A (n == m, B[l][j] == A[j][l]; e.g. B = A with A symmetric,
  * the square of an undirected graph's adjacency matrix).  The tensor-core
  * tiles then stage one copy of A and read it for both operands, with no
- * transpose.  The flag is a precondition, not checked: if B is not A^T the
- * result is that of A A^T.  Any other bit: GFP_EINVAL. */
+ * transpose, and since C = A A^T is symmetric they compute only the 128 x 128
+ * tiles on and above the diagonal, writing each one above it twice (as
+ * itself and transposed).  The flag is a precondition, not checked: if B is
+ * not A^T the result is that of A A^T.  Any other bit: GFP_EINVAL. */
 #define GFP_PROBLEM_B_IS_A_T 1
 typedef struct gfp_problem {
     uint32_t p;

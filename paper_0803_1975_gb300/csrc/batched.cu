@@ -658,6 +658,7 @@ bool dot32_params(uint32_t p, int64_t k, int *t_out, int *d_out, int *kbw_out) {
 struct TcHostProb {                          // a problem of the grouped tcgen05 launch
     int bin;                                 // k-stride bin of its operands
     int f16;                                 // centred fp16 operands (else raw e4m3)
+    int sym;                                 // B = A^T: tiles on and above the diagonal only
     int32_t rowA0, rowB0, ktiles, klast;     // rows in the bin's array, k in 128-slices,
                                              // 32-wide MMAs of the last slice
     int64_t m, n, k, ldc;
@@ -893,13 +894,16 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             T.ldc = q.ldc;
             T.C = q.C;
             T.p = q.p;
+            // B = A^T: C = A A^T is symmetric, so only the tiles on and above the
+            // diagonal are computed; each one above it is stored twice
+            T.sym = (q.flags & GFP_PROBLEM_B_IS_A_T) ? 1 : 0;
             const int ti = (int)plan.tc.size();
             plan.tc.push_back(T);
             const int tmn = (int)((q.m + 127) / 128), tnn = (int)((q.n + 127) / 128);
             for (int a = 0; a < tmn; ++a)
-                for (int b = 0; b < tnn; ++b) {
+                for (int b = T.sym ? a : 0; b < tnn; ++b) {
                     plan.tc_items.push_back(TcGroupItem{ti, (uint16_t)a, (uint16_t)b});
-                    tc_cost.push_back((double)T.ktiles + 2.0);
+                    tc_cost.push_back((double)T.ktiles + (T.sym && b > a ? 4.0 : 2.0));
                 }
             continue;
         }
@@ -1070,7 +1074,8 @@ gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
         Q.ktiles = T.ktiles;                 // one k-block: k within the kind's bound by eligibility
         Q.klast = T.klast;
         Q.bin = (int16_t)map_of[T.bin];
-        Q.kind = (int16_t)T.f16;
+        Q.kind = (int8_t)T.f16;
+        Q.sym = (int8_t)T.sym;
         Q.p = T.p;
         Q.m32 = (uint32_t)(0xFFFFFFFFull / T.p + 1);
         if (T.f16) {

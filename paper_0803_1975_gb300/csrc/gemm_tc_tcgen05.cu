@@ -285,6 +285,7 @@ struct TileInfo {
     int64_t ldc, m, n;
     uint32_t p, off, m32;
     float scale;
+    bool mirror;               // grouped, C symmetric: also store the tile transposed at (tn, tm)
 };
 
 // Walks the tiles of this CTA: a strided raster over one product, or this
@@ -337,6 +338,7 @@ struct TileWalk {
             t.off = np.off;
             t.m32 = np.m32;
             t.scale = np.scale;
+            t.mirror = np.sym && nit.tn != nit.tm;
             cur += 1;
             if (cur < end) fetch(cur);
         } else {
@@ -357,6 +359,7 @@ struct TileWalk {
             t.off = g.off;
             t.m32 = g.m32;
             t.scale = g.scale;
+            t.mirror = false;
             cur += gridDim.x;
         }
         return true;
@@ -583,7 +586,36 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const int64_t row0 = (int64_t)ti.tm * BM + q * 32;
                 const int nchunks = row0 >= ti.m ? 0 : (int)min((int64_t)(BN / 32), (ti.n - col0 + 31) / 32);
                 // the load of chunk c + 1 is in flight while chunk c is reduced and stored
-                auto store_chunk = [&](int c, const uint32_t(&w)[8]) {
+                // grouped, C symmetric: the transposed tile.  Row `row` of this tile is
+                // column `row` of C there, so the 32 lanes write 32 consecutive bytes of
+                // one of its rows per store (square tiles, m = n).
+                auto mirror_chunk = [&](int c, uint32_t(&w)[8]) {
+                    if constexpr (GROUPED && !BLOCKED) {
+                        if (ti.mirror && row < ti.m) {
+                            const int64_t tcol = col0 + c * 32, ldc = ti.ldc;
+                            uint8_t *dst = ti.C + tcol * ldc + row;
+                            if (tcol + 32 <= ti.n) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b, dst += ldc) *dst = (uint8_t)(w[e] >> (8 * b));
+                            } else {
+                                // the last columns of C: 4 bytes per pass, words shifted down
+                                const int nv = (int)(ti.n - tcol);
+#pragma unroll 1
+                                for (int i = 0; i < nv; i += 4) {
+#pragma unroll
+                                    for (int b = 0; b < 4; ++b, dst += ldc)
+                                        if (i + b < nv) *dst = (uint8_t)(w[0] >> (8 * b));
+#pragma unroll
+                                    for (int e = 0; e < 7; ++e) w[e] = w[e + 1];
+                                }
+                            }
+                        }
+                    }
+                };
+                // w is dead once both tiles are written (the mirror shifts it)
+                auto store_chunk = [&](int c, uint32_t(&w)[8]) {
                     const int64_t col = col0 + c * 32;
                     // warp-uniform: every row of C 16-byte aligned and 32 columns inside
                     const bool vec = col + 32 <= ti.n &&
@@ -594,10 +626,12 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             reinterpret_cast<uint4 *>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
                             reinterpret_cast<uint4 *>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
                         }
+                        mirror_chunk(c, w);
                     } else {
                         // through shared memory: one row segment per store instruction
 #pragma unroll
                         for (int e = 0; e < 8; ++e) stg[lane * 9 + e] = w[e];
+                        mirror_chunk(c, w);
                         __syncwarp();
                         const int nr = (int)min((int64_t)32, ti.m - row0);
                         if (col + lane < ti.n) {
@@ -615,7 +649,8 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 };
                 uint32_t vn[32];
                 if (nchunks > 0) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN, vn);
-#pragma unroll
+                // grouped tiles: a rolled chunk loop (fewer registers, no spills)
+#pragma unroll(GROUPED ? 1 : BN / 32)
                 for (int c = 0; c < BN / 32; ++c) {
                     if (c >= nchunks) break;
                     uint32_t v[32];

@@ -20,8 +20,11 @@ struct alignas(64) TcGroupProblem {          // 64 bytes
     int32_t rowA0, rowB0;                    // first row of A and of B^T in the bin's array
     int32_t ktiles;                          // k in 128-byte slices
     int16_t bin;                             // stride bin (tensor map index)
-    int16_t kind;                            // 0: raw e4m3 (kind::f8f6f4), 1: centred fp16 (kind::f16);
+    int8_t kind;                             // 0: raw e4m3 (kind::f8f6f4), 1: centred fp16 (kind::f16);
                                              // the kernel tells them apart by `scale`
+    int8_t sym;                              // 1: B = A^T, so C = A A^T is symmetric; the schedule
+                                             // holds the tiles tn >= tm only and the epilogue also
+                                             // writes each tile with tn > tm transposed at (tn, tm)
     uint32_t p, off;                         // off: 0 (raw products are non-negative)
     float scale;                             // 2^18 (raw e4m3), 1 (fp16)
     uint32_t m32;                            // ceil(2^32 / p)

@@ -437,12 +437,11 @@ def gfp_gemm_compressed_compc(p: int, m: int, k: int, n: int, d: int, Q: int, wo
     dt = WORD_DTYPE[word]
     if out is None:
         out = torch.empty((m, cdiv(n, d_out + 1)), dtype=dt, device=CA.device)
-    _mat(CA, dt, "CA")
-    _mat(CB, dt, "CB")
-    _mat(out, dt, "out")
-    _check(L.gfp_gemm_compressed_compc(p, m, k, n, d, Q, WORDS[word], ctypes.c_void_p(CA.data_ptr()), CA.stride(0),
-                                       ctypes.c_void_p(CB.data_ptr()), CB.stride(0), kb, d_out, Q_out,
-                                       ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream(out, stream)),
+    ap, lda = _mat(CA, dt, "CA")
+    bp, ldb = _mat(CB, dt, "CB")
+    cp, ldc = _mat(out, dt, "out")
+    _check(L.gfp_gemm_compressed_compc(p, m, k, n, d, Q, WORDS[word], ap, lda, bp, ldb, kb, d_out, Q_out,
+                                       cp, ldc, _stream(out, stream)),
            "gfp_gemm_compressed_compc")
     return out
 
@@ -503,8 +502,9 @@ def make_problems(items, flags: int = 0) -> ctypes.Array:
     for i, (p, A, B, C) in enumerate(items):
         m, k = A.shape
         n = B.shape[1]
-        arr[i] = Problem(p, m, k, n, A.data_ptr(), B.data_ptr(), C.data_ptr(),
-                         max(A.stride(0), 1), max(B.stride(0), 1), max(C.stride(0), 1), flags)
+        # leading dimensions as _mat reads them (a one-row view's stride(0) is arbitrary)
+        lds = [_mat(X, torch.uint8, name)[1] for X, name in ((A, "A"), (B, "B"), (C, "C"))]
+        arr[i] = Problem(p, m, k, n, A.data_ptr(), B.data_ptr(), C.data_ptr(), *lds, flags)
     return arr, len(items)
 
 

@@ -281,3 +281,35 @@ def test_b_is_a_transpose_flag_validation():
     arr, cnt = gfp.make_problems([(5, dev(A), dev(At), C)], flags=gfp.PROBLEM_B_IS_A_T)
     gfp.gfp_gemm_batched(arr, cnt, "tc_f8")
     assert (host(C) == oracle.gemm(5, A, At)).all()
+
+
+@pytest.mark.parametrize("algo", ["tc_f8", "auto"])
+def test_b_is_a_transpose_symmetric_tiles(algo):
+    """Flagged B = A^T with A not symmetric and k != m: C = A A^T is
+    symmetric, so the tensor-core tiles compute only the tiles on and above
+    the diagonal and store each one above it twice.  Ragged sizes of one to
+    five 128-row tiles, raw e4m3 (p < 16) and centred fp16 (p >= 16) operands
+    in one launch, C written into views with a wider row stride inside a
+    sentinel-filled buffer; every entry against the oracle, nothing outside
+    the views touched."""
+    g = np.random.Generator(np.random.PCG64(37))
+    items, host_ops, bufs = [], [], []
+    for p, m, k in ((3, 129, 40), (5, 300, 513), (7, 513, 200), (31, 257, 300), (251, 640, 64),
+                    (2, 128, 128), (5, 1, 7), (7, 255, 1)):
+        A = inputs.residues(g, p, m, k)
+        At = np.ascontiguousarray(A.T)
+        buf = torch.full((m + 2, m + 19), 254, dtype=torch.uint8, device="cuda")
+        C = buf[1:m + 1, 3:m + 3]
+        items.append((p, dev(A), dev(At), C))
+        host_ops.append((p, A, At))
+        bufs.append(buf)
+    arr, cnt = gfp.make_problems(items, flags=gfp.PROBLEM_B_IS_A_T)
+    gfp.gfp_gemm_batched(arr, cnt, algo)
+    torch.cuda.synchronize()
+    for (p, A, At), (_, _, _, C), buf in zip(host_ops, items, bufs):
+        ref = oracle.gemm(p, A, At)
+        assert (ref == ref.T).all()
+        assert (host(C) == ref).all(), (p, A.shape)
+        out = host(buf).copy()
+        out[1:A.shape[0] + 1, 3:A.shape[0] + 3] = 254
+        assert (out == 254).all(), (p, A.shape)
