@@ -313,3 +313,31 @@ def test_b_is_a_transpose_symmetric_tiles(algo):
         out = host(buf).copy()
         out[1:A.shape[0] + 1, 3:A.shape[0] + 3] = 254
         assert (out == 254).all(), (p, A.shape)
+
+
+@pytest.mark.parametrize("algo", ["tc_f8", "tc_f16", "dot32", "auto"])
+def test_batched_strided_unaligned_operands(algo):
+    """Operands given as views with a wider row stride at odd byte offsets
+    (every row of A and B starts at another alignment), so that the operand
+    staging joins misaligned 16-byte blocks and zero-fills row ends; raw e4m3,
+    fp16 and word tiles in one launch; every entry against the oracle."""
+    g = np.random.Generator(np.random.PCG64(41))
+    items, host_ops, keep = [], [], []
+    for p, m, k, n in ((3, 37, 1, 5), (5, 130, 17, 129), (7, 64, 300, 70), (31, 200, 129, 33),
+                       (251, 90, 513, 140), (2, 257, 64, 1), (13, 1, 700, 300), (17, 45, 31, 400)):
+        A = inputs.residues(g, p, m, k)
+        B = inputs.residues(g, p, k, n)
+        bufA = dev(inputs.residues(g, p, m + 3, k + 21))
+        bufB = dev(inputs.residues(g, p, k + 2, n + 13))
+        Av = bufA[2:m + 2, 5:k + 5]
+        Bv = bufB[1:k + 1, 7:n + 7]
+        Av.copy_(dev(A))
+        Bv.copy_(dev(B))
+        items.append((p, Av, Bv, torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A, B))
+        keep += [bufA, bufB]
+    arr, cnt = gfp.make_problems(items)
+    gfp.gfp_gemm_batched(arr, cnt, algo)
+    torch.cuda.synchronize()
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all(), (p, A.shape, B.shape)
