@@ -589,7 +589,7 @@ TRAFFIC = {"dot_u64": 17443889920 + 282185472}
 KERNEL_NAMES = {"plain": "simt_gemm_kernel<PlainP>", "dp4a": "simt_gemm_kernel<Dp4aT>",
                 "dot_u64": "simt_gemm_kernel<DotU64>", "mixed_u64": "simt_gemm_kernel<MixedU64>",
                 "tc_mma_s8": "mma_s8_kernel", "tc_f16": "tc_pair_kernel<PairCfg<256, fp16>>",
-                "tc_f8": "tc_pair_kernel<PairCfg<256, e4m3>>", "tc_e2m1": "tc_pair_kernel<PairCfg<192, e2m1>>"}
+                "tc_f8": "tc_pair_kernel<PairCfg<256, e4m3>>", "tc_e2m1": "tc_pair_kernel<PairCfg<224, e2m1>>"}
 
 
 def main():
