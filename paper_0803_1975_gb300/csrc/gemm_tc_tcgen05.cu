@@ -739,23 +739,44 @@ __device__ __forceinline__ void put16(void *dst, const int (&c)[16]) {
     }
 }
 
-// 16 consecutive residues (zero outside [0, limit)): one 16-byte load when the
-// run is inside the row and aligned, else byte loads.
-__device__ __forceinline__ void load16(const uint8_t *src, int64_t c0, int64_t limit, bool row_ok,
-                                       uint32_t (&r)[16]) {
-    if (row_ok && c0 + 16 <= limit && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(src);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+// 16 consecutive residues as four words (zero outside [c0, limit) or when
+// !row_ok): one 16-byte load when the run is inside the row and aligned.
+__device__ __forceinline__ uint4 load16w(const uint8_t *src, int64_t c0, int64_t limit, bool row_ok) {
+    if (row_ok && c0 + 16 <= limit && (reinterpret_cast<uintptr_t>(src) & 15) == 0)
+        return *reinterpret_cast<const uint4 *>(src);
+    uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int e = 0; e < 16; ++e) r[e] = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
-        return;
-    }
+    for (int e = 0; e < 16; ++e)
+        if (row_ok && c0 + e < limit) w[e >> 2] |= (uint32_t)src[e] << (8 * (e & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Operand conversions take two rows (the row kernels) or CONV_TU column
+// tiles (the transposes) per step of a grid-stride loop, their loads issued
+// before any of them is converted, so that more bytes are in flight per SM.
+constexpr int CONV_TU = 4;
+
+// Grid heights of the conversions: rows of mp taken two at a time, column
+// tiles of 64 of np taken CONV_TU at a time; at most 65535.
+unsigned conv_rows_grid_y(int64_t mp) {
+    const int64_t y = (mp + 1) / 2;
+    return (unsigned)(y < 1 ? 1 : y < 65535 ? y : 65535);
+}
+unsigned conv_tiles_grid_y(int64_t np) {
+    const int64_t y = (np / 64 + CONV_TU - 1) / CONV_TU;
+    return (unsigned)(y < 1 ? 1 : y < 65535 ? y : 65535);
+}
+
+// the 16 bytes of w as residues: c[e] = centre(byte e)
+__device__ __forceinline__ void centre16(const uint4 &v, uint32_t p, uint32_t h, int (&c)[16]) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = (row_ok && c0 + e < limit) ? src[e] : 0u;
+    for (int e = 0; e < 16; ++e) c[e] = centre_i((w[e >> 2] >> (8 * (e & 3))) & 0xffu, p, h);
 }
 
 // out[i][l] = centre(A[i][l]) for i < m, l < k; zero elsewhere in mp x kp.
-// One thread per 16 consecutive values of a row.
+// One thread per 16 consecutive values of a row, rows i and i + gridDim.y of
+// each step.
 template <bool FP8>
 __global__ void to_op_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m, int64_t k,
                                   uint8_t *__restrict__ out, int64_t kp, int64_t mp, uint32_t p,
@@ -763,18 +784,23 @@ __global__ void to_op_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, in
     constexpr int ES = FP8 ? 1 : 2;
     const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
     if (l >= kp) return;
-    for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
-        uint32_t r[16];
-        load16(A + i * lda + l, l, k, i < m, r);
+    for (int64_t i = blockIdx.y; i < mp; i += 2 * (int64_t)gridDim.y) {
+        const int64_t i2 = i + gridDim.y;
+        const uint4 a = load16w(A + i * lda + l, l, k, i < m);
+        const uint4 b = i2 < mp ? load16w(A + i2 * lda + l, l, k, i2 < m) : make_uint4(0u, 0u, 0u, 0u);
         int c[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) c[e] = centre_i(r[e], p, h);
+        centre16(a, p, h, c);
         put16<FP8>(out + (i * kp + l) * ES, c);
+        if (i2 < mp) {
+            centre16(b, p, h, c);
+            put16<FP8>(out + (i2 * kp + l) * ES, c);
+        }
     }
 }
 
 // out[j][l] = centre(B[l][j]) for l < k, j < n; zero elsewhere in np x kp.
-// 64 x 64 tiles through shared memory; 256 threads, 16 values each way.
+// 64 x 64 tiles through shared memory; 256 threads, 16 values each way;
+// CONV_TU column tiles per step, all of their loads first.
 // RAW: residues copied unchanged (for e4m3 operands of p < 16, the byte r is
 // the e4m3 code of r 2^-9, see launch_tc).
 template <bool FP8, bool RAW = false>
@@ -782,35 +808,54 @@ __global__ void to_op_transpose_kernel(const uint8_t *__restrict__ B, int64_t ld
                                        int64_t n, uint8_t *__restrict__ out, int64_t kp, int64_t np,
                                        uint32_t p, uint32_t h) {
     constexpr int ES = FP8 ? 1 : 2;
-    __shared__ int8_t tile[64][64 + 4];
+    __shared__ __align__(16) uint8_t tile[64][64 + 4];
     const int64_t l0 = (int64_t)blockIdx.x * 64;
     const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
-    // column tiles of 64 in a grid-stride loop (np / 64 may exceed the grid's y limit)
-    for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
-        const int64_t j0 = jt * 64;
-        {
-            const int64_t l = l0 + r;
-            uint32_t v[16];
-            load16(B + l * ldb + j0 + q, j0 + q, n, l < k, v);
+    const int64_t l = l0 + r;
+    // column tiles in a grid-stride loop (np / 64 may exceed the grid's y limit)
+    for (int64_t jt = blockIdx.y; jt < np / 64; jt += CONV_TU * (int64_t)gridDim.y) {
+        uint4 v[CONV_TU];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) tile[r][q + e] = (int8_t)(RAW ? (int)v[e] : centre_i(v[e], p, h));
+        for (int u = 0; u < CONV_TU; ++u) {
+            const int64_t j0 = (jt + u * (int64_t)gridDim.y) * 64;
+            v[u] = j0 < np ? load16w(B + l * ldb + j0 + q, j0 + q, n, l < k) : make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncthreads();
-        const int64_t j = j0 + r;
-        if (j < np) {
+#pragma unroll
+        for (int u = 0; u < CONV_TU; ++u) {
+            const int64_t j0 = (jt + u * (int64_t)gridDim.y) * 64;
+            if (j0 >= np) break;   // the same in every thread of the block
+            {
+                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&tile[r][q]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t x = w[e];
+                    if constexpr (!RAW) {
+                        // each byte r as the byte of centre(r) (two's complement)
+                        uint32_t y = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            y |= ((uint32_t)centre_i((x >> (8 * b)) & 0xffu, p, h) & 0xffu) << (8 * b);
+                        x = y;
+                    }
+                    dst[e] = x;
+                }
+            }
+            __syncthreads();
+            const int64_t j = j0 + r;   // np is a multiple of 64: j < np
             if constexpr (RAW) {
                 uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-                for (int e = 0; e < 16; ++e) w[e >> 2] |= (uint32_t)(uint8_t)tile[q + e][r] << (8 * (e & 3));
+                for (int e = 0; e < 16; ++e) w[e >> 2] |= (uint32_t)tile[q + e][r] << (8 * (e & 3));
                 *reinterpret_cast<uint4 *>(out + j * kp + l0 + q) = make_uint4(w[0], w[1], w[2], w[3]);
             } else {
                 int c[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) c[e] = tile[q + e][r];
+                for (int e = 0; e < 16; ++e) c[e] = (int8_t)tile[q + e][r];
                 put16<FP8>(out + (j * kp + l0 + q) * ES, c);
             }
+            __syncthreads();   // the tile is refilled by the next column tile
         }
-        __syncthreads();   // the tile is refilled by the next iteration
     }
 }
 
@@ -843,17 +888,6 @@ __device__ __forceinline__ uint32_t nib4(uint32_t w) {
 __device__ __forceinline__ uint32_t codes4(uint32_t w, uint32_t lo, uint32_t hi) {
     return __byte_perm(lo, hi, nib4(w));
 }
-// 16 consecutive residues as four words (zero outside [c0, limit) or when
-// !row_ok): one 16-byte load when the run is inside the row and aligned.
-__device__ __forceinline__ uint4 load16w(const uint8_t *src, int64_t c0, int64_t limit, bool row_ok) {
-    if (row_ok && c0 + 16 <= limit && (reinterpret_cast<uintptr_t>(src) & 15) == 0)
-        return *reinterpret_cast<const uint4 *>(src);
-    uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int e = 0; e < 16; ++e)
-        if (row_ok && c0 + e < limit) w[e >> 2] |= (uint32_t)src[e] << (8 * (e & 3));
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
 // eight residues (two words) as eight packed codes, value e in nibble e
 __device__ __forceinline__ uint32_t pack8(uint32_t x, uint32_t y, uint32_t lo, uint32_t hi) {
     return nib4(codes4(x, lo, hi)) | (nib4(codes4(y, lo, hi)) << 16);
@@ -878,34 +912,39 @@ __global__ void to_e2m1_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, 
 
 // out[j][l] = code(centre(B[l][j])) for l < k, j < n; zero elsewhere in np x kp.
 // 64 x 64 tiles through shared memory as in to_op_transpose_kernel (codes
-// written four at a time); each thread writes 16 values (8 bytes) of one row
-// of B^T.
+// written four at a time, CONV_TU column tiles per step); each thread writes
+// 16 values (8 bytes) of one row of B^T.
 __global__ void to_e2m1_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k, int64_t n,
                                          uint8_t *__restrict__ out, int64_t kp, int64_t np, uint32_t lo,
                                          uint32_t hi) {
     __shared__ __align__(16) uint8_t tile[64][64 + 4];
     const int64_t l0 = (int64_t)blockIdx.x * 64;
     const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
-    for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
-        const int64_t j0 = jt * 64;
-        {
-            const int64_t l = l0 + r;
-            const uint4 v = load16w(B + l * ldb + j0 + q, j0 + q, n, l < k);
-            uint32_t *dst = reinterpret_cast<uint32_t *>(&tile[r][q]);
-            dst[0] = codes4(v.x, lo, hi);
-            dst[1] = codes4(v.y, lo, hi);
-            dst[2] = codes4(v.z, lo, hi);
-            dst[3] = codes4(v.w, lo, hi);
+    const int64_t l = l0 + r;
+    for (int64_t jt = blockIdx.y; jt < np / 64; jt += CONV_TU * (int64_t)gridDim.y) {
+        uint4 v[CONV_TU];
+#pragma unroll
+        for (int u = 0; u < CONV_TU; ++u) {
+            const int64_t j0 = (jt + u * (int64_t)gridDim.y) * 64;
+            v[u] = j0 < np ? load16w(B + l * ldb + j0 + q, j0 + q, n, l < k) : make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncthreads();
-        const int64_t j = j0 + r;
-        if (j < np) {
+#pragma unroll
+        for (int u = 0; u < CONV_TU; ++u) {
+            const int64_t j0 = (jt + u * (int64_t)gridDim.y) * 64;
+            if (j0 >= np) break;   // the same in every thread of the block
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&tile[r][q]);
+            dst[0] = codes4(v[u].x, lo, hi);
+            dst[1] = codes4(v[u].y, lo, hi);
+            dst[2] = codes4(v[u].z, lo, hi);
+            dst[3] = codes4(v[u].w, lo, hi);
+            __syncthreads();
+            const int64_t j = j0 + r;   // np is a multiple of 64: j < np
             uint32_t w[2] = {0, 0};
 #pragma unroll
             for (int e = 0; e < 16; ++e) w[e >> 3] |= (uint32_t)tile[q + e][r] << (4 * (e & 7));
             *reinterpret_cast<uint2 *>(out + j * (kp / 2) + (l0 + q) / 2) = make_uint2(w[0], w[1]);
+            __syncthreads();   // the tile is refilled by the next column tile
         }
-        __syncthreads();   // the tile is refilled by the next iteration
     }
 }
 
@@ -1469,8 +1508,8 @@ gfp_status launch_tc(uint32_t p, int64_t m, int64_t k, int64_t n, const uint8_t 
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e);
     {
-        dim3 grid((unsigned)((kp / 16 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
-        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
+        dim3 grid((unsigned)((kp / 16 + 255) / 256), conv_rows_grid_y(mp));
+        dim3 gt((unsigned)(kp / 64), conv_tiles_grid_y(np));
         if (raw) {
             to_op_transpose_kernel<true, true><<<gt, 256, 0, s>>>(B, ldb, k, n, Bop, kp, np, p, h);
         } else if (fp8) {
@@ -1541,7 +1580,7 @@ gfp_status launch_transpose_bytes(const uint8_t *B, int64_t ldb, int64_t k, int6
                                   int64_t np, cudaStream_t s) {
     if (kp % 64 || np % 64 || kp / 64 > 2147483647) return GFP_EINVAL;
     if (kp == 0 || np == 0) return GFP_OK;
-    to_op_transpose_kernel<true, true><<<dim3((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535)),
+    to_op_transpose_kernel<true, true><<<dim3((unsigned)(kp / 64), conv_tiles_grid_y(np)),
                                          256, 0, s>>>(
         B, ldb, k, n, out, kp, np, 0u, 0u);
     return check_launch();
@@ -1938,7 +1977,7 @@ gfp_status launch_tc_e2m1(uint32_t p, int64_t m, int64_t k, int64_t n, const uin
     if (e != cudaSuccess) return cuda_fail(e);
     {
         dim3 grid((unsigned)((kp / 32 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
-        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
+        dim3 gt((unsigned)(kp / 64), conv_tiles_grid_y(np));
         uint32_t lo, hi;
         e2m1_table(p, &lo, &hi);
         to_e2m1_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, Aop, kp, mp, lo, hi);
