@@ -555,6 +555,10 @@ GFP_API gfp_status gfp_batched_workspace_size(int64_t count, const gfp_problem *
  *                aligned).  It receives the schedule: problem table, tiles,
  *                and each CTA's range of tiles, balanced on the host
  *                (longest tile first onto the least loaded CTA).
+ * Bytes 192 .. 195 of the workspace hold, once a launch's kernels complete,
+ * the status of its bounded internal waits: 0, or non-zero if one gave up
+ * (1-4 the tcgen05 tiles' roles, 6 an operand copy of the conversion; the
+ * results are then invalid).
  * gfp_gemm_batched = gfp_batched_prepare + gfp_batched_launch.
  * gfp_batched_prepare writes the schedule with one host-to-device copy and
  * synchronizes `stream` (run it outside stream capture).  gfp_batched_launch

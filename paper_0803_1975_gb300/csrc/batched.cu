@@ -87,11 +87,12 @@ static_assert(sizeof(ConvJob) == 48, "layout");
 
 struct ConvItem {            // CONV_F16 / CONV_RAW: nrows rows from row0; CONV_RAW_T: 128 x 128 of dst
     int32_t job, row0, col0, nrows;
+    int32_t bulk;            // rows staged by one bulk copy (see convert_kernel)
 };
 
 struct ConvTask {            // 64 bytes: an item with its job, read in one piece by the kernel
     ConvJob J;
-    int32_t row0, col0, nrows, pad;
+    int32_t row0, col0, nrows, bulk;
 };
 static_assert(sizeof(ConvTask) == 64, "layout");
 
@@ -141,6 +142,36 @@ __device__ __forceinline__ void cp_async16_zfill(uint32_t saddr, const void *g, 
                  : "memory");
 }
 
+// mbarrier and bulk-copy helpers of the conversion's bulk row tasks
+__device__ __forceinline__ uint64_t conv_globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool conv_mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase `parity` of the barrier at a (every thread of
+// the CTA); false when it did not complete within limit_ns.
+__device__ __forceinline__ bool conv_mbar_wait(uint32_t a, uint32_t parity, uint64_t limit_ns) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (conv_mbar_try(a, parity)) return true;
+        if ((it & 63) == 63) {
+            const uint64_t now = conv_globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
+    }
+}
+
 // Bytes 16 ch .. 16 ch + 15 of a staged row run whose first byte is buf[d]
 // (the run staged as aligned 16-byte blocks from floor16 of its start), zero
 // from the nvalid-th byte on.
@@ -162,7 +193,12 @@ __device__ __forceinline__ uint4 staged16(const uint8_t *buf, uint32_t d, int ch
 // CONV_F16  : c = r - p [r > h] as fp16 (HMMA tiles).
 // CONV_RAW  : residue bytes copied (e4m3 codes of r 2^-9 for the tcgen05
 //             tiles).
-//             Both: warp w takes rows row0 + w + 8 g (g < nrows / 8) of the
+//             Bulk tasks (rows that fit a staging buffer): one bulk copy
+//             (cp.async.bulk, completion counted on an mbarrier) stages the
+//             aligned 16-byte blocks holding a run of whole rows, the next
+//             task's copy in flight meanwhile; threads then take the rows'
+//             16-element chunks, realigned by funnel shifts.
+//             Other row tasks: warp w takes rows row0 + w + 8 g (g < nrows / 8) of the
 //             item and stages runs of up to 512 source bytes of all of them
 //             at once (aligned 16-byte blocks by cp.async, zero-filled where
 //             a block holds no byte of the row -- a block that does cannot
@@ -179,24 +215,129 @@ constexpr int CONV_CTAS_PER_SM = 4;
 constexpr int CONV_WBUF = 2048;            // staging bytes per warp (row runs)
 constexpr int TT_BLK = 9;                  // 16-byte blocks per staged row: 128 bytes from any offset
 constexpr int TT_PITCH = TT_BLK * 16;      // bytes per staged row
+// Bulk row tasks: the source bytes of a task, from the 16-byte block holding
+// its first byte to the one holding its last, fit one staging buffer
+// (128 TT_PITCH bytes) with room for the 5-word reads past a row's end.
+constexpr int CONV_BULK_BYTES = 128 * TT_PITCH - 64;
+constexpr int ST_TIMEOUT_CONVERT = 6;      // status: a bulk copy's wait ran out
+constexpr unsigned long long CONV_WAIT_NS = 4000000000ull;
 
-__global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(const uint8_t *__restrict__ ws) {
-    // two staging buffers so that one barrier per transposed block suffices
-    __shared__ __align__(16) uint8_t stage[2][128 * TT_PITCH];
+// Source rows of a bulk task (the destination's padding rows have none) and
+// its copy: the aligned 16-byte blocks from the one holding the first byte to
+// the one holding the last, each holding a byte of the source rows, so none
+// lies outside the caller's allocation.
+__device__ __forceinline__ int64_t bulk_rows(const ConvTask &t) {
+    const int64_t n = (int64_t)t.J.rows - t.row0;
+    return t.J.cols <= 0 ? 0 : (n < t.nrows ? n : (int64_t)t.nrows);
+}
+__device__ __forceinline__ void bulk_issue(const ConvTask &t, uint8_t *buf, uint32_t bar) {
+    const int64_t nr = bulk_rows(t);
+    if (nr <= 0) return;
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(t.J.src) + (uintptr_t)((int64_t)t.row0 * t.J.ld);
+    const uintptr_t s1 = s0 + (uintptr_t)((nr - 1) * t.J.ld + t.J.cols);
+    const uintptr_t a0 = s0 & ~(uintptr_t)15, a1 = (s1 + 15) & ~(uintptr_t)15;
+    const uint32_t bytes = (uint32_t)(a1 - a0);
+    // the buffer's earlier contents were read by generic loads (ordered by the
+    // CTA barrier before this call); the copy writes it through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            s2u(buf)),
+        "l"(a0), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(256, CONV_CTAS_PER_SM) convert_kernel(uint8_t *__restrict__ ws) {
+    // two staging buffers so that one barrier per transposed block suffices;
+    // the bulk row tasks use them as the two buffers of their copies
+    __shared__ __align__(128) uint8_t stage[2][128 * TT_PITCH];
     __shared__ __align__(16) uint8_t dstage[2][128];      // misalignment of each staged row
     __shared__ __align__(16) uint8_t wbuf[8][CONV_WBUF];  // per warp: staged row runs
+    __shared__ __align__(8) uint64_t bulk_bar[2];
     int tb = 0;
     const Header *H = reinterpret_cast<const Header *>(ws);
     const ConvTask *tasks = reinterpret_cast<const ConvTask *>(ws + H->off_citems);
+    int *status = reinterpret_cast<int *>(ws + OFF_TCSTATUS);
     const int ntasks = H->ncitems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t bars[2] = {s2u(&bulk_bar[0]), s2u(&bulk_bar[1])};
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars[0]) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars[1]) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     // the next task is read while the current one is converted
     ConvTask nx;
     if ((int)blockIdx.x < ntasks) nx = tasks[blockIdx.x];
+    // bulk tasks lead the task list, so a CTA's bulk tasks come first; the
+    // copy of the next one is in flight while the current one is written
+    int nbulk = 0;
+    uint32_t bulk_parity = 0;                              // bit b: parity of buffer b's next phase
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntasks && nx.bulk) bulk_issue(nx, stage[0], bars[0]);
     for (int it = blockIdx.x; it < ntasks; it += gridDim.x) {
         const ConvTask ci = nx;
         if (it + (int)gridDim.x < ntasks) nx = tasks[it + gridDim.x];
         const ConvJob &J = ci.J;
+        if (ci.bulk) {
+            const int b = nbulk & 1;
+            ++nbulk;
+            const bool next_copy = it + (int)gridDim.x < ntasks && nx.bulk && bulk_rows(nx) > 0;
+            if (threadIdx.x == 0 && next_copy) bulk_issue(nx, stage[b ^ 1], bars[b ^ 1]);
+            if (bulk_rows(ci) > 0) {
+                const uint32_t par = (bulk_parity >> b) & 1u;
+                const bool ok = conv_mbar_wait(bars[b], par, CONV_WAIT_NS);
+                bulk_parity ^= 1u << b;
+                if (__syncthreads_or(!ok)) {
+                    // a copy that never completed: record it, let the copies in
+                    // flight land (bounded waits), and leave the rest undone
+                    if (threadIdx.x == 0) {
+                        atomicCAS(status, 0, ST_TIMEOUT_CONVERT);
+                        conv_mbar_wait(bars[b], par, CONV_WAIT_NS);
+                        if (next_copy) conv_mbar_wait(bars[b ^ 1], (bulk_parity >> (b ^ 1)) & 1u, CONV_WAIT_NS);
+                    }
+                    __syncthreads();
+                    return;
+                }
+            }
+            // chunks of 16 destination elements; row g of the task starts at
+            // byte d0 + g ld of the staged blocks
+            const uint8_t *buf = stage[b];
+            const uint32_t d0 =
+                (uint32_t)((reinterpret_cast<uintptr_t>(J.src) + (uintptr_t)((int64_t)ci.row0 * J.ld)) & 15);
+            const int rend = min(J.drows, ci.row0 + ci.nrows);
+            const int cpr = J.dcols / 16;
+            const int nq = (rend - ci.row0) * cpr;
+            const uint32_t mcpr = cpr == 1 ? 0u : 0xFFFFFFFFu / (uint32_t)cpr + 1u;
+            const bool f16 = J.mode == CONV_F16;
+            const float hf = J.p == 2 ? 1.f : (float)((J.p - 1) / 2);
+            const __half2 c1536 = __floats2half2_rn(1536.f, 1536.f);
+            const __half2 hh = __floats2half2_rn(hf, hf);
+            const __half2 mp = __floats2half2_rn(-(float)J.p, -(float)J.p);
+            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                const int g = cpr == 1 ? q : (int)__umulhi((uint32_t)q, mcpr), ch = q - g * cpr;
+                const int r = ci.row0 + g, c = 16 * ch;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (r < J.rows && c < J.cols) v = staged16(buf, d0 + (uint32_t)(g * J.ld), ch, (int64_t)J.cols - c);
+                if (!f16) {
+                    *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(J.dst) + (int64_t)r * J.dld + c) = v;
+                } else {
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        o[2 * e] = centre2(w[e], 0x4140u, c1536, hh, mp);
+                        o[2 * e + 1] = centre2(w[e], 0x4342u, c1536, hh, mp);
+                    }
+                    uint4 *dp = reinterpret_cast<uint4 *>(static_cast<__half *>(J.dst) + (int64_t)r * J.dld + c);
+                    dp[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                    dp[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            __syncthreads();   // buffer b is read: the copy after next may fill it
+            continue;
+        }
         if (J.mode == CONV_RAW_T || J.mode == CONV_F16_T) {
             // dst[j][l] = src[l][j]: dst rows j0 .. j0+127, dst columns l0 .. l0+127
             const int j0 = ci.row0, l0 = ci.col0;
@@ -697,6 +838,21 @@ int conv_rows_per_item(int32_t dcols) {
     return 8 * std::max(1, std::min(16, CONV_WBUF / (16 * nb)));
 }
 
+// Items of a row-wise conversion job: bulk items when a row's blocks fit a
+// staging buffer (as many whole rows as fit: (rows - 1) ld + cols + 31 <=
+// CONV_BULK_BYTES), else the per-warp staged runs.
+void push_row_items(Plan &plan, const ConvJob &J, int jid) {
+    const int64_t span = (int64_t)J.cols + 31;
+    if (J.cols > 0 && J.ld > 0 && span <= CONV_BULK_BYTES) {
+        const int64_t fit = (CONV_BULK_BYTES - span) / J.ld + 1;
+        const int32_t nr = (int32_t)std::min<int64_t>(fit, std::max<int32_t>(J.drows, 1));
+        for (int32_t r = 0; r < J.drows; r += nr) plan.citems.push_back(ConvItem{jid, r, 0, nr, 1});
+        return;
+    }
+    const int nr = conv_rows_per_item(J.dcols);
+    for (int32_t r = 0; r < J.drows; r += nr) plan.citems.push_back(ConvItem{jid, r, 0, nr, 0});
+}
+
 // fp32-exact k-block of the raw e4m3 products (residues r < 16 uncentred)
 int64_t tc8_kmax(uint32_t p) {
     const int64_t pr = (int64_t)(p - 1) * (p - 1);
@@ -798,8 +954,7 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
         plan.ops_bytes += round_to((int64_t)J.drows * J.dld * 2, 256);
         const int jid = (int)plan.jobs.size();
         plan.jobs.push_back(J);
-        const int nr = conv_rows_per_item(J.dcols);
-        for (int32_t r = 0; r < J.drows; r += nr) plan.citems.push_back(ConvItem{jid, r, 0, nr});
+        push_row_items(plan, J, jid);
         seen[key] = off;
         return off;
     };
@@ -839,8 +994,7 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
             for (int32_t r = 0; r < J.drows; r += 128)
                 for (int32_t c = 0; c < J.dcols; c += 128) plan.citems.push_back(ConvItem{jid, r, c, 128});
         } else {
-            const int nr = conv_rows_per_item(J.dcols);
-        for (int32_t r = 0; r < J.drows; r += nr) plan.citems.push_back(ConvItem{jid, r, 0, nr});
+            push_row_items(plan, J, jid);
         }
         tc_seen[key] = row0;
         return row0;
@@ -999,7 +1153,7 @@ size_t bound_bytes(int64_t count, const gfp_problem *probs) {
         tcitems += ((m + 127) / 128) * ((n + 127) / 128);
         const int64_t mm = round_to(m, 128), kk = round_to(k, 128), nn = round_to(n, 128);
         ops += round_to((mm * kk + kk * nn) * 4, 256) + 2 * 256;   // fp16 rows in a bin up to twice as wide
-        citems += (mm + kk) / 16 + (kk / 64) * (nn / 64);
+        citems += mm + kk + (kk / 64) * (nn / 64);   // row tasks: at most one per row
     }
     ops += TC_GROUP_BINS * 256;
     const int grid = std::max(1, num_sms() * CTAS_PER_SM);
@@ -1099,6 +1253,9 @@ gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
     put(L.items, plan.items.data(), plan.items.size() * sizeof(Item));
     put(L.ranges, plan.ranges.data(), plan.ranges.size() * sizeof(int32_t));
     put(L.jobs, plan.jobs.data(), plan.jobs.size() * sizeof(ConvJob));
+    // the bulk row tasks first: a CTA's grid-stride walk then meets its bulk
+    // tasks before any other, and keeps one copy in flight across them
+    std::stable_partition(plan.citems.begin(), plan.citems.end(), [](const ConvItem &c) { return c.bulk != 0; });
     std::vector<ConvTask> tasks(plan.citems.size());
     for (size_t i = 0; i < tasks.size(); ++i) {
         const ConvItem &c = plan.citems[i];
@@ -1106,7 +1263,7 @@ gfp_status upload(Plan &plan, void *ws, size_t ws_bytes, cudaStream_t s) {
         tasks[i].row0 = c.row0;
         tasks[i].col0 = c.col0;
         tasks[i].nrows = c.nrows;
-        tasks[i].pad = 0;
+        tasks[i].bulk = c.bulk;
     }
     put(L.citems, tasks.data(), tasks.size() * sizeof(ConvTask));
     put(L.tcprobs, tcp.data(), tcp.size() * sizeof(TcGroupProblem));
@@ -1134,8 +1291,12 @@ gfp_status launch_plan(void *ws, cudaStream_t s) {
         }
     }
     uint8_t *base = static_cast<uint8_t *>(ws);
-    // operand conversion (a grid-stride loop over the jobs' items; it reads
-    // their count from the workspace), then the grouped products
+    // the status word of the launch's bounded waits (conversion copies,
+    // tcgen05 tiles), then the operand conversion (a grid-stride loop over the
+    // jobs' items; it reads their count from the workspace), then the grouped
+    // products
+    cudaError_t e0 = cudaMemsetAsync(base + OFF_TCSTATUS, 0, sizeof(int), s);
+    if (e0 != cudaSuccess) return cuda_fail(e0);
     convert_kernel<<<std::max(1, num_sms() * CONV_CTAS_PER_SM), 256, 0, s>>>(base);
     gfp_status st = check_launch();
     if (st != GFP_OK) return st;
@@ -1148,8 +1309,6 @@ gfp_status launch_plan(void *ws, cudaStream_t s) {
         if (st != GFP_OK) return st;
     }
     if (tc) {
-        cudaError_t e = cudaMemsetAsync(base + OFF_TCSTATUS, 0, sizeof(int), s);
-        if (e != cudaSuccess) return cuda_fail(e);
         st = launch_tc_grouped(base + OFF_TCHDR, std::max(1, num_sms() * tc_grouped_ctas_per_sm()),
                                reinterpret_cast<int *>(base + OFF_TCSTATUS), s);
     }
