@@ -898,10 +898,14 @@ gfp_status validate_problem(const gfp_problem &q) {
 // Longest processing time first onto the least loaded of `grid` CTAs; returns
 // the items reordered by CTA and the per-CTA ranges.
 template <class T>
-void lpt(std::vector<T> &items, const std::vector<double> &cost, int grid, std::vector<int32_t> &ranges) {
+void lpt(std::vector<T> &items, const std::vector<double> &cost, int grid, std::vector<int32_t> &ranges,
+         const std::vector<double> *key = nullptr) {
+    // items in decreasing order of `key` (default: their cost), ties in their
+    // given order, each onto the least loaded CTA by cost
+    const std::vector<double> &k = key ? *key : cost;
     std::vector<int> order(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return k[a] > k[b]; });
     std::vector<std::vector<int>> per(grid);
     std::vector<std::pair<double, int>> heap;
     for (int g = 0; g < grid; ++g) heap.push_back({0.0, g});
@@ -932,7 +936,7 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
     gfp_status first_bad = GFP_OK;
     plan = Plan();
     std::map<std::tuple<uintptr_t, int32_t, int32_t, int32_t, uint32_t, int, int>, int64_t> seen;
-    std::vector<double> cost, tc_cost;
+    std::vector<double> cost, tc_cost, tc_key;
     // one converted copy per distinct (matrix, ld, shape, p, padding, mode)
     auto job_for = [&](const uint8_t *src, int32_t rows, int32_t cols, int32_t ld, uint32_t p, int rpad,
                        int cpad, int mode) -> int64_t {
@@ -1058,6 +1062,9 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
                 for (int b = T.sym ? a : 0; b < tnn; ++b) {
                     plan.tc_items.push_back(TcGroupItem{ti, (uint16_t)a, (uint16_t)b});
                     tc_cost.push_back((double)T.ktiles + (T.sym && b > a ? 4.0 : 2.0));
+                    // a problem's tiles keep one key, so they are placed (and run)
+                    // together while its operands are in L2
+                    tc_key.push_back((double)T.ktiles);
                 }
             continue;
         }
@@ -1101,7 +1108,7 @@ gfp_status make_plan(int64_t count, const gfp_problem *probs, gfp_algo algo, gfp
     plan.grid = std::max(1, num_sms() * CTAS_PER_SM);
     lpt(plan.items, cost, plan.grid, plan.ranges);
     plan.tc_grid = std::max(1, num_sms() * tc_grouped_ctas_per_sm());
-    lpt(plan.tc_items, tc_cost, plan.tc_grid, plan.tc_ranges);
+    lpt(plan.tc_items, tc_cost, plan.tc_grid, plan.tc_ranges, &tc_key);
     // the bin arrays follow the fp16 copies in the operand area
     for (int b = 0; b < TC_GROUP_BINS; ++b) {
         plan.bin_off[b] = plan.ops_bytes;
