@@ -658,33 +658,31 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = vn[i];
                     if (c + 1 < nchunks) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN + (c + 1) * 32, vn);
+                    // raw sums x < 2^23 held as v = x 2^-18: v + 32 lies in [32, 64),
+                    // where the mantissa counts units of 2^-18, so it is x exactly
+                    // (0x42000000 encodes 32); the quotient estimate is exact for
+                    // x < 2^32 / p.  The residue so far (k-blocked) joins the sum
+                    // before its one reduction: it is below p, and the bounds of both
+                    // reductions (that one, a < 2^25 in mod_acc) still hold.
                     uint32_t rr32[32];
-                    if (ti.red) {
-                        // raw sums x < 2^23 held as v = x 2^-18: v + 32 lies in [32, 64),
-                        // where the mantissa counts units of 2^-18, so it is x exactly
-                        // (0x42000000 encodes 32); the quotient estimate is exact for x < 2^32 / p
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u;
+                    for (int i = 0; i < 32; ++i) {
+                        uint32_t prev = 0;
+                        if constexpr (BLOCKED) prev = __byte_perm(run[c * 8 + i / 4], 0u, 0x4440u + (i & 3));
+                        if (ti.red) {
+                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u + prev;
                             rr32[i] = x - __umulhi(x, ti.m32) * ti.p;
+                        } else {
+                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * ti.scale) + (int)prev, ti.off,
+                                              ti.m32, ti.p);
                         }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * ti.scale), ti.off, ti.m32, ti.p);
                     }
                     uint32_t w[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         uint32_t r[4];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            r[b] = rr32[e * 4 + b];
-                            if constexpr (BLOCKED) {
-                                r[b] += (run[c * 8 + e] >> (8 * b)) & 0xffu;
-                                r[b] = r[b] >= ti.p ? r[b] - ti.p : r[b];
-                            }
-                        }
+                        for (int b = 0; b < 4; ++b) r[b] = rr32[e * 4 + b];
                         const uint32_t packed =
                             __byte_perm(__byte_perm(r[0], r[1], 0x0040), __byte_perm(r[2], r[3], 0x0040), 0x5410);
                         w[e] = packed;
@@ -1368,30 +1366,29 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = vn[i];
                     if (c + 1 < nchunks) tmem_ld32_async(tmem + lane_addr + buf * (uint32_t)BN + (c + 1) * 32, vn);
+                    // the residue so far (k-blocked) joins the sum before its one
+                    // reduction: it is below p, and the bounds of both reductions
+                    // (a < 2^25 with the offset, x < 2^32 / p) still hold; only the
+                    // raw e4m3 operands carry a scale (2^18), fp16 and e2m1 have 1
                     uint32_t rr32[32];
-                    if (g.red) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u;
+                    for (int i = 0; i < 32; ++i) {
+                        uint32_t prev = 0;
+                        if constexpr (BLOCKED) prev = __byte_perm(run[c * 8 + i / 4], 0u, 0x4440u + (i & 3));
+                        if (g.red) {
+                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u + prev;
                             rr32[i] = x - __umulhi(x, g.m32) * g.p;
+                        } else {
+                            const float f = CFG::KIND != 1 ? __uint_as_float(v[i]) : __uint_as_float(v[i]) * g.scale;
+                            rr32[i] = mod_acc(__float2int_rn(f) + (int)prev, g.off, g.m32, g.p);
                         }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * g.scale), g.off, g.m32, g.p);
                     }
                     uint32_t w[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         uint32_t r[4];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            r[b] = rr32[e * 4 + b];
-                            if constexpr (BLOCKED) {
-                                r[b] += (run[c * 8 + e] >> (8 * b)) & 0xffu;
-                                r[b] = r[b] >= g.p ? r[b] - g.p : r[b];
-                            }
-                        }
+                        for (int b = 0; b < 4; ++b) r[b] = rr32[e * 4 + b];
                         const uint32_t packed =
                             __byte_perm(__byte_perm(r[0], r[1], 0x0040), __byte_perm(r[2], r[3], 0x0040), 0x5410);
                         w[e] = packed;
