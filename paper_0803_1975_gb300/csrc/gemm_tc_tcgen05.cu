@@ -665,17 +665,21 @@ tc_f16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     // before its one reduction: it is below p, and the bounds of both
                     // reductions (that one, a < 2^25 in mod_acc) still hold.
                     uint32_t rr32[32];
+                    auto prev_of = [&](int i) -> uint32_t {
+                        if constexpr (BLOCKED) return __byte_perm(run[c * 8 + i / 4], 0u, 0x4440u + (i & 3));
+                        else return 0u;
+                    };
+                    if (ti.red) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        uint32_t prev = 0;
-                        if constexpr (BLOCKED) prev = __byte_perm(run[c * 8 + i / 4], 0u, 0x4440u + (i & 3));
-                        if (ti.red) {
-                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u + prev;
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u + prev_of(i);
                             rr32[i] = x - __umulhi(x, ti.m32) * ti.p;
-                        } else {
-                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * ti.scale) + (int)prev, ti.off,
-                                              ti.m32, ti.p);
                         }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            rr32[i] = mod_acc(__float2int_rn(__uint_as_float(v[i]) * ti.scale) + (int)prev_of(i), ti.off,
+                                              ti.m32, ti.p);
                     }
                     uint32_t w[8];
 #pragma unroll
@@ -1371,16 +1375,21 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     // (a < 2^25 with the offset, x < 2^32 / p) still hold; only the
                     // raw e4m3 operands carry a scale (2^18), fp16 and e2m1 have 1
                     uint32_t rr32[32];
+                    auto prev_of = [&](int i) -> uint32_t {
+                        if constexpr (BLOCKED) return __byte_perm(run[c * 8 + i / 4], 0u, 0x4440u + (i & 3));
+                        else return 0u;
+                    };
+                    if (g.red) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        uint32_t prev = 0;
-                        if constexpr (BLOCKED) prev = __byte_perm(run[c * 8 + i / 4], 0u, 0x4440u + (i & 3));
-                        if (g.red) {
-                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u + prev;
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t x = __float_as_uint(__uint_as_float(v[i]) + 32.0f) - 0x42000000u + prev_of(i);
                             rr32[i] = x - __umulhi(x, g.m32) * g.p;
-                        } else {
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
                             const float f = CFG::KIND != 1 ? __uint_as_float(v[i]) : __uint_as_float(v[i]) * g.scale;
-                            rr32[i] = mod_acc(__float2int_rn(f) + (int)prev, g.off, g.m32, g.p);
+                            rr32[i] = mod_acc(__float2int_rn(f) + (int)prev_of(i), g.off, g.m32, g.p);
                         }
                     }
                     uint32_t w[8];
