@@ -341,3 +341,32 @@ def test_batched_strided_unaligned_operands(algo):
     torch.cuda.synchronize()
     for (p, A, B), (_, _, _, C) in zip(host_ops, items):
         assert (host(C) == oracle.gemm(p, A, B)).all(), (p, A.shape, B.shape)
+
+
+@pytest.mark.parametrize("algo", ["tc_f8", "tc_f16"])
+def test_batched_row_staging_boundary(algo):
+    """Rows of A around the largest that one bulk copy stages (k + 31 source
+    bytes against the 18,368-byte limit, from any byte offset): k = 18,337
+    fits, 18,338 goes through the per-warp row runs; both in one launch, as
+    views at odd offsets, and against the oracle.  tc_f8 stages raw e4m3 rows
+    (p < 16) and centred fp16 rows (p = 31); tc_f16 the padded fp16 copies of
+    the mma.sync tiles."""
+    g = np.random.Generator(np.random.PCG64(43))
+    items, host_ops, keep = [], [], []
+    for p, m, k, n in ((3, 5, 18337, 7), (3, 6, 18338, 9), (31, 3, 18337, 5), (5, 2, 18336, 3)):
+        A = inputs.residues(g, p, m, k)
+        B = inputs.residues(g, p, k, n)
+        bufA = dev(inputs.residues(g, p, m + 1, k + 7))
+        Av = bufA[1:m + 1, 3:k + 3]
+        Av.copy_(dev(A))
+        items.append((p, Av, dev(B), torch.full((m, n), 255, dtype=torch.uint8, device="cuda")))
+        host_ops.append((p, A, B))
+        keep.append(bufA)
+    arr, cnt = gfp.make_problems(items)
+    ws = torch.full((gfp.gfp_batched_workspace_size(arr, cnt),), 255, dtype=torch.uint8, device="cuda")
+    gfp.gfp_batched_prepare(arr, cnt, algo, ws)
+    gfp.gfp_batched_launch(ws)
+    torch.cuda.synchronize()
+    assert int(ws[192:196].cpu().numpy().view(np.int32)[0]) == 0
+    for (p, A, B), (_, _, _, C) in zip(host_ops, items):
+        assert (host(C) == oracle.gemm(p, A, B)).all(), (p, A.shape, B.shape)
