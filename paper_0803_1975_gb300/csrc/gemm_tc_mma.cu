@@ -34,50 +34,79 @@ __device__ __forceinline__ uint32_t fastmod(uint32_t a, uint64_t M, uint32_t p) 
 }
 
 // ---- preprocess -------------------------------------------------------------
-__device__ __forceinline__ int8_t centre(uint8_t r, uint32_t p, uint32_t h) {
-    return (int8_t)((int)r - ((uint32_t)r > h ? (int)p : 0));
+// Four residue bytes centred at once: c = r - p where r > h, as int8 bytes
+// (two's complement).  The byte-wise compare gives 0xFF where r > h; the
+// byte-wise subtraction takes p off there (r - p >= -h: no borrow crosses a
+// byte as the result wraps into the byte's own int8 value).
+__device__ __forceinline__ uint32_t centre4(uint32_t w, uint32_t h4, uint32_t p4) {
+    return __vsub4(w, __vcmpgtu4(w, h4) & p4);
 }
 
-// Ac[i][l] = centre(A[i][l]) for i < m, l < k; zero elsewhere in mp x kp.
+// 16 consecutive residues as four words, zero outside [c0, limit) or when
+// !row_ok: one 16-byte load when the run is inside the row and aligned.
+__device__ __forceinline__ uint4 load16_bytes(const uint8_t *src, int64_t c0, int64_t limit, bool row_ok) {
+    if (row_ok && c0 + 16 <= limit && (reinterpret_cast<uintptr_t>(src) & 15) == 0)
+        return *reinterpret_cast<const uint4 *>(src);
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        if (row_ok && c0 + e < limit) w[e >> 2] |= (uint32_t)src[e] << (8 * (e & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Ac[i][l] = centre(A[i][l]) for i < m, l < k; zero elsewhere in mp x kp
+// (zero residues stay zero).  One thread per 16 consecutive values of a row.
 __global__ void centre_rows_kernel(const uint8_t *__restrict__ A, int64_t lda, int64_t m,
                                    int64_t k, int8_t *__restrict__ Ac, int64_t kp, int64_t mp,
                                    uint32_t p, uint32_t h) {
-    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
     if (l >= kp) return;
+    const uint32_t h4 = h * 0x01010101u, p4 = p * 0x01010101u;
     for (int64_t i = blockIdx.y; i < mp; i += gridDim.y) {
-        char4 v = make_char4(0, 0, 0, 0);
-        if (i < m) {
-            const uint8_t *a = A + i * lda;
-            v.x = l + 0 < k ? centre(a[l + 0], p, h) : 0;
-            v.y = l + 1 < k ? centre(a[l + 1], p, h) : 0;
-            v.z = l + 2 < k ? centre(a[l + 2], p, h) : 0;
-            v.w = l + 3 < k ? centre(a[l + 3], p, h) : 0;
-        }
-        *reinterpret_cast<char4 *>(Ac + i * kp + l) = v;
+        const uint4 v = load16_bytes(A + i * lda + l, l, k, i < m);
+        *reinterpret_cast<uint4 *>(Ac + i * kp + l) =
+            make_uint4(centre4(v.x, h4, p4), centre4(v.y, h4, p4), centre4(v.z, h4, p4), centre4(v.w, h4, p4));
     }
 }
 
 // Bt[j][l] = centre(B[l][j]) for l < k, j < n; zero elsewhere in np x kp.
-// 64 x 64 byte tiles through shared memory.
+// 64 x 64 byte tiles through shared memory, 256 threads, 16 values each way;
+// CENTRE_TU column tiles per step of the grid-stride loop, all of their loads
+// issued first.
+constexpr int CENTRE_TU = 4;
+
 __global__ void centre_transpose_kernel(const uint8_t *__restrict__ B, int64_t ldb, int64_t k,
                                         int64_t n, int8_t *__restrict__ Bt, int64_t kp, int64_t np,
                                         uint32_t p, uint32_t h) {
-    __shared__ int8_t tile[64][64 + 4];
+    __shared__ __align__(16) uint8_t tile[64][64 + 4];
     const int64_t l0 = (int64_t)blockIdx.x * 64;
-    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;   // 256 threads: 64 x 4
-    // column tiles of 64 in a grid-stride loop (np / 64 may exceed the grid's y limit)
-    for (int64_t jt = blockIdx.y; jt < np / 64; jt += gridDim.y) {
-        const int64_t j0 = jt * 64;
-        for (int r = ty; r < 64; r += 4) {
-            const int64_t l = l0 + r, j = j0 + tx;
-            tile[r][tx] = (l < k && j < n) ? centre(B[l * ldb + j], p, h) : (int8_t)0;
+    const int t = threadIdx.x, r = t >> 2, q = (t & 3) * 16;
+    const int64_t l = l0 + r;
+    const uint32_t h4 = h * 0x01010101u, p4 = p * 0x01010101u;
+    for (int64_t jt = blockIdx.y; jt < np / 64; jt += CENTRE_TU * (int64_t)gridDim.y) {
+        uint4 v[CENTRE_TU];
+#pragma unroll
+        for (int u = 0; u < CENTRE_TU; ++u) {
+            const int64_t j0 = (jt + u * (int64_t)gridDim.y) * 64;
+            v[u] = j0 < np ? load16_bytes(B + l * ldb + j0 + q, j0 + q, n, l < k) : make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncthreads();
-        for (int r = ty; r < 64; r += 4) {
-            const int64_t j = j0 + r, l = l0 + tx;
-            if (j < np && l < kp) Bt[j * kp + l] = tile[tx][r];
+#pragma unroll
+        for (int u = 0; u < CENTRE_TU; ++u) {
+            const int64_t j0 = (jt + u * (int64_t)gridDim.y) * 64;
+            if (j0 >= np) break;   // the same in every thread of the block
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&tile[r][q]);
+            dst[0] = centre4(v[u].x, h4, p4);
+            dst[1] = centre4(v[u].y, h4, p4);
+            dst[2] = centre4(v[u].z, h4, p4);
+            dst[3] = centre4(v[u].w, h4, p4);
+            __syncthreads();
+            // row j0 + r of Bt, columns l0 + q .. l0 + q + 15 (np a multiple of 64: j < np)
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int e = 0; e < 16; ++e) w[e >> 2] |= (uint32_t)tile[q + e][r] << (8 * (e & 3));
+            *reinterpret_cast<uint4 *>(Bt + (j0 + r) * kp + l0 + q) = make_uint4(w[0], w[1], w[2], w[3]);
+            __syncthreads();   // the tile is refilled by the next column tile
         }
-        __syncthreads();
     }
 }
 
@@ -258,9 +287,10 @@ gfp_status launch_tc_mma(uint32_t p, int64_t m, int64_t k, int64_t n, const uint
     int8_t *Bt = Ac + mp * kp;
     const uint32_t h = p == 2 ? 1u : (p - 1) / 2;   // p = 2: residues stay 0/1
     {
-        dim3 grid((unsigned)((kp / 4 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
+        dim3 grid((unsigned)((kp / 16 + 255) / 256), (unsigned)(mp < 65535 ? mp : 65535));
         centre_rows_kernel<<<grid, 256, 0, s>>>(A, lda, m, k, Ac, kp, mp, p, h);
-        dim3 gt((unsigned)(kp / 64), (unsigned)(np / 64 < 65535 ? np / 64 : 65535));
+        const int64_t gy = (np / 64 + CENTRE_TU - 1) / CENTRE_TU;
+        dim3 gt((unsigned)(kp / 64), (unsigned)(gy < 65535 ? gy : 65535));
         centre_transpose_kernel<<<gt, 256, 0, s>>>(B, ldb, k, n, Bt, kp, np, p, h);
     }
     MmaArgs g;
